@@ -1,0 +1,389 @@
+/*
+ * mxm_oracle.c -- CPU oracle for the mod2am dense product and its
+ * FP64-accurate Ozaki-split emulation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * reference that the CUDA library is checked against.  Only the test suite,
+ * the package smoke check and the CPU-baseline leg of the benchmark load it.
+ * It shares no code, header, table or constant with the CUDA path.
+ *
+ * Build: gcc -std=c11 -O2 -fno-fast-math -ffp-contract=off [-fopenmp]
+ * (-ffp-contract=off matters: every a*b+c below is two roundings, never an
+ * FMA, except where fma() is written out on purpose in Dot2.)
+ *
+ * Storage: every matrix is dense row-major, element (i,j) of an r x c matrix
+ * at X[i*c + j]; A is m x k, B is k x n, C is m x n (Sec. 3.1 states the
+ * square n x n case; general m,k,n is the reading used throughout).
+ *
+ * Contents
+ *   oracle_gemm_naive   c_ij = sum_l a_il b_lj, three nested loops, l in order
+ *                       (Sec. 3.1: the naive three-loop C version, arbb_mxm0);
+ *                       rows shared out by an OpenMP parallel-for on the
+ *                       outermost loop, as in the paper's OpenMP baseline.
+ *   oracle_gemm_outer   rank-1 update order of arbb_mxm2a (Sec. 3.1):
+ *                       c = a_col(0) b_row(0); c += a_col(l) b_row(l).
+ *   oracle_gemm_dot2    each c_ij by Dot2 (Ogita, Rump, Oishi, "Accurate sum
+ *                       and dot product", SIAM J. Sci. Comput. 26(6), 2005,
+ *                       Algorithm 5.3): as accurate as twice-FP64 evaluation.
+ *   oracle_gemm_abs     |A|.|B|, the scale of the elementwise error bound.
+ *   oracle_ozaki_*      the Ozaki split (Ozaki, Ogita, Oishi, Rump, Numer.
+ *                       Algorithms 59, 2012; integer-slice form of Ootomo,
+ *                       Ozaki, Yokota, IJHPCA 2024) in the steps:
+ *                       scale, split, exact slice products, recombination.
+ *   oracle_gemm_f32     FP32 naive loop (comparison mode).
+ *   oracle_round_bf16   double -> bfloat16, round to nearest even.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_OK 0
+#define ORACLE_NONFINITE 4
+#define ORACLE_INVALID 1
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------ */
+/* Plain definition: c_ij = sum_{l=0}^{k-1} a_il * b_lj  (Sec. 3.1).   */
+/* ------------------------------------------------------------------ */
+void oracle_gemm_naive(const double* A, const double* B, double* C,
+                       int64_t m, int64_t k, int64_t n) {
+  int64_t i;
+#pragma omp parallel for schedule(static)
+  for (i = 0; i < m; ++i) {
+    for (int64_t j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int64_t l = 0; l < k; ++l) s += A[i * k + l] * B[l * n + j];
+      C[i * n + j] = s;
+    }
+  }
+}
+
+/* arbb_mxm2a (Sec. 3.1): c starts as the first rank-1 product
+ * a.col(0) * b.row(0), then every further l adds a.col(l) * b.row(l).
+ * Per element this is the same left-to-right sum as the naive loop.    */
+void oracle_gemm_outer(const double* A, const double* B, double* C,
+                       int64_t m, int64_t k, int64_t n) {
+  if (k == 0) {
+    for (int64_t t = 0; t < m * n; ++t) C[t] = 0.0;
+    return;
+  }
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t j = 0; j < n; ++j) C[i * n + j] = A[i * k + 0] * B[0 * n + j];
+  for (int64_t l = 1; l < k; ++l)
+    for (int64_t i = 0; i < m; ++i)
+      for (int64_t j = 0; j < n; ++j) C[i * n + j] += A[i * k + l] * B[l * n + j];
+}
+
+/* Error-free transformations (Ogita, Rump, Oishi 2005, Sec. 2-3). */
+static void two_sum(double a, double b, double* x, double* y) {
+  double s = a + b;
+  double z = s - a;
+  *x = s;
+  *y = (a - (s - z)) + (b - z);
+}
+
+static void two_product(double a, double b, double* x, double* y) {
+  double p = a * b;
+  *x = p;
+  *y = fma(a, b, -p);
+}
+
+/* Dot2 of row i of A with column j of B. */
+static double dot2_entry(const double* A, const double* B, int64_t k, int64_t n,
+                         int64_t i, int64_t j) {
+  if (k == 0) return 0.0;
+  double p, s;
+  two_product(A[i * k + 0], B[0 * n + j], &p, &s);
+  for (int64_t l = 1; l < k; ++l) {
+    double h, r, q;
+    two_product(A[i * k + l], B[l * n + j], &h, &r);
+    two_sum(p, h, &p, &q);
+    s = s + (q + r);
+  }
+  return p + s;
+}
+
+void oracle_gemm_dot2(const double* A, const double* B, double* C,
+                      int64_t m, int64_t k, int64_t n) {
+  int64_t i;
+#pragma omp parallel for schedule(static)
+  for (i = 0; i < m; ++i)
+    for (int64_t j = 0; j < n; ++j) C[i * n + j] = dot2_entry(A, B, k, n, i, j);
+}
+
+/* (|A|.|B|)_ij, naive order. */
+void oracle_gemm_abs(const double* A, const double* B, double* C,
+                     int64_t m, int64_t k, int64_t n) {
+  int64_t i;
+#pragma omp parallel for schedule(static)
+  for (i = 0; i < m; ++i) {
+    for (int64_t j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int64_t l = 0; l < k; ++l) s += fabs(A[i * k + l]) * fabs(B[l * n + j]);
+      C[i * n + j] = s;
+    }
+  }
+}
+
+/* Selected entries (ii[t], jj[t]) only: used to check full-size results on
+ * a sample.  out_dot2 and out_abs may each be NULL.                    */
+void oracle_entries_dot2_abs(const double* A, const double* B, int64_t m,
+                             int64_t k, int64_t n, int64_t count,
+                             const int64_t* ii, const int64_t* jj,
+                             double* out_dot2, double* out_abs) {
+  (void)m;
+  int64_t t;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (t = 0; t < count; ++t) {
+    int64_t i = ii[t], j = jj[t];
+    if (out_dot2) out_dot2[t] = dot2_entry(A, B, k, n, i, j);
+    if (out_abs) {
+      double s = 0.0;
+      for (int64_t l = 0; l < k; ++l) s += fabs(A[i * k + l]) * fabs(B[l * n + j]);
+      out_abs[t] = s;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Ozaki split, step by step.                                          */
+/*                                                                     */
+/* Step 1, scale: every row i of A gets the exponent e_i with          */
+/*   max_l |a_il| = mu * 2^{e_i},  mu in [1/2, 1)   (frexp),            */
+/* so that every a_il * 2^{-e_i} lies in (-1, 1); an all-zero row gets  */
+/* e_i = 0.  Columns j of B get f_j the same way.                       */
+/* Step 2, split: with r_0 = x * 2^{-e} and slice width beta bits,      */
+/*   t_s = r_{s-1} * 2^beta,  d_s = trunc(t_s),  r_s = t_s - d_s,       */
+/* for s = 1..S, so x = 2^e (sum_s d_s 2^{-beta s} + r_S 2^{-beta S})   */
+/* with integer digits |d_s| <= 2^beta - 1 (127 for beta = 7: int8).     */
+/* Step 3, exact products: for every diagonal g = s + t in 2..S+1,       */
+/*   D_g(i,j) = sum_{s+t=g} sum_l d^A_s(i,l) d^B_t(l,j),  in int64.      */
+/* Step 4, recombine in FP64, smallest weight first:                    */
+/*   acc = 0; for g = S+1 down to 2: acc = acc + D_g * 2^{-beta g};     */
+/*   c_ij = acc * 2^{e_i + f_j}.                                        */
+/* ------------------------------------------------------------------ */
+
+/* frexp exponent of |x|, 0 for x == 0 (x finite). */
+static int oracle_exponent(double x) {
+  int e = 0;
+  if (x == 0.0) return 0;
+  (void)frexp(x, &e);
+  return e;
+}
+
+static int is_finite(double x) { return isfinite(x) ? 1 : 0; }
+
+/* Step 1 for the rows of an r x c matrix (by_col = 0) or for its
+ * columns (by_col = 1).  Returns ORACLE_NONFINITE if any entry is not
+ * finite (exps then unspecified).                                      */
+int oracle_ozaki_exponents(const double* X, int64_t rows, int64_t cols,
+                           int by_col, int32_t* exps) {
+  int bad = 0;
+  if (!by_col) {
+    for (int64_t i = 0; i < rows; ++i) {
+      double mx = 0.0;
+      for (int64_t l = 0; l < cols; ++l) {
+        double v = X[i * cols + l];
+        if (!is_finite(v)) bad = 1;
+        if (fabs(v) > mx) mx = fabs(v);
+      }
+      exps[i] = oracle_exponent(mx);
+    }
+  } else {
+    for (int64_t j = 0; j < cols; ++j) {
+      double mx = 0.0;
+      for (int64_t l = 0; l < rows; ++l) {
+        double v = X[l * cols + j];
+        if (!is_finite(v)) bad = 1;
+        if (fabs(v) > mx) mx = fabs(v);
+      }
+      exps[j] = oracle_exponent(mx);
+    }
+  }
+  return bad ? ORACLE_NONFINITE : ORACLE_OK;
+}
+
+/* Step 2 for one value. */
+static void split_value(double x, int e, int beta, int S, int16_t* d, int64_t stride) {
+  double r = ldexp(x, -e);
+  for (int s = 0; s < S; ++s) {
+    double t = ldexp(r, beta);
+    double q = trunc(t);
+    r = t - q;
+    d[s * stride] = (int16_t)q;
+  }
+}
+
+/* Steps 1 and 2 for a whole matrix.  digits is [S][rows][cols] int16. */
+int oracle_ozaki_split(const double* X, int64_t rows, int64_t cols, int by_col,
+                       int beta, int S, int32_t* exps, int16_t* digits) {
+  if (beta < 1 || beta > 8 || S < 1) return ORACLE_INVALID;
+  int st = oracle_ozaki_exponents(X, rows, cols, by_col, exps);
+  if (st != ORACLE_OK) return st;
+  const int64_t plane = rows * cols;
+  for (int64_t i = 0; i < rows; ++i)
+    for (int64_t l = 0; l < cols; ++l) {
+      int e = by_col ? exps[l] : exps[i];
+      split_value(X[i * cols + l], e, beta, S, digits + i * cols + l, plane);
+    }
+  return ORACLE_OK;
+}
+
+/* Steps 3 and 4 for one entry.  dA is [S][m][k]; dBt holds the digits of
+ * B with each column stored contiguously, [S][n][k] (a storage choice:
+ * the integer sums are exact, so it does not change any value).        */
+static double ozaki_entry(const int16_t* dA, const int16_t* dBt, int64_t m,
+                          int64_t k, int64_t n, int S, int beta, int32_t e_i,
+                          int32_t f_j, int64_t i, int64_t j) {
+  const int64_t planeA = m * k, planeB = n * k;
+  double acc = 0.0;
+  for (int g = S + 1; g >= 2; --g) {
+    int64_t Dg = 0;
+    for (int s = 1; s <= g - 1; ++s) {
+      int t = g - s;
+      const int16_t* a = dA + (int64_t)(s - 1) * planeA + i * k;
+      const int16_t* b = dBt + (int64_t)(t - 1) * planeB + j * k;
+      for (int64_t l = 0; l < k; ++l) Dg += (int64_t)a[l] * (int64_t)b[l];
+    }
+    acc = acc + ldexp((double)Dg, -beta * g);
+  }
+  return ldexp(acc, e_i + f_j);
+}
+
+/* Full emulated product C = A.B with S slices of beta bits. */
+int oracle_ozaki_gemm(const double* A, const double* B, double* C, int64_t m,
+                      int64_t k, int64_t n, int S, int beta) {
+  if (beta < 1 || beta > 8 || S < 1 || S > 16) return ORACLE_INVALID;
+  size_t szA = (size_t)(S * m * k > 0 ? S * m * k : 1);
+  size_t szB = (size_t)(S * k * n > 0 ? S * k * n : 1);
+  int32_t* e = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+  int32_t* f = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int16_t* dA = (int16_t*)malloc(sizeof(int16_t) * szA);
+  int16_t* dB = (int16_t*)malloc(sizeof(int16_t) * szB);
+  int16_t* dBt = (int16_t*)malloc(sizeof(int16_t) * szB);
+  int st = ORACLE_OK;
+  if (!e || !f || !dA || !dB || !dBt) { st = ORACLE_INVALID; goto done; }
+  st = oracle_ozaki_split(A, m, k, 0, beta, S, e, dA);
+  if (st == ORACLE_OK) st = oracle_ozaki_split(B, k, n, 1, beta, S, f, dB);
+  if (st != ORACLE_OK) goto done;
+  for (int s = 0; s < S; ++s)
+    for (int64_t l = 0; l < k; ++l)
+      for (int64_t j = 0; j < n; ++j)
+        dBt[(int64_t)s * n * k + j * k + l] = dB[(int64_t)s * k * n + l * n + j];
+  {
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (i = 0; i < m; ++i)
+      for (int64_t j = 0; j < n; ++j)
+        C[i * n + j] = ozaki_entry(dA, dBt, m, k, n, S, beta, e[i], f[j], i, j);
+  }
+done:
+  free(e); free(f); free(dA); free(dB); free(dBt);
+  return st;
+}
+
+/* Selected entries of the emulated product; splits only the rows and
+ * columns the sample touches.                                          */
+int oracle_ozaki_entries(const double* A, const double* B, int64_t m, int64_t k,
+                         int64_t n, int S, int beta, int64_t count,
+                         const int64_t* ii, const int64_t* jj, double* out) {
+  (void)m;
+  if (beta < 1 || beta > 8 || S < 1 || S > 16) return ORACLE_INVALID;
+  int bad = 0;
+  int64_t t;
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : bad)
+  for (t = 0; t < count; ++t) {
+    int64_t i = ii[t], j = jj[t];
+    int16_t* da = (int16_t*)malloc(sizeof(int16_t) * (size_t)(S * k > 0 ? S * k : 1));
+    int16_t* db = (int16_t*)malloc(sizeof(int16_t) * (size_t)(S * k > 0 ? S * k : 1));
+    double ma = 0.0, mb = 0.0;
+    for (int64_t l = 0; l < k; ++l) {
+      double a = A[i * k + l], b = B[l * n + j];
+      if (!is_finite(a) || !is_finite(b)) bad = 1;
+      if (fabs(a) > ma) ma = fabs(a);
+      if (fabs(b) > mb) mb = fabs(b);
+    }
+    /* the column exponent needs the whole column of B; the row exponent
+     * the whole row of A: both were just scanned.                      */
+    int ei = oracle_exponent(ma), fj = oracle_exponent(mb);
+    for (int64_t l = 0; l < k; ++l) {
+      split_value(A[i * k + l], ei, beta, S, da + l, k);
+      split_value(B[l * n + j], fj, beta, S, db + l, k);
+    }
+    double acc = 0.0;
+    for (int g = S + 1; g >= 2; --g) {
+      int64_t Dg = 0;
+      for (int s = 1; s <= g - 1; ++s) {
+        const int16_t* a = da + (int64_t)(s - 1) * k;
+        const int16_t* b = db + (int64_t)(g - s - 1) * k;
+        for (int64_t l = 0; l < k; ++l) Dg += (int64_t)a[l] * (int64_t)b[l];
+      }
+      acc = acc + ldexp((double)Dg, -beta * g);
+    }
+    out[t] = ldexp(acc, ei + fj);
+    free(da); free(db);
+  }
+  return bad ? ORACLE_NONFINITE : ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Comparison modes.                                                   */
+/* ------------------------------------------------------------------ */
+/* FP32 inputs, FP32 naive accumulation. */
+void oracle_gemm_f32(const float* A, const float* B, float* C, int64_t m,
+                     int64_t k, int64_t n) {
+  int64_t i;
+#pragma omp parallel for schedule(static)
+  for (i = 0; i < m; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      float s = 0.0f;
+      for (int64_t l = 0; l < k; ++l) s += A[i * k + l] * B[l * n + j];
+      C[i * n + j] = s;
+    }
+}
+
+/* double -> bfloat16 (1 sign, 8 exponent, 7 fraction bits), round to
+ * nearest, ties to even, by exact arithmetic on the value: bf16 spacing
+ * in [2^q, 2^{q+1}) is 2^{q-7}; below 2^-126 the spacing is 2^-133.
+ * Returns the 16-bit pattern.                                          */
+static uint16_t round_bf16_one(double x) {
+  uint64_t bits;
+  memcpy(&bits, &x, sizeof bits);
+  uint16_t sign = (uint16_t)((bits >> 48) & 0x8000u);
+  if (isnan(x)) return (uint16_t)(sign | 0x7FC0u);
+  double ax = fabs(x);
+  if (isinf(x)) return (uint16_t)(sign | 0x7F80u);
+  if (ax == 0.0) return sign;
+  int q;
+  (void)frexp(ax, &q);          /* ax in [2^{q-1}, 2^q) */
+  int lsb_exp = (q - 1) - 7;    /* spacing of the bf16 grid at ax */
+  if (lsb_exp < -133) lsb_exp = -133;
+  double scaled = ldexp(ax, -lsb_exp); /* exact: in [0, 2^8) */
+  double lo = floor(scaled);
+  double frac = scaled - lo;
+  double r = lo;
+  if (frac > 0.5 || (frac == 0.5 && fmod(lo, 2.0) != 0.0)) r = lo + 1.0;
+  double v = ldexp(r, lsb_exp);
+  if (v >= ldexp(1.0, 128)) return (uint16_t)(sign | 0x7F80u);
+  /* encode v exactly */
+  float fv = (float)v; /* exact: v has <= 8 significant bits, in float range */
+  uint32_t fb;
+  memcpy(&fb, &fv, sizeof fb);
+  return (uint16_t)(sign | (uint16_t)((fb >> 16) & 0x7FFFu));
+}
+
+void oracle_round_bf16(const double* x, uint16_t* out, int64_t count) {
+  for (int64_t t = 0; t < count; ++t) out[t] = round_bf16_one(x[t]);
+}

@@ -1,0 +1,127 @@
+"""Seeded synthetic inputs for the mod2am product (Sec. 3.1) and its variants.
+
+This module only draws numbers; it holds none of the product's arithmetic.
+Both the CUDA path and the CPU oracle are fed from it.  The paper measured
+on the EuroBen reference input sets, which are not available; these
+generators stand in for them with the shapes and value distributions of
+the workloads the library is benchmarked on.
+
+Generator: counter-based SplitMix64 (Steele, Lea, Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014).  Word ``i`` of stream
+``(seed, stream)`` is ``mix(key + (i + 1) * GAMMA)`` with
+``key = mix(seed * GAMMA ^ (stream + 1) * STREAM_MUL)`` and ``mix`` the
+SplitMix64 finaliser; all arithmetic modulo 2^64.  A uniform double in
+[0, 1) is the top 53 bits times 2^-53.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+STREAM_MUL = np.uint64(0xD1B54A32D192ED03)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    z = z.copy()
+    z ^= z >> np.uint64(30)
+    z *= _M1
+    z ^= z >> np.uint64(27)
+    z *= _M2
+    z ^= z >> np.uint64(31)
+    return z
+
+
+def words(seed: int, stream: int, count: int, *, chunk: int = 1 << 24) -> np.ndarray:
+    """``count`` 64-bit words of stream (seed, stream)."""
+    with np.errstate(over="ignore"):
+        s = np.array([seed & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64)
+        st = np.array([(stream + 1) & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64)
+        key = _mix(s * GAMMA ^ st * STREAM_MUL)[0]
+        out = np.empty(count, dtype=np.uint64)
+        for lo in range(0, count, chunk):
+            hi = min(count, lo + chunk)
+            ctr = np.arange(lo + 1, hi + 1, dtype=np.uint64)
+            out[lo:hi] = _mix(key + ctr * GAMMA)
+    return out
+
+
+def unit(seed: int, stream: int, count: int) -> np.ndarray:
+    """Uniform doubles in [0, 1): top 53 bits of each word times 2^-53."""
+    w = words(seed, stream, count)
+    return (w >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def uniform_pm1(seed: int, stream: int, shape) -> np.ndarray:
+    """Entries uniform in [-1, 1): 2u - 1 (exact in FP64)."""
+    shape = tuple(shape)
+    u = unit(seed, stream, int(np.prod(shape)))
+    return (2.0 * u - 1.0).reshape(shape)
+
+
+def int_uniform(seed: int, stream: int, shape, lo: int, hi: int) -> np.ndarray:
+    """Integers uniform in [lo, hi] (as float64), word mod (hi - lo + 1)."""
+    shape = tuple(shape)
+    w = words(seed, stream, int(np.prod(shape)))
+    span = np.uint64(hi - lo + 1)
+    return ((w % span).astype(np.int64) + lo).astype(np.float64).reshape(shape)
+
+
+def exp_spread(seed: int, stream: int, shape, emin: int = -20, emax: int = 20) -> np.ndarray:
+    """Entries s * u * 2^e: u uniform in [1, 2), s a random sign, e a
+    uniform integer in [emin, emax].  u comes from one word, s and e from
+    a second word of the same counter (stream + 1000003)."""
+    shape = tuple(shape)
+    cnt = int(np.prod(shape))
+    u = 1.0 + unit(seed, stream, cnt)
+    w2 = words(seed, stream + 1000003, cnt)
+    sign = np.where((w2 & np.uint64(1)) == 1, -1.0, 1.0)
+    span = np.uint64(emax - emin + 1)
+    e = ((w2 >> np.uint64(1)) % span).astype(np.int64) + emin
+    return (sign * np.ldexp(u, e)).reshape(shape)
+
+
+def permutation(seed: int, stream: int, n: int) -> np.ndarray:
+    """A permutation of range(n): argsort of n random words (stable)."""
+    return np.argsort(words(seed, stream, n), kind="stable")
+
+
+def permutation_matrix(seed: int, stream: int, n: int) -> np.ndarray:
+    p = permutation(seed, stream, n)
+    P = np.zeros((n, n), dtype=np.float64)
+    P[np.arange(n), p] = 1.0
+    return P
+
+
+def logu_dims(seed: int, stream: int, count: int, lo: int = 16, hi: int = 1024) -> np.ndarray:
+    """``count`` sizes round(exp(U[ln lo, ln hi]))."""
+    u = unit(seed, stream, count)
+    v = np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))
+    return np.clip(np.rint(v), lo, hi).astype(np.int64)
+
+
+def grouped_problems(seed: int, count: int, lo: int = 16, hi: int = 1024):
+    """Sizes (m, k, n) of ``count`` problems, each dimension log-uniform
+    in [lo, hi]: m from stream 0, k from stream 1, n from stream 2."""
+    m = logu_dims(seed, 0, count, lo, hi)
+    k = logu_dims(seed, 1, count, lo, hi)
+    n = logu_dims(seed, 2, count, lo, hi)
+    return np.stack([m, k, n], axis=1)
+
+
+def gemm_operands(kind: str, m: int, k: int, n: int, seed: int = 0, cfg: int = 0):
+    """A (m x k) and B (k x n) for one workload.
+
+    kind: ``"uniform"`` (U[-1,1)), ``"int8"`` (integers in [-8, 8]),
+    ``"spread"`` (s u 2^e, e in [-20, 20]).  A uses stream 2*cfg, B stream
+    2*cfg + 1.
+    """
+    if kind == "uniform":
+        return uniform_pm1(seed, 2 * cfg, (m, k)), uniform_pm1(seed, 2 * cfg + 1, (k, n))
+    if kind == "int8":
+        return (int_uniform(seed, 2 * cfg, (m, k), -8, 8),
+                int_uniform(seed, 2 * cfg + 1, (k, n), -8, 8))
+    if kind == "spread":
+        return exp_spread(seed, 2 * cfg, (m, k)), exp_spread(seed, 2 * cfg + 1, (k, n))
+    raise ValueError(f"unknown input kind {kind!r}")

@@ -1,0 +1,67 @@
+"""The oracle pins must catch plausible mistakes.
+
+Each case below plants one mistake in a private copy of the oracle's C
+source (a dropped term, a flipped sign, a wrong slice weight, a missing
+diagonal, rounding instead of truncation, an off-by-one exponent, a wrong
+slice index, a missing absolute value, a dropped Dot2 correction), compiles
+it, and runs tests/test_oracle_pins.py against it in a subprocess: every
+mutant must make that suite fail.  Nothing here touches a GPU.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "mxm_oracle.c")
+
+MUTANTS = {
+    "naive_drops_last_term": (
+        "for (int64_t l = 0; l < k; ++l) s += A[i * k + l] * B[l * n + j];\n      C[i * n + j] = s;\n    }\n  }\n}\n\n/* arbb_mxm2a",
+        "for (int64_t l = 0; l + 1 < k; ++l) s += A[i * k + l] * B[l * n + j];\n      C[i * n + j] = s;\n    }\n  }\n}\n\n/* arbb_mxm2a"),
+    "naive_sign_flip": (
+        "s += A[i * k + l] * B[l * n + j];\n      C[i * n + j] = s;\n    }\n  }\n}\n\n/* arbb_mxm2a",
+        "s -= A[i * k + l] * B[l * n + j];\n      C[i * n + j] = s;\n    }\n  }\n}\n\n/* arbb_mxm2a"),
+    "dot2_drops_correction": ("s = s + (q + r);", "s = s + q;"),
+    "ozaki_wrong_weight": (
+        "acc = acc + ldexp((double)Dg, -beta * g);\n  }\n  return ldexp(acc, e_i + f_j);",
+        "acc = acc + ldexp((double)Dg, -beta * (g - 1));\n  }\n  return ldexp(acc, e_i + f_j);"),
+    "ozaki_drops_last_diagonal": (
+        "double acc = 0.0;\n  for (int g = S + 1; g >= 2; --g) {\n    int64_t Dg = 0;\n    for (int s = 1; s <= g - 1; ++s) {\n      int t = g - s;",
+        "double acc = 0.0;\n  for (int g = S; g >= 2; --g) {\n    int64_t Dg = 0;\n    for (int s = 1; s <= g - 1; ++s) {\n      int t = g - s;"),
+    "ozaki_rounds_not_truncates": ("double q = trunc(t);", "double q = round(t);"),
+    "ozaki_exponent_off_by_one": ("(void)frexp(x, &e);\n  return e;", "(void)frexp(x, &e);\n  return e + 1;"),
+    "ozaki_wrong_slice_index": (
+        "const int16_t* b = dBt + (int64_t)(t - 1) * planeB + j * k;",
+        "const int16_t* b = dBt + (int64_t)(s - 1) * planeB + j * k; (void)t;"),
+    "abs_missing_fabs": (
+        "s += fabs(A[i * k + l]) * fabs(B[l * n + j]);\n      C[i * n + j] = s;",
+        "s += A[i * k + l] * fabs(B[l * n + j]);\n      C[i * n + j] = s;"),
+}
+
+
+def _compile(src_text, out_dir):
+    c = os.path.join(out_dir, "mut.c")
+    so = os.path.join(out_dir, "libmut.so")
+    with open(c, "w") as fh:
+        fh.write(src_text)
+    cmd = ["gcc", "-std=c11", "-O2", "-fno-fast-math", "-ffp-contract=off", "-shared",
+           "-fPIC", c, "-o", so, "-lm"]
+    subprocess.run(cmd, check=True, capture_output=True)
+    return so
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site for {name} not unique/found"
+    so = _compile(text.replace(old, new), str(tmp_path))
+    env = dict(os.environ, MXM_ORACLE_LIB=so, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived the oracle pins"
