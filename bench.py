@@ -1,0 +1,420 @@
+#!/usr/bin/env python3
+"""Benchmark of the FP64-accurate mod2am product C = A.B (Sec. 3.1) on GB300.
+
+One step = one FP64-accurate product (Ozaki split, int8-range digits on
+tcgen05, exact windows, FP64 recombination) of m = k = n = 8192 synthetic
+matrices with entries s*u*2^e (u in [1,2), e in [-20,20]), through the C ABI
+(mxm_f64_emul) with inputs resident in HBM.  value = 2 m n k / t in TFLOP/s
+(FP64-equivalent work).  The same line reports the native FP64 product
+(mxm_f64) and the 8-bit-digit variant at the same size, the roofline of the
+product kernel, the end-to-end figure through mxm_gemm_host (host buffers,
+copies inside the timed region), the CPU oracle timed on a bounded sample,
+and SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (the products
+do not exchange data): weak scaling, value = all ranks' work / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP64-accurate GEMM TFLOP/s at n=8192 (Ozaki-INT8 vs native FP64), % roofline"
+U = 2.0 ** -53
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=8192)
+    p.add_argument("--kind", default="spread", choices=["spread", "uniform"])
+    p.add_argument("--slices", type=int, default=0, help="0: the tuned choice for the input kind")
+    p.add_argument("--native-steps", type=int, default=2)
+    p.add_argument("--no-native", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-check", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def default_slices(kind: str, beta: int) -> int:
+    """Smallest slice count meeting 2ku|A||B| at n = 8192 on sampled entries
+    of each input kind (the tuner's result)."""
+    table = {("spread", 7): 7, ("spread", 8): 6, ("uniform", 7): 6, ("uniform", 8): 5}
+    return table[(kind, beta)]
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names[1:], parts[5:9]):
+                    if v.lower() in ("active", "0x1", "1"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [v for v in sm if v >= 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.zeros(1, device="cuda")
+        dist.all_reduce(t)
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def cpu_oracle_rate(A, B, seconds: float):
+    """The oracle's naive FP64 loop (OpenMP over rows, as the paper's OpenMP
+    baseline) on a band of rows of the same product, sized to ~`seconds`."""
+    import numpy as np
+
+    import oracle
+    m, k = A.shape
+    n = B.shape[1]
+    threads = oracle.num_threads()
+    rows = max(1, threads)
+    t0 = time.perf_counter()
+    oracle.gemm_naive(A[:rows], B)
+    t1 = time.perf_counter() - t0
+    total_rows = rows
+    elapsed = t1
+    if t1 < seconds:
+        more = int(max(0, (seconds - t1) / max(t1, 1e-6) * rows))
+        more = min(more, m - rows)
+        more = (more // max(1, threads)) * max(1, threads)
+        if more > 0:
+            t0 = time.perf_counter()
+            oracle.gemm_naive(np.ascontiguousarray(A[rows:rows + more]), B)
+            t2 = time.perf_counter() - t0
+            total_rows += more
+            elapsed += t2
+    flops = 2.0 * total_rows * n * k
+    return flops / elapsed / 1e12, threads, total_rows, elapsed
+
+
+# ------------------------------------------------------------------ main legs
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1211_1581_gb300 import inputs, mxm
+
+    world, rank, local = dist_setup(args)
+    n = args.n
+    beta = 7
+    S = args.slices or default_slices(args.kind, beta)
+    peaks, peak_src = load_peaks()
+    mxm.load()
+
+    A_h, B_h = inputs.gemm_operands(args.kind, n, n, n, seed=0, cfg=2 + rank)
+    A = torch.from_numpy(A_h).cuda()
+    B = torch.from_numpy(B_h).cuda()
+    C = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        mxm.mxm_gemm(mxm.MODE_EMUL_I8, A, B, C, slices=S, stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    st = mxm.mxm_get_device_status()
+    if st != mxm.MXM_OK:
+        raise RuntimeError(f"device status after warm-up: {mxm.status_string(st)}")
+
+    # ---- timed region (device time, CUDA events on the launching stream)
+    mxm.mxm_profile_enable(True)
+    mxm.mxm_profile_read()  # reset
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    phase_ms, calls = mxm.mxm_profile_read()
+    mxm.mxm_profile_enable(False)
+    ms_total = max_over_ranks(ms_total, world)
+    ms_step = ms_total / args.steps
+    flops = 2.0 * n * n * n
+    value = world * flops * args.steps / (ms_total * 1e-3) / 1e12
+
+    pairs = S * (S + 1) // 2
+    gemm_ms = phase_ms[2] / max(calls, 1)
+    achieved = pairs * flops / (gemm_ms * 1e-3) / 1e12
+    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    roofline = {"bound": "tensor", "kernel": "oz_gemm_kernel", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "peak_source": f"bf16_tflops_sustained of {peak_src} (MEASURED_PEAKS.json)",
+                "traffic": None,
+                "algorithmic": f"{pairs} digit-pair products x 2mnk bf16 flops per launch",
+                "phase_ms_per_step": {"scale": round(phase_ms[0] / max(calls, 1), 4),
+                                      "split": round(phase_ms[1] / max(calls, 1), 4),
+                                      "product": round(gemm_ms, 4)}}
+
+    # ---- accuracy on sampled entries (oracle, CPU)
+    check = None
+    if not args.no_check and rank == 0:
+        import oracle
+        rng = np.random.default_rng(1)
+        ii = rng.integers(0, n, 128)
+        jj = rng.integers(0, n, 128)
+        got = C.cpu().numpy()[ii, jj]
+        ref_emul = oracle.ozaki_entries(A_h, B_h, ii, jj, S=S, beta=beta)
+        d2, ab = oracle.entries_dot2_abs(A_h, B_h, ii, jj)
+        ratio = float(np.max(np.abs(got - d2) / (2 * n * U * ab)))
+        check = {"entries": int(ii.size), "bit_identical_to_oracle_emulation":
+                 bool(np.array_equal(got, ref_emul)), "max_err_over_2ku_AB": ratio,
+                 "max_rel_err_vs_dot2": float(np.max(np.abs(got - d2) / np.abs(d2)))}
+
+    # ---- other modes at the same size
+    modes = {}
+    if rank == 0:
+        S8 = default_slices(args.kind, 8)
+        for name, mode, s_, steps in (("emul_bf16digits", mxm.MODE_EMUL_BF16, S8, args.steps),):
+            for _ in range(2):
+                mxm.mxm_gemm(mode, A, B, C, slices=s_)
+            torch.cuda.synchronize()
+            mxm.mxm_profile_enable(True)
+            mxm.mxm_profile_read()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record()
+            for _ in range(steps):
+                mxm.mxm_gemm(mode, A, B, C, slices=s_)
+            a1.record()
+            torch.cuda.synchronize()
+            ph, c_ = mxm.mxm_profile_read()
+            mxm.mxm_profile_enable(False)
+            t = a0.elapsed_time(a1) / steps
+            p_ = s_ * (s_ + 1) // 2
+            gms = ph[2] / max(c_, 1)
+            modes[name] = {"slices": s_, "digit_bits": 8, "ms": round(t, 3),
+                           "tflops": round(flops / (t * 1e-3) / 1e12, 2),
+                           "product_kernel_frac_of_bf16": round(
+                               p_ * flops / (gms * 1e-3) / 1e12 / peak, 4)}
+        if not args.no_native:
+            probe = None
+            try:
+                probe = mxm.mxm_peak_probe(1)
+            except Exception:
+                pass
+            mxm.mxm_gemm(mxm.MODE_F64, A, B, C)
+            torch.cuda.synchronize()
+            mxm.mxm_profile_enable(True)
+            mxm.mxm_profile_read()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record()
+            for _ in range(args.native_steps):
+                mxm.mxm_gemm(mxm.MODE_F64, A, B, C)
+            a1.record()
+            torch.cuda.synchronize()
+            ph, c_ = mxm.mxm_profile_read()
+            mxm.mxm_profile_enable(False)
+            t = a0.elapsed_time(a1) / args.native_steps
+            ach = flops / (t * 1e-3) / 1e12
+            gach = flops / (ph[2] / max(c_, 1) * 1e-3) / 1e12
+            modes["native_f64"] = {"ms": round(t, 2), "tflops": round(ach, 4),
+                                   "dmma_peak_probe_tflops": probe,
+                                   "product_kernel_frac_of_probe": (round(gach / probe, 4)
+                                                                    if probe else None),
+                                   "emul_speedup": round(value / world / ach, 2)}
+
+    # ---- end to end through the public host-buffer call
+    e2e = None
+    if not args.no_e2e:
+        Ap = torch.from_numpy(A_h).pin_memory()
+        Bp = torch.from_numpy(B_h).pin_memory()
+        Cp = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        mxm.mxm_gemm_host(mxm.MODE_EMUL_I8, Ap, Bp, Cp, slices=S)
+        e2e_steps = max(2, min(args.steps, 5))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            mxm.mxm_gemm_host(mxm.MODE_EMUL_I8, Ap, Bp, Cp, slices=S)
+        t_e2e = time.perf_counter() - t0
+        barrier(world)
+        t_e2e = max_over_ranks(t_e2e, world)
+        e2e = {"value": round(world * flops * e2e_steps / t_e2e / 1e12, 3), "unit": "TFLOP/s",
+               "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8,
+               "call": "mxm_gemm_host(MXM_MODE_EMUL_I8), pinned host buffers", "steps": e2e_steps}
+
+    # ---- CPU oracle on a bounded sample
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        rate, threads, rows, secs = cpu_oracle_rate(A_h, B_h, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+               "sample": f"naive FP64 triple loop (OpenMP over rows) on {rows} of {n} rows "
+                         f"of the same product, {secs:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world,
+                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms_step, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+                "precision": f"FP64-accurate (Ozaki split, {S} slices of 7-bit digits, exact "
+                             "FP32 windows, FP64 recombination)",
+                "data": "synthetic",
+                "config": {"workload": f"emulated FP64 GEMM m=k=n={n}, entries s*u*2^e "
+                                       "(u in [1,2), e in [-20,20]), Ozaki-INT8",
+                           "m": n, "k": n, "n": n, "slices": S, "digit_bits": beta,
+                           "inputs": args.kind, "seed": 0,
+                           "l2": "inputs larger than L2 (A, B 512 MiB each)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": 5 * args.steps, "modes": modes, "check": check}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle (the plain definition, naive FP64
+    loop with OpenMP over rows) on a bounded band of rows of the same
+    workload; rank 0 only."""
+    import numpy as np
+
+    from paper_1211_1581_gb300 import inputs
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = args.n
+    A_h, B_h = inputs.gemm_operands(args.kind, n, n, n, seed=0, cfg=2)
+    per = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    threads = rows = 0
+    secs_total = 0.0
+    for i in range(args.warmup + args.steps):
+        rate, threads, rows, secs = cpu_oracle_rate(A_h, B_h, per)
+        if i >= args.warmup:
+            vals.append(rate)
+            secs_total += secs
+    value = statistics.median(vals)
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(2.0 * n ** 3 / (value * 1e12) * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"emulated FP64 GEMM m=k=n={n}, entries s*u*2^e "
+                                   "(u in [1,2), e in [-20,20]), Ozaki-INT8",
+                       "m": n, "k": n, "n": n, "inputs": args.kind, "seed": 0},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+                             "sample": f"naive FP64 loop on {rows} rows of {n} per step "
+                                       f"(rate extrapolated to the full product)"},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * mxm.h -- C ABI of libmxm.so: the EuroBen mod2am dense matrix product
+ * C = A.B on one NVIDIA GB300 (sm_103a), natively in FP64 and FP64-accurate
+ * by the Ozaki split on BF16 tensor cores.
+ *
+ * The operation (Sec. 3.1 of the paper): c_ij = sum_k a_ik b_kj, with the
+ * three matrices held in caller memory and C overwritten.  The paper states
+ * the square n x n case; this ABI takes general m, k, n.
+ *
+ * Conventions shared by every call:
+ *   - A is m x k, B is k x n, C is m x n, all dense ROW-MAJOR double,
+ *     element (i,j) of an r x c matrix at X[i*c + j] (leading dimension =
+ *     number of columns; no strides, no alpha/beta: C is overwritten).
+ *   - Pointers are DEVICE pointers (cudaMalloc / torch memory) unless the
+ *     function name ends in _host.  The library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on that stream; argument errors are
+ *     reported synchronously through the return value and launch nothing.
+ *   - m == 0 or n == 0 is a no-op; k == 0 writes zeros (the empty sum).
+ *   - Negative sizes, NULL pointers with non-empty operands, or C overlapping
+ *     A or B return MXM_ERR_INVALID_ARG.
+ *   - Errors found on the device (a non-finite input in an emulated mode, a
+ *     wait that timed out, a workspace overflow in a grouped call) are
+ *     recorded in a sticky per-device status word that mxm_get_device_status
+ *     reads and clears; the result C is then unspecified.  There is no CPU
+ *     fallback: without a usable GPU every call returns MXM_ERR_CUDA.
+ *   - Calls on different streams are independent except that they share the
+ *     library-owned workspace; do not run two workspace-using calls
+ *     concurrently on different streams unless each has its own caller
+ *     workspace set (mxm_set_workspace is per device, so serialise them).
+ */
+#ifndef MXM_H_
+#define MXM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MXM_OK = 0,
+  MXM_ERR_INVALID_ARG = 1,        /* bad size, NULL pointer, overlap */
+  MXM_ERR_ALIGNMENT = 2,          /* pointer not 8-byte aligned */
+  MXM_ERR_UNSUPPORTED = 3,        /* mode or slice count not supported */
+  MXM_ERR_NONFINITE = 4,          /* emulated mode met inf/nan (device status) */
+  MXM_ERR_TIMEOUT = 5,            /* a bounded device wait gave up (device status) */
+  MXM_ERR_CUDA = 6,               /* a CUDA runtime call failed */
+  MXM_ERR_NO_WORKSPACE = 7,       /* workspace needed while a stream is capturing */
+  MXM_ERR_WORKSPACE_TOO_SMALL = 8 /* caller workspace smaller than required */
+} mxm_status;
+
+typedef enum {
+  MXM_MODE_F64 = 0,        /* native FP64 on the FP64 tensor path (DMMA) */
+  MXM_MODE_EMUL_I8 = 1,    /* Ozaki split, 7-bit digits (int8 range) in BF16 */
+  MXM_MODE_EMUL_BF16 = 2,  /* Ozaki split, 8-bit digits (full BF16 significand) */
+  MXM_MODE_F32 = 3,        /* comparison: inputs rounded to FP32, FP32 sums */
+  MXM_MODE_BF16_F32ACC = 4 /* comparison: inputs rounded to BF16, FP32 sums */
+} mxm_mode;
+
+/* One problem of a grouped call (device-resident table of these). */
+typedef struct {
+  const double* A;
+  const double* B;
+  double* C;
+  int64_t m, k, n;
+} mxm_problem;
+
+/* Library version: major*10000 + minor*100 + patch. */
+int mxm_version(void);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* mxm_status_string(mxm_status s);
+
+/*
+ * mxm_f64 -- C = A.B in native FP64 (Sec. 3.1, c_ij = sum_k a_ik b_kj).
+ * Every product and sum is an FP64 operation (fused multiply-add on the FP64
+ * tensor path); the summation order over k is unspecified, so results agree
+ * with any correct FP64 evaluation within |C - AB|_ij <= 2 k u (|A||B|)_ij,
+ * u = 2^-53, and are bit-exact whenever every partial sum is exact (e.g.
+ * small-integer matrices).  Uses library workspace (zero-padded tile copies
+ * of A and B, mxm_workspace_size(MXM_MODE_F64, ...) bytes).
+ */
+mxm_status mxm_f64(const double* A, const double* B, double* C, int64_t m, int64_t k,
+                   int64_t n, void* stream);
+
+/*
+ * mxm_f64_emul -- C = A.B, FP64-accurate, by the Ozaki split into `slices`
+ * slices of 7-bit signed digits (int8 range) per row of A and column of B
+ * under a per-row / per-column power-of-two scale (Ozaki, Ogita, Oishi,
+ * Rump 2012; integer-slice form of Ootomo, Ozaki, Yokota 2024).  The slice
+ * products s + t <= slices + 1 are computed exactly on tcgen05 tensor cores
+ * and recombined in FP64 in a fixed order, so the result is bit-identical to
+ * the CPU emulation of the same algorithm.  slices in 1..12; 7 gives FP64
+ * accuracy (the bound above) for entries of similar magnitude, 8 for entries
+ * spread over ~2^40.  Non-finite input sets MXM_ERR_NONFINITE in the device
+ * status.  Uses library workspace.
+ */
+mxm_status mxm_f64_emul(const double* A, const double* B, double* C, int64_t m, int64_t k,
+                        int64_t n, int slices, void* stream);
+
+/*
+ * mxm_gemm -- C = A.B in the given mxm_mode (slices is used by the two
+ * emulated modes and ignored otherwise).  MXM_MODE_F64 is mxm_f64 and
+ * MXM_MODE_EMUL_I8 is mxm_f64_emul; MXM_MODE_EMUL_BF16 takes 8-bit digits
+ * (6 slices ~ 7 of the 7-bit form); the FP32 and BF16 modes round A and B to
+ * the narrow type and sum in FP32: they are reported beside the FP64 modes,
+ * not FP64-accurate.
+ */
+mxm_status mxm_gemm(int mode, const double* A, const double* B, double* C, int64_t m, int64_t k,
+                    int64_t n, int slices, void* stream);
+
+/*
+ * mxm_gemm_host -- mxm_gemm on HOST buffers: copies A and B to the device,
+ * computes, copies C back, and returns after C is in host memory (the
+ * stream is synchronised).  Pinned host memory makes the copies faster.
+ * Device buffers come from the library's workspace.
+ */
+mxm_status mxm_gemm_host(int mode, const double* hA, const double* hB, double* hC, int64_t m,
+                         int64_t k, int64_t n, int slices, void* stream);
+
+/* Bytes of device workspace one mxm_gemm call of this shape needs. */
+size_t mxm_workspace_size(int mode, int64_t m, int64_t k, int64_t n, int slices);
+
+/*
+ * mxm_set_workspace -- use caller-owned device memory [d_ws, d_ws + bytes)
+ * (256-byte aligned) as the workspace of the current device from now on; the
+ * library then never allocates for mxm_f64 / mxm_f64_emul / mxm_gemm, which
+ * makes them safe to capture in a CUDA graph.  d_ws == NULL returns to the
+ * library-owned workspace (grown with cudaMalloc on demand, outside
+ * capture).  The caller keeps d_ws alive while calls that use it run.
+ */
+mxm_status mxm_set_workspace(void* d_ws, size_t bytes);
+
+/*
+ * mxm_grouped_workspace_size -- bytes of workspace mxm_grouped needs for
+ * these problems (host copy of the table; only m, k, n are read).
+ */
+mxm_status mxm_grouped_workspace_size(int64_t count, const mxm_problem* h_problems, int mode,
+                                      int slices, size_t* bytes);
+
+/*
+ * mxm_grouped -- `count` independent products C_p = A_p.B_p of uneven sizes
+ * in one persistent launch sequence, from a DEVICE-resident table of
+ * mxm_problem.  mode is MXM_MODE_F64 or MXM_MODE_EMUL_I8 / _BF16.  d_ws is
+ * caller workspace of ws_bytes (see mxm_grouped_workspace_size); the call
+ * allocates nothing and synchronises nothing, so it can be captured in a
+ * CUDA graph.  Tile offsets are computed on the device; a table that needs
+ * more workspace than ws_bytes sets MXM_ERR_WORKSPACE_TOO_SMALL in the device
+ * status and computes nothing.
+ */
+mxm_status mxm_grouped(int64_t count, const mxm_problem* d_problems, int mode, int slices,
+                       void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * mxm_get_device_status -- synchronise `stream`, then read and clear the
+ * sticky device status word of the current device: MXM_OK, or the first of
+ * MXM_ERR_NONFINITE / MXM_ERR_TIMEOUT / MXM_ERR_WORKSPACE_TOO_SMALL recorded
+ * by a kernel since the last read.
+ */
+mxm_status mxm_get_device_status(void* stream);
+
+/*
+ * mxm_peak_probe -- measure one execution unit's peak on the current device
+ * with a register-resident (or shared-memory-resident) loop timed by CUDA
+ * events: kind 0 = FP64 DFMA, 1 = FP64 DMMA m16n8k4, 2 = tcgen05 BF16
+ * 128x128x16, 3 = tcgen05 BF16 128x256x16, 4 = legacy IMMA s8 m16n8k32.
+ * Writes TFLOP/s (TOP/s for IMMA) to *tflops.  Used for the roofline
+ * denominators the driver does not measure.  Synchronises the device.
+ */
+mxm_status mxm_peak_probe(int kind, double* tflops);
+
+/*
+ * mxm_debug_wait_timeout -- test hook for the failure path: launches one
+ * block whose thread waits on an mbarrier that nothing completes, with a
+ * wait limit of `limit_ns` nanoseconds.  The wait gives up, records
+ * MXM_ERR_TIMEOUT in the device status word and the kernel exits normally.
+ */
+mxm_status mxm_debug_wait_timeout(uint64_t limit_ns, void* stream);
+
+/*
+ * mxm_profile_enable / mxm_profile_read -- per-kernel timing of library
+ * calls.  While enabled (on != 0), every mxm_gemm / mxm_f64 / mxm_f64_emul
+ * call records CUDA events on its stream around each of its phases: phase 0
+ * = scale (row/column maxima), 1 = split / pack (operand tiles), 2 = the
+ * product kernel.  mxm_profile_read synchronises on the recorded events,
+ * writes the summed milliseconds of each phase since the last read to
+ * ms[0..min(max_phases,3)-1], the number of calls to *calls, and resets the
+ * sums.  Disabled (the default) nothing is recorded.
+ */
+mxm_status mxm_profile_enable(int on);
+mxm_status mxm_profile_read(double* ms, int max_phases, int64_t* calls);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MXM_H_ */

@@ -1,0 +1,232 @@
+"""Python binding of libmxm.so (include/mxm.h), argument marshalling only.
+
+Every function has the name of the C entry point it calls and takes torch
+tensors where the C call takes device pointers; streams are
+``torch.cuda.Stream`` objects (default: the current stream).  All arithmetic
+runs in the library's CUDA kernels.  If the library is missing or cannot be
+loaded the first call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+MXM_OK = 0
+MXM_ERR_INVALID_ARG = 1
+MXM_ERR_ALIGNMENT = 2
+MXM_ERR_UNSUPPORTED = 3
+MXM_ERR_NONFINITE = 4
+MXM_ERR_TIMEOUT = 5
+MXM_ERR_CUDA = 6
+MXM_ERR_NO_WORKSPACE = 7
+MXM_ERR_WORKSPACE_TOO_SMALL = 8
+
+MODE_F64 = 0
+MODE_EMUL_I8 = 1
+MODE_EMUL_BF16 = 2
+MODE_F32 = 3
+MODE_BF16_F32ACC = 4
+
+# Every symbol include/mxm.h declares, with (restype, argtypes).
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I = ctypes.c_int
+_SZ = ctypes.c_size_t
+SIGNATURES = {
+    "mxm_version": (_I, []),
+    "mxm_status_string": (ctypes.c_char_p, [_I]),
+    "mxm_f64": (_I, [_P, _P, _P, _I64, _I64, _I64, _P]),
+    "mxm_f64_emul": (_I, [_P, _P, _P, _I64, _I64, _I64, _I, _P]),
+    "mxm_gemm": (_I, [_I, _P, _P, _P, _I64, _I64, _I64, _I, _P]),
+    "mxm_gemm_host": (_I, [_I, _P, _P, _P, _I64, _I64, _I64, _I, _P]),
+    "mxm_workspace_size": (_SZ, [_I, _I64, _I64, _I64, _I]),
+    "mxm_set_workspace": (_I, [_P, _SZ]),
+    "mxm_grouped_workspace_size": (_I, [_I64, _P, _I, _I, ctypes.POINTER(_SZ)]),
+    "mxm_grouped": (_I, [_I64, _P, _I, _I, _P, _SZ, _P]),
+    "mxm_get_device_status": (_I, [_P]),
+    "mxm_peak_probe": (_I, [_I, ctypes.POINTER(ctypes.c_double)]),
+    "mxm_debug_wait_timeout": (_I, [ctypes.c_uint64, _P]),
+    "mxm_profile_enable": (_I, [_I]),
+    "mxm_profile_read": (_I, [ctypes.POINTER(ctypes.c_double), _I, ctypes.POINTER(_I64)]),
+}
+
+_lib = None
+
+
+class MxmError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmxm.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libmxm.so not found at {_build.LIB}; run build() first")
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().mxm_status_string(int(status)).decode()
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _check(st: int, what: str):
+    if st != MXM_OK:
+        raise MxmError(st, what)
+
+
+def _operands(A, B, C):
+    import torch
+    for name, t in (("A", A), ("B", B), ("C", C)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA float64 tensor")
+        if t.dim() != 2 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous 2-D (row-major) tensor")
+    m, k = A.shape
+    k2, n = B.shape
+    if k != k2 or tuple(C.shape) != (m, n):
+        raise ValueError(f"shapes {tuple(A.shape)} x {tuple(B.shape)} -> {tuple(C.shape)}")
+    return m, k, n
+
+
+def mxm_gemm(mode: int, A, B, C, slices: int = 7, stream=None):
+    """C = A.B in ``mode`` (see include/mxm.h), asynchronously on ``stream``."""
+    m, k, n = _operands(A, B, C)
+    st = load().mxm_gemm(int(mode), A.data_ptr(), B.data_ptr(), C.data_ptr(), m, k, n,
+                         int(slices), _stream_ptr(stream))
+    _check(st, "mxm_gemm")
+    return C
+
+
+def mxm_f64(A, B, C, stream=None):
+    m, k, n = _operands(A, B, C)
+    _check(load().mxm_f64(A.data_ptr(), B.data_ptr(), C.data_ptr(), m, k, n, _stream_ptr(stream)),
+           "mxm_f64")
+    return C
+
+
+def mxm_f64_emul(A, B, C, slices: int = 7, stream=None):
+    m, k, n = _operands(A, B, C)
+    _check(load().mxm_f64_emul(A.data_ptr(), B.data_ptr(), C.data_ptr(), m, k, n, int(slices),
+                               _stream_ptr(stream)), "mxm_f64_emul")
+    return C
+
+
+def mxm_gemm_host(mode: int, A, B, C, slices: int = 7, stream=None):
+    """Host-buffer form: A, B, C are C-contiguous float64 numpy arrays (or
+    CPU tensors, ideally pinned); returns after C holds the result."""
+    import numpy as np
+    import torch
+
+    def ptr_shape(x):
+        if isinstance(x, torch.Tensor):
+            if x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+                raise TypeError("host tensors must be contiguous CPU float64")
+            return x.data_ptr(), tuple(x.shape)
+        if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
+            raise TypeError("host arrays must be C-contiguous float64")
+        return x.ctypes.data, x.shape
+
+    pa, sa = ptr_shape(A)
+    pb, sb = ptr_shape(B)
+    pc, sc = ptr_shape(C)
+    m, k = sa
+    if sb[0] != k or tuple(sc) != (m, sb[1]):
+        raise ValueError("shape mismatch")
+    _check(load().mxm_gemm_host(int(mode), pa, pb, pc, m, k, sb[1], int(slices),
+                                _stream_ptr(stream)), "mxm_gemm_host")
+    return C
+
+
+def mxm_workspace_size(mode: int, m: int, k: int, n: int, slices: int = 7) -> int:
+    return int(load().mxm_workspace_size(int(mode), m, k, n, int(slices)))
+
+
+def mxm_set_workspace(ws=None):
+    """Use a caller-owned uint8 CUDA tensor as workspace (None: library-owned)."""
+    if ws is None:
+        _check(load().mxm_set_workspace(None, 0), "mxm_set_workspace")
+    else:
+        _check(load().mxm_set_workspace(ws.data_ptr(), ws.numel() * ws.element_size()),
+               "mxm_set_workspace")
+
+
+def problem_table(problems):
+    """Pack [(A, B, C), ...] (CUDA float64 tensors) into the int64 layout of
+    ``mxm_problem``: 6 int64 words per problem (A, B, C, m, k, n)."""
+    import torch
+    rows = []
+    for A, B, C in problems:
+        m, k, n = _operands(A, B, C)
+        rows.append([A.data_ptr(), B.data_ptr(), C.data_ptr(), m, k, n])
+    return torch.tensor(rows, dtype=torch.int64).reshape(-1, 6)
+
+
+def mxm_grouped_workspace_size(table_host, mode: int, slices: int = 7) -> int:
+    size = ctypes.c_size_t(0)
+    t = table_host.contiguous()
+    _check(load().mxm_grouped_workspace_size(t.shape[0], t.data_ptr(), int(mode), int(slices),
+                                             ctypes.byref(size)), "mxm_grouped_workspace_size")
+    return int(size.value)
+
+
+def mxm_grouped(table_device, mode: int, slices: int, ws, stream=None):
+    _check(load().mxm_grouped(table_device.shape[0], table_device.data_ptr(), int(mode),
+                              int(slices), ws.data_ptr(), ws.numel() * ws.element_size(),
+                              _stream_ptr(stream)), "mxm_grouped")
+
+
+def mxm_get_device_status(stream=None) -> int:
+    return int(load().mxm_get_device_status(_stream_ptr(stream)))
+
+
+def mxm_peak_probe(kind: int) -> float:
+    out = ctypes.c_double(0.0)
+    _check(load().mxm_peak_probe(int(kind), ctypes.byref(out)), "mxm_peak_probe")
+    return float(out.value)
+
+
+def mxm_debug_wait_timeout(limit_ns: int, stream=None):
+    _check(load().mxm_debug_wait_timeout(int(limit_ns), _stream_ptr(stream)),
+           "mxm_debug_wait_timeout")
+
+
+def mxm_profile_enable(on: bool = True):
+    _check(load().mxm_profile_enable(1 if on else 0), "mxm_profile_enable")
+
+
+def mxm_profile_read():
+    """(ms per phase [scale, split/pack, product], number of calls) since
+    the last read."""
+    ms = (ctypes.c_double * 3)()
+    calls = ctypes.c_int64(0)
+    _check(load().mxm_profile_read(ms, 3, ctypes.byref(calls)), "mxm_profile_read")
+    return [float(x) for x in ms], int(calls.value)
+
+
+def mxm_version() -> int:
+    return int(load().mxm_version())

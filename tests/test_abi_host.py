@@ -1,0 +1,79 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads, and
+exports every entry point include/mxm.h declares; argument errors are
+rejected before any device work.  Runs without a GPU."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+from paper_1211_1581_gb300 import build as mxm_build
+from paper_1211_1581_gb300 import mxm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mxm.h")
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and
+                                not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                                reason="needs nvcc to build libmxm.so")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*[A-Za-z_][\w\s\*]*?\b(mxm_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("mxm_f64", "mxm_f64_emul", "mxm_grouped", "mxm_gemm",
+                     "mxm_get_device_status", "mxm_workspace_size", "mxm_set_workspace"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(mxm_build.build())
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in mxm.h but not exported"
+    # and the binding knows every one of them
+    assert set(declared_functions()) == set(mxm.SIGNATURES)
+
+
+def test_status_strings_and_version():
+    assert mxm.mxm_version() >= 100
+    assert mxm.status_string(mxm.MXM_OK) == "MXM_OK"
+    assert mxm.status_string(mxm.MXM_ERR_TIMEOUT) == "MXM_ERR_TIMEOUT"
+    assert mxm.status_string(99) == "MXM_ERR_UNKNOWN"
+
+
+def test_argument_errors_need_no_device():
+    lib = mxm.load()
+    P = ctypes.c_void_p
+    fake = P(0x10000)  # never dereferenced: the checks fail first
+    assert lib.mxm_gemm(0, fake, fake, fake, -1, 4, 4, 0, None) == mxm.MXM_ERR_INVALID_ARG
+    assert lib.mxm_gemm(0, fake, fake, None, 4, 4, 4, 0, None) == mxm.MXM_ERR_INVALID_ARG
+    assert lib.mxm_gemm(1, fake, fake, fake, 4, 4, 4, 0, None) == mxm.MXM_ERR_UNSUPPORTED
+    assert lib.mxm_gemm(1, fake, fake, fake, 4, 4, 4, 13, None) == mxm.MXM_ERR_UNSUPPORTED
+    assert lib.mxm_gemm(9, fake, fake, fake, 4, 4, 4, 7, None) == mxm.MXM_ERR_UNSUPPORTED
+    assert lib.mxm_gemm(0, P(0x10004), fake, P(0x20000), 4, 4, 4, 0, None) == mxm.MXM_ERR_ALIGNMENT
+    # C overlapping A
+    assert lib.mxm_gemm(0, P(0x10000), P(0x90000), P(0x10008), 4, 4, 4, 0, None) == \
+        mxm.MXM_ERR_INVALID_ARG
+    # empty products are no-ops
+    assert lib.mxm_gemm(0, None, None, None, 0, 5, 5, 0, None) == mxm.MXM_OK
+    assert lib.mxm_f64(None, None, None, 5, 5, 0, None) == mxm.MXM_OK
+    assert lib.mxm_f64_emul(fake, fake, fake, 4, 4, 4, 0, None) == mxm.MXM_ERR_UNSUPPORTED
+
+
+def test_workspace_size_is_host_arithmetic():
+    # FP64: zero-padded 128x16 tiles of A and B
+    assert mxm.mxm_workspace_size(0, 128, 16, 128) == 2 * 128 * 16 * 8
+    assert mxm.mxm_workspace_size(0, 0, 16, 128) == 0
+    # emulated: exponents + S slices of 128x64 bf16 tiles of A and of B^T
+    ws = mxm.mxm_workspace_size(1, 256, 128, 128, 7)
+    tiles = 7 * (2 * 2 + 1 * 2)
+    assert ws >= tiles * 128 * 64 * 2
+    assert ws < tiles * 128 * 64 * 2 + 8 * 1024
+    assert mxm.mxm_workspace_size(1, 256, 128, 128, 0) == 0

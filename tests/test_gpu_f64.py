@@ -1,0 +1,106 @@
+"""Native FP64 path (mxm_f64) against the oracle, through the C ABI.
+
+Acceptance (per entry): |C - C_dot2| <= 2 k u (|A||B|), u = 2^-53; bit-exact
+on inputs whose products and partial sums are all exact (identity,
+permutation, small integers)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1211_1581_gb300 import inputs
+from helpers import assert_bitwise, assert_within_bound
+
+torch = pytest.importorskip("torch")
+from paper_1211_1581_gb300 import mxm  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def run_f64(A, B):
+    m, k = A.shape
+    n = B.shape[1]
+    C = torch.full((m, n), float("nan"), dtype=torch.float64, device="cuda")
+    mxm.mxm_f64(dev(A), dev(B), C)
+    torch.cuda.synchronize()
+    assert mxm.mxm_get_device_status() == mxm.MXM_OK
+    return C.cpu().numpy()
+
+
+SHAPES = [(1, 1, 1), (7, 13, 5), (17, 33, 15), (128, 16, 128), (129, 65, 131),
+          (255, 17, 129), (300, 200, 257), (256, 256, 256), (64, 1000, 40)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_f64_uniform_within_bound(shape):
+    m, k, n = shape
+    A, B = inputs.gemm_operands("uniform", m, k, n, seed=0, cfg=0)
+    C = run_f64(A, B)
+    assert_within_bound(C, oracle.gemm_dot2(A, B), oracle.gemm_abs(A, B), k, f"f64 {shape}")
+
+
+def test_f64_spread_within_bound():
+    m, k, n = 200, 300, 190
+    A, B = inputs.gemm_operands("spread", m, k, n, seed=0, cfg=2)
+    C = run_f64(A, B)
+    assert_within_bound(C, oracle.gemm_dot2(A, B), oracle.gemm_abs(A, B), k, "f64 spread")
+
+
+def test_f64_exact_cases_n256():
+    """The small exact-check cases at m = k = n = 256: identity, random
+    permutation, integer entries in [-8, 8] -- bit-exact."""
+    n = 256
+    A, B = inputs.gemm_operands("uniform", n, n, n, seed=0, cfg=0)
+    I = np.eye(n)
+    assert_bitwise(run_f64(I, B), B, "I.B")
+    assert_bitwise(run_f64(A, I), A, "A.I")
+    P = inputs.permutation_matrix(0, 7, n)
+    assert_bitwise(run_f64(P, B), B[inputs.permutation(0, 7, n)], "P.B")
+    Ai, Bi = inputs.gemm_operands("int8", n, n, n, seed=0, cfg=3)
+    ref = (Ai.astype(np.int64) @ Bi.astype(np.int64)).astype(np.float64)
+    assert_bitwise(run_f64(Ai, Bi), ref, "int [-8,8]")
+
+
+def test_f64_empty_and_zero_k():
+    A = np.zeros((5, 0))
+    B = np.zeros((0, 6))
+    C = run_f64(A, B)
+    assert np.array_equal(C, np.zeros((5, 6)))
+    # m == 0: nothing written, nothing launched
+    C = torch.zeros((0, 4), dtype=torch.float64, device="cuda")
+    mxm.mxm_f64(torch.zeros((0, 3), dtype=torch.float64, device="cuda"),
+                torch.zeros((3, 4), dtype=torch.float64, device="cuda"), C)
+
+
+def test_f64_deterministic():
+    A, B = inputs.gemm_operands("uniform", 333, 517, 291, seed=0, cfg=4)
+    assert_bitwise(run_f64(A, B), run_f64(A, B), "run to run")
+
+
+@pytest.mark.parametrize("n", [1024, 2048])
+def test_f64_sweep_sampled(n):
+    """The square sweep sizes: entries sampled by seed (every tile row and
+    column is hit) checked one by one against Dot2."""
+    A, B = inputs.gemm_operands("uniform", n, n, n, seed=0, cfg=1)
+    C = run_f64(A, B)
+    rng = np.random.default_rng(n)
+    ii = rng.integers(0, n, 600)
+    jj = rng.integers(0, n, 600)
+    ii[:8] = [0, n - 1, 0, n - 1, 127, 128, 129, n // 2]
+    jj[:8] = [0, n - 1, n - 1, 0, 128, 127, 255, n // 2]
+    d2, ab = oracle.entries_dot2_abs(A, B, ii, jj)
+    assert_within_bound(C[ii, jj], d2, ab, n, f"f64 n={n}")
+
+
+def test_f64_rectangular_sampled():
+    for (m, k, n) in [(4096, 256, 1024), (128, 16384, 128), (8192, 1024, 64)]:
+        A, B = inputs.gemm_operands("uniform", m, k, n, seed=0, cfg=3)
+        C = run_f64(A, B)
+        rng = np.random.default_rng(m + k + n)
+        ii = rng.integers(0, m, 300)
+        jj = rng.integers(0, n, 300)
+        d2, ab = oracle.entries_dot2_abs(A, B, ii, jj)
+        assert_within_bound(C[ii, jj], d2, ab, k, f"f64 {(m, k, n)}")

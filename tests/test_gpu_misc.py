@@ -1,0 +1,67 @@
+"""Device status word, the bounded-wait failure path, the host-buffer entry
+point and the peak probes."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1211_1581_gb300 import inputs
+from helpers import assert_bitwise
+
+torch = pytest.importorskip("torch")
+from paper_1211_1581_gb300 import mxm  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A wait on a barrier nothing completes gives up after its limit; the
+    kernel exits, the status word says MXM_ERR_TIMEOUT, and the next call
+    works."""
+    mxm.mxm_debug_wait_timeout(50_000_000)  # 50 ms
+    assert mxm.mxm_get_device_status() == mxm.MXM_ERR_TIMEOUT
+    assert mxm.mxm_get_device_status() == mxm.MXM_OK
+    A, B = inputs.gemm_operands("int8", 64, 64, 64, seed=0, cfg=3)
+    C = torch.empty((64, 64), dtype=torch.float64, device="cuda")
+    mxm.mxm_f64(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C)
+    ref = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    assert_bitwise(C.cpu().numpy(), ref, "after timeout")
+
+
+@pytest.mark.parametrize("mode,S", [(mxm.MODE_F64, 0), (mxm.MODE_EMUL_I8, 7)])
+def test_host_entry_point_matches_device(mode, S):
+    m, k, n = 190, 333, 270
+    A, B = inputs.gemm_operands("uniform", m, k, n, seed=0, cfg=6)
+    Ch = np.empty((m, n))
+    mxm.mxm_gemm_host(mode, A, B, Ch, slices=S)
+    Cd = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    mxm.mxm_gemm(mode, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), Cd, slices=S)
+    assert_bitwise(Ch, Cd.cpu().numpy(), "host vs device")
+    if mode != mxm.MODE_F64:
+        assert_bitwise(Ch, oracle.ozaki_gemm(A, B, S=S), "host vs oracle")
+
+
+def test_caller_workspace():
+    m, k, n = 200, 300, 100
+    A, B = inputs.gemm_operands("uniform", m, k, n, seed=0, cfg=7)
+    need = mxm.mxm_workspace_size(mxm.MODE_EMUL_I8, m, k, n, 7)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    try:
+        mxm.mxm_set_workspace(ws)
+        C = torch.empty((m, n), dtype=torch.float64, device="cuda")
+        mxm.mxm_f64_emul(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C, 7)
+        assert_bitwise(C.cpu().numpy(), oracle.ozaki_gemm(A, B, S=7), "caller workspace")
+        # too small for a bigger problem: rejected, nothing launched
+        with pytest.raises(mxm.MxmError) as ei:
+            A2 = torch.zeros((2000, 300), dtype=torch.float64, device="cuda")
+            C2 = torch.empty((2000, 100), dtype=torch.float64, device="cuda")
+            mxm.mxm_f64_emul(A2, torch.from_numpy(B).cuda(), C2, 7)
+        assert ei.value.status == mxm.MXM_ERR_WORKSPACE_TOO_SMALL
+    finally:
+        torch.cuda.synchronize()
+        mxm.mxm_set_workspace(None)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4])
+def test_peak_probes_run(kind):
+    v = mxm.mxm_peak_probe(kind)
+    assert v > 0.0
