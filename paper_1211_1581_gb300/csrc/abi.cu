@@ -143,6 +143,7 @@ size_t workspace_bytes(int mode, int64_t m, int64_t k, int64_t n, int slices) {
   if (m <= 0 || n <= 0 || k <= 0) return 0;
   if (mode == MXM_MODE_F64) return f64_workspace(f64_dims(m, k, n));
   if (emul_mode(mode)) return ozaki_layout(ozaki_dims(m, k, n, slices, mode_beta(mode))).total;
+  if (mode == MXM_MODE_BF16_F32ACC) return ozaki_layout(ozaki_dims(m, k, n, 1, 8)).total;
   return 0;
 }
 
@@ -174,6 +175,20 @@ mxm_status run_gemm(int mode, const double* A, const double* B, double* C, int64
     if (e == cudaSuccess)
       e = launch_ozaki_gemm(ws + L.aslices, ws + L.bslices, rowbits, colbits, C, d, status, s);
     profile_mark(ce, 3, s);
+  } else if (mode == MXM_MODE_BF16_F32ACC) {
+    const OzakiDims d = ozaki_dims(m, k, n, 1, 8);
+    const OzakiLayout L = ozaki_layout(d);
+    CallEvents* ce = profile_begin(s);
+    profile_mark(ce, 1, s);
+    profile_mark(ce, 2, s);
+    e = launch_bf16_gemm(A, B, C, d, ws + L.aslices, ws + L.bslices, status, s);
+    profile_mark(ce, 3, s);
+  } else if (mode == MXM_MODE_F32) {
+    CallEvents* ce = profile_begin(s);
+    profile_mark(ce, 1, s);
+    profile_mark(ce, 2, s);
+    e = launch_f32_gemm(A, B, C, m, k, n, s);
+    profile_mark(ce, 3, s);
   } else {
     return MXM_ERR_UNSUPPORTED;
   }
@@ -181,12 +196,21 @@ mxm_status run_gemm(int mode, const double* A, const double* B, double* C, int64
 }
 
 mxm_status check_mode(int mode, int slices) {
-  if (mode == MXM_MODE_F64) return MXM_OK;
+  if (mode == MXM_MODE_F64 || mode == MXM_MODE_F32 || mode == MXM_MODE_BF16_F32ACC) return MXM_OK;
   if (emul_mode(mode)) return (slices >= 1 && slices <= kOzMaxSlices) ? MXM_OK : MXM_ERR_UNSUPPORTED;
   return MXM_ERR_UNSUPPORTED;
 }
 
 }  // namespace
+
+// The current device's status word (nullptr if CUDA is unusable).
+int* device_status_word() {
+  std::lock_guard<std::mutex> lock(g_mutex);
+  DeviceState* ds = nullptr;
+  if (current_state(&ds) != MXM_OK) return nullptr;
+  return ds->status;
+}
+
 }  // namespace mxm
 
 using namespace mxm;

@@ -47,7 +47,7 @@ struct OzakiLayout {
   size_t rowbits, colbits, aslices, bslices, total;
 };
 
-inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 inline OzakiLayout ozaki_layout(const OzakiDims& d) {
   OzakiLayout L;
@@ -107,5 +107,78 @@ cudaError_t launch_f64_gemm(const uint8_t* ws, double* C, const F64Dims& d, int*
                             cudaStream_t s);
 
 cudaError_t launch_zero_fill(double* C, int64_t count, cudaStream_t s);
+
+// ---------------------------------------------------------------- grouped
+// Device plan of a grouped call, written by grouped_plan_kernel at the start
+// of the caller's workspace: a header, one record per problem (with prefix
+// sums of every per-problem count), then the data regions.
+struct GroupedProblem {
+  const double* A;
+  const double* B;
+  double* C;
+  int64_t m, k, n;
+  int64_t Mt, Nt, Kt;      // 128-row tiles of A, 128-column tiles of B, k-blocks
+  int64_t tile_begin;      // first C tile (prefix of Mt*Nt)
+  int64_t atile_begin;     // first A operand tile (prefix of Mt*Kt)
+  int64_t btile_begin;     // first B operand tile (prefix of Nt*Kt)
+  int64_t row_begin;       // first row maximum (prefix of m)
+  int64_t col_begin;       // first column maximum (prefix of n)
+  int64_t cgrp_begin;      // first 32-column group of B (prefix of ceil(n/32))
+};
+
+struct GroupedHeader {
+  int64_t valid;           // 0: workspace too small, every later kernel does nothing
+  int64_t count;           // problems
+  int64_t tiles, atiles, btiles, rows, cols, cgroups, max_kt;
+  int64_t off_rowbits, off_colbits, off_a, off_b, total;  // byte offsets in the workspace
+};
+
+constexpr size_t kGroupedRecordsOff = 256;
+
+__host__ __device__ inline size_t grouped_data_begin(int64_t count) {
+  return align_up(kGroupedRecordsOff + sizeof(GroupedProblem) * static_cast<size_t>(count), 1024);
+}
+
+// Byte offsets of the data regions from the totals (same on host and device).
+__host__ __device__ inline void grouped_offsets(GroupedHeader& h, int planes, size_t tile_bytes,
+                                                bool bits) {
+  size_t off = grouped_data_begin(h.count);
+  h.off_rowbits = off;
+  if (bits) off = align_up(off + 8 * static_cast<size_t>(h.rows > 0 ? h.rows : 1), 1024);
+  h.off_colbits = off;
+  if (bits) off = align_up(off + 8 * static_cast<size_t>(h.cols > 0 ? h.cols : 1), 1024);
+  h.off_a = off;
+  off = align_up(off + static_cast<size_t>(planes) * h.atiles * tile_bytes, 1024);
+  h.off_b = off;
+  off = align_up(off + static_cast<size_t>(planes) * h.btiles * tile_bytes, 1024);
+  h.total = off;
+}
+
+// Index of the problem owning item t of the prefix field `begin`: the last
+// record whose begin is <= t (problems with no items share their begin with
+// the next one and are skipped by "last").
+template <typename Rec>
+__device__ __forceinline__ int64_t grouped_find(const Rec* recs, int64_t count, int64_t t,
+                                                int64_t Rec::*begin) {
+  int64_t lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (recs[mid].*begin <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+cudaError_t launch_grouped_plan(const void* table, int64_t count, int emul, int S,
+                                size_t ws_bytes, uint8_t* ws, int* status, cudaStream_t s);
+cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t max_kt, int* status,
+                                 cudaStream_t s);
+cudaError_t launch_f64_grouped(uint8_t* ws, int* status, cudaStream_t s);
+int sm_count();
+
+// Comparison modes (not FP64-accurate).
+cudaError_t launch_bf16_gemm(const double* A, const double* B, double* C, const OzakiDims& d,
+                             uint8_t* aplane, uint8_t* bplane, int* status, cudaStream_t s);
+cudaError_t launch_f32_gemm(const double* A, const double* B, double* C, int64_t m, int64_t k,
+                            int64_t n, cudaStream_t s);
 
 }  // namespace mxm

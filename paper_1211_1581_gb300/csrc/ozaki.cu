@@ -109,39 +109,67 @@ __global__ void oz_colmax_kernel(const double* __restrict__ B, int64_t k, int64_
 // Digits of 8 consecutive k-values of one operand row, written as 16-byte
 // chunks of bf16 into the pre-swizzled tile image (chunk c of tile row r at
 // chunk position c ^ (r % 8)).
-__device__ __forceinline__ uint32_t bf16_bits_of_digit(int d) {
-  // |d| <= 255: exact in fp32 and in bf16 (at most 8 significant bits), so
-  // the bf16 pattern is the top half of the fp32 pattern.
-  return __float_as_uint(static_cast<float>(d)) >> 16;
+// bf16 bit pattern of the integer sign * mag, 0 < mag <= 255 (exact: at most
+// 8 significant bits), built from the bits: exponent floor(log2 mag).
+__device__ __forceinline__ uint32_t bf16_of_digit(uint32_t mag, uint32_t sign) {
+  if (mag == 0) return 0u;
+  const int ex = 31 - __clz(static_cast<int>(mag));
+  const uint32_t frac = (mag << (7 - ex)) & 0x7Fu;
+  return (sign << 15) | (static_cast<uint32_t>(127 + ex) << 7) | frac;
 }
 
-__device__ __forceinline__ void split_chunk_store(double (&r)[8], int S, int beta,
+// Digits of 8 consecutive values of one operand row, written as 16-byte
+// chunks of bf16 into the pre-swizzled tile image, one chunk per slice.
+//
+// The truncating split r = x 2^-e; t = r 2^beta; d = trunc(t); r = t - d is
+// exact in FP64 (every step is exact for |r| < 1), so digit s is simply the
+// s-th beta-bit field below the binary point of |x| 2^-e, with the sign of x.
+// With |x| = M 2^E2 (M the integer significand), digit s is bits
+// [beta (S - s) - sh, + beta) of M, sh = E2 - e + beta S: integer shifts, no
+// FP64 arithmetic (FP64 is the slow pipe on this GPU).  When x 2^-e is below
+// 2^-1022 every digit is 0 either way.
+__device__ __forceinline__ void split_chunk_store(const double (&x)[8], int e, int S, int beta,
                                                   uint8_t* dst, size_t slice_stride) {
-  const double scale = pow2_normal(beta);
-  for (int s = 0; s < S; ++s) {
+  uint64_t M[8];
+  int sh[8];
+  uint32_t sg[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x[j]));
+    const int be = static_cast<int>((b >> 52) & 0x7FF);
+    const uint64_t mant = b & 0x000FFFFFFFFFFFFFull;
+    M[j] = be ? (mant | 0x0010000000000000ull) : mant;
+    const int E2 = be ? be - 1075 : -1074;
+    sh[j] = E2 - e + beta * S;
+    sg[j] = static_cast<uint32_t>(b >> 63);
+  }
+  const uint64_t mask = (1ull << beta) - 1;
+  for (int s = 1; s <= S; ++s) {
     uint32_t packed[4];
 #pragma unroll
     for (int j = 0; j < 8; j += 2) {
-      double t0 = __dmul_rn(r[j], scale);
-      double t1 = __dmul_rn(r[j + 1], scale);
-      int d0 = __double2int_rz(t0);
-      int d1 = __double2int_rz(t1);
-      r[j] = __dsub_rn(t0, static_cast<double>(d0));
-      r[j + 1] = __dsub_rn(t1, static_cast<double>(d1));
-      packed[j >> 1] = bf16_bits_of_digit(d0) | (bf16_bits_of_digit(d1) << 16);
+      uint32_t bits2[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int p = beta * (S - s) - sh[j + h];  // lowest bit of the field in M
+        uint64_t dg;
+        if (p >= 0) dg = p < 64 ? (M[j + h] >> p) & mask : 0;
+        else dg = -p < 64 ? (M[j + h] << -p) & mask : 0;
+        bits2[h] = bf16_of_digit(static_cast<uint32_t>(dg), sg[j + h]);
+      }
+      packed[j >> 1] = bits2[0] | (bits2[1] << 16);
     }
-    *reinterpret_cast<uint4*>(dst + static_cast<size_t>(s) * slice_stride) =
+    *reinterpret_cast<uint4*>(dst + static_cast<size_t>(s - 1) * slice_stride) =
         make_uint4(packed[0], packed[1], packed[2], packed[3]);
   }
 }
 
-// A (m x k, row-major) -> A_s tiles [S][Mt][Kt] of 128 x 64 bf16.
-__global__ void __launch_bounds__(256) oz_split_a_kernel(
-    const double* __restrict__ A, int64_t m, int64_t k, const uint64_t* __restrict__ rowbits,
-    int S, int beta, int64_t Mt, int64_t Kt, uint8_t* __restrict__ aslices) {
-  const int64_t tk = blockIdx.x, tm = blockIdx.y;
-  const size_t slice_stride = static_cast<size_t>(Mt) * Kt * kOzTileBytes;
-  uint8_t* tile = aslices + (static_cast<size_t>(tm) * Kt + tk) * kOzTileBytes;
+// One 128 x 64 tile (tm, tk) of A (m x k, row-major) -> its S digit tiles,
+// `slice_stride` bytes apart.
+__device__ __forceinline__ void split_a_tile(const double* __restrict__ A, int64_t m, int64_t k,
+                                             const uint64_t* __restrict__ rowbits, int S,
+                                             int beta, int64_t tm, int64_t tk, uint8_t* tile,
+                                             size_t slice_stride) {
   for (int p = threadIdx.x; p < kOzTileRows * 8; p += blockDim.x) {
     const int c = p & 7, r = p >> 3;
     const int64_t row = tm * kOzTileRows + r;
@@ -150,22 +178,17 @@ __global__ void __launch_bounds__(256) oz_split_a_kernel(
     int e = 0;
     if (row < m) e = exponent_from_absbits(rowbits[row]);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      double x = (row < m && k0 + j < k) ? __ldg(A + row * k + k0 + j) : 0.0;
-      v[j] = ldexp_rn(x, -e);
-    }
-    split_chunk_store(v, S, beta, tile + r * 128 + ((c ^ (r & 7)) << 4), slice_stride);
+    for (int j = 0; j < 8; ++j) v[j] = (row < m && k0 + j < k) ? __ldg(A + row * k + k0 + j) : 0.0;
+    split_chunk_store(v, e, S, beta, tile + r * 128 + ((c ^ (r & 7)) << 4), slice_stride);
   }
 }
 
-// B (k x n, row-major) -> B_t tiles [S][Nt][Kt] of 128 (columns j) x 64 (k)
-// bf16, i.e. B transposed so that both MMA operands are K-major.
-__global__ void __launch_bounds__(256) oz_split_b_kernel(
-    const double* __restrict__ B, int64_t k, int64_t n, const uint64_t* __restrict__ colbits,
-    int S, int beta, int64_t Nt, int64_t Kt, uint8_t* __restrict__ bslices) {
-  const int64_t tk = blockIdx.x, tn = blockIdx.y;
-  const size_t slice_stride = static_cast<size_t>(Nt) * Kt * kOzTileBytes;
-  uint8_t* tile = bslices + (static_cast<size_t>(tn) * Kt + tk) * kOzTileBytes;
+// One tile (tn, tk) of B^T, i.e. 128 columns j x 64 k of B (k x n,
+// row-major) -> its S digit tiles: both MMA operands are K-major.
+__device__ __forceinline__ void split_b_tile(const double* __restrict__ B, int64_t k, int64_t n,
+                                             const uint64_t* __restrict__ colbits, int S,
+                                             int beta, int64_t tn, int64_t tk, uint8_t* tile,
+                                             size_t slice_stride) {
   for (int p = threadIdx.x; p < kOzTileRows * 8; p += blockDim.x) {
     const int c = p & 7, r = p >> 3;
     const int64_t col = tn * kOzTileRows + r;
@@ -174,11 +197,161 @@ __global__ void __launch_bounds__(256) oz_split_b_kernel(
     int f = 0;
     if (col < n) f = exponent_from_absbits(colbits[col]);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      double x = (col < n && k0 + j < k) ? __ldg(B + (k0 + j) * n + col) : 0.0;
-      v[j] = ldexp_rn(x, -f);
+    for (int j = 0; j < 8; ++j) v[j] = (col < n && k0 + j < k) ? __ldg(B + (k0 + j) * n + col) : 0.0;
+    split_chunk_store(v, f, S, beta, tile + r * 128 + ((c ^ (r & 7)) << 4), slice_stride);
+  }
+}
+
+// A -> A_s tiles [S][Mt][Kt].
+__global__ void __launch_bounds__(256) oz_split_a_kernel(
+    const double* __restrict__ A, int64_t m, int64_t k, const uint64_t* __restrict__ rowbits,
+    int S, int beta, int64_t Mt, int64_t Kt, uint8_t* __restrict__ aslices) {
+  const int64_t tk = blockIdx.x, tm = blockIdx.y;
+  split_a_tile(A, m, k, rowbits, S, beta, tm, tk,
+               aslices + (static_cast<size_t>(tm) * Kt + tk) * kOzTileBytes,
+               static_cast<size_t>(Mt) * Kt * kOzTileBytes);
+}
+
+// B -> B_t tiles [S][Nt][Kt].
+__global__ void __launch_bounds__(256) oz_split_b_kernel(
+    const double* __restrict__ B, int64_t k, int64_t n, const uint64_t* __restrict__ colbits,
+    int S, int beta, int64_t Nt, int64_t Kt, uint8_t* __restrict__ bslices) {
+  const int64_t tk = blockIdx.x, tn = blockIdx.y;
+  split_b_tile(B, k, n, colbits, S, beta, tn, tk,
+               bslices + (static_cast<size_t>(tn) * Kt + tk) * kOzTileBytes,
+               static_cast<size_t>(Nt) * Kt * kOzTileBytes);
+}
+
+// ---------------------------------------------------------------- grouped steps 1-2
+// The same scale and split over every problem of a grouped call, items
+// located through the device plan.
+__global__ void oz_grouped_rowmax_kernel(const uint8_t* __restrict__ ws, int* __restrict__ status) {
+  const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
+  if (!hdr->valid) return;
+  const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
+  uint64_t* rowbits = reinterpret_cast<uint64_t*>(const_cast<uint8_t*>(ws) + hdr->off_rowbits);
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+       r < hdr->rows; r += warps) {
+    const GroupedProblem& p = recs[grouped_find(recs, hdr->count, r, &GroupedProblem::row_begin)];
+    const double* a = p.A + (r - p.row_begin) * p.k;
+    uint64_t mx = 0;
+    for (int64_t l = lane; l < p.k; l += 32) {
+      const uint64_t b = static_cast<uint64_t>(__double_as_longlong(__ldg(a + l))) & kAbsMask;
+      mx = mx > b ? mx : b;
     }
-    split_chunk_store(v, S, beta, tile + r * 128 + ((c ^ (r & 7)) << 4), slice_stride);
+    mx = warp_max_u64(mx);
+    if (lane == 0) {
+      rowbits[r] = mx;
+      if (mx >= kInfBits) atomicOr(status, kStatusNonFinite);
+    }
+  }
+}
+
+__global__ void oz_grouped_colmax_kernel(const uint8_t* __restrict__ ws, int* __restrict__ status) {
+  const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
+  if (!hdr->valid) return;
+  const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
+  uint64_t* colbits = reinterpret_cast<uint64_t*>(const_cast<uint8_t*>(ws) + hdr->off_colbits);
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t gi = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+       gi < hdr->cgroups; gi += warps) {
+    const GroupedProblem& p =
+        recs[grouped_find(recs, hdr->count, gi, &GroupedProblem::cgrp_begin)];
+    const int64_t col = (gi - p.cgrp_begin) * 32 + lane;
+    if (col >= p.n) continue;
+    uint64_t mx = 0;
+    for (int64_t l = 0; l < p.k; ++l) {
+      const uint64_t b = static_cast<uint64_t>(__double_as_longlong(__ldg(p.B + l * p.n + col))) & kAbsMask;
+      mx = mx > b ? mx : b;
+    }
+    colbits[p.col_begin + col] = mx;
+    if (mx >= kInfBits) atomicOr(status, kStatusNonFinite);
+  }
+}
+
+__global__ void __launch_bounds__(256) oz_grouped_split_kernel(uint8_t* __restrict__ ws, int S,
+                                                               int beta) {
+  const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
+  if (!hdr->valid) return;
+  const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
+  const uint64_t* rowbits = reinterpret_cast<const uint64_t*>(ws + hdr->off_rowbits);
+  const uint64_t* colbits = reinterpret_cast<const uint64_t*>(ws + hdr->off_colbits);
+  const int64_t na = hdr->atiles, nb = hdr->btiles;
+  for (int64_t t = blockIdx.x; t < na + nb; t += gridDim.x) {
+    if (t < na) {
+      const GroupedProblem& p = recs[grouped_find(recs, hdr->count, t, &GroupedProblem::atile_begin)];
+      const int64_t local = t - p.atile_begin;
+      split_a_tile(p.A, p.m, p.k, rowbits + p.row_begin, S, beta, local / p.Kt, local % p.Kt,
+                   ws + hdr->off_a + static_cast<size_t>(t) * kOzTileBytes,
+                   static_cast<size_t>(na) * kOzTileBytes);
+    } else {
+      const int64_t tb = t - na;
+      const GroupedProblem& p = recs[grouped_find(recs, hdr->count, tb, &GroupedProblem::btile_begin)];
+      const int64_t local = tb - p.btile_begin;
+      split_b_tile(p.B, p.k, p.n, colbits + p.col_begin, S, beta, local / p.Kt, local % p.Kt,
+                   ws + hdr->off_b + static_cast<size_t>(tb) * kOzTileBytes,
+                   static_cast<size_t>(nb) * kOzTileBytes);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- BF16 mode
+// Comparison mode (not part of the Ozaki method): x rounded to the nearest
+// bf16 (ties to even), computed on the binary64 bit pattern.
+__device__ __forceinline__ uint32_t bf16_rne_bits(double x) {
+  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
+  const uint32_t sign = static_cast<uint32_t>(b >> 48) & 0x8000u;
+  const uint64_t ab = b & kAbsMask;
+  if (ab > kInfBits) return sign | 0x7FC0u;   // nan
+  if (ab == kInfBits) return sign | 0x7F80u;  // inf
+  const int be = static_cast<int>(ab >> 52);
+  if (be == 0) return sign;                   // |x| < 2^-1022: rounds to zero in bf16
+  const int E = be - 1023;                    // |x| in [2^E, 2^{E+1})
+  if (E >= 128) return sign | 0x7F80u;
+  const int Eq = E < -126 ? -126 : E;         // bf16 spacing 2^{Eq-7}
+  const uint64_t sig = (ab & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;  // 2^{E-52} units
+  const int shift = 45 + (Eq - E);
+  if (shift >= 63) return sign;
+  uint64_t q = sig >> shift;
+  const uint64_t rem = sig & ((1ull << shift) - 1);
+  const uint64_t half = 1ull << (shift - 1);
+  if (rem > half || (rem == half && (q & 1))) ++q;
+  uint32_t bits;
+  if (E < -126) bits = static_cast<uint32_t>(q);  // subnormal (q = 128 is the least normal)
+  else bits = (static_cast<uint32_t>(Eq + 127) << 7) + static_cast<uint32_t>(q - 128);
+  if (bits >= 0x7F80u) bits = 0x7F80u;
+  return sign | bits;
+}
+
+// A (m x k) or B (k x n, transposed) -> one plane of 128 x 64 bf16 tiles,
+// same layout as a slice plane.
+__global__ void __launch_bounds__(256) bf16_tiles_kernel(const double* __restrict__ X,
+                                                         int64_t rows, int64_t cols, int trans,
+                                                         int64_t Kt, uint8_t* __restrict__ out) {
+  const int64_t tk = blockIdx.x, tr = blockIdx.y;
+  uint8_t* tile = out + (static_cast<size_t>(tr) * Kt + tk) * kOzTileBytes;
+  for (int p = threadIdx.x; p < kOzTileRows * 8; p += blockDim.x) {
+    const int c = p & 7, r = p >> 3;
+    const int64_t row = tr * kOzTileRows + r;   // row of A, or column of B
+    const int64_t k0 = tk * kOzTileK + c * 8;
+    uint32_t packed[4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      double x0 = 0.0, x1 = 0.0;
+      if (!trans) {
+        if (row < rows && k0 + j < cols) x0 = __ldg(X + row * cols + k0 + j);
+        if (row < rows && k0 + j + 1 < cols) x1 = __ldg(X + row * cols + k0 + j + 1);
+      } else {  // X is k x n: element (k0 + j, row)
+        if (row < cols && k0 + j < rows) x0 = __ldg(X + (k0 + j) * cols + row);
+        if (row < cols && k0 + j + 1 < rows) x1 = __ldg(X + (k0 + j + 1) * cols + row);
+      }
+      packed[j >> 1] = bf16_rne_bits(x0) | (bf16_rne_bits(x1) << 16);
+    }
+    *reinterpret_cast<uint4*>(tile + r * 128 + ((c ^ (r & 7)) << 4)) =
+        make_uint4(packed[0], packed[1], packed[2], packed[3]);
   }
 }
 
@@ -207,8 +380,8 @@ constexpr size_t kGemmSmemBytes = sizeof(GemmSmem) + 1024;
 
 __device__ __forceinline__ void tile_coords(int64_t tile, int64_t Mt, int64_t Nt, int64_t& tm,
                                             int64_t& tn) {
-  // groups of 8 tile-rows, column-major inside a group: neighbouring CTAs
-  // share A tiles and B tiles in L2
+  // groups of 8 tile-rows, column-major inside a group: CTAs working at the
+  // same time share A tiles and B tiles in L2
   constexpr int64_t G = 8;
   const int64_t per_group = G * Nt;
   const int64_t grp = tile / per_group;
@@ -219,20 +392,95 @@ __device__ __forceinline__ void tile_coords(int64_t tile, int64_t Mt, int64_t Nt
   tn = in / gsz;
 }
 
-template <typename Acc>
-__global__ void __launch_bounds__(kThreads, 1) oz_gemm_kernel(
-    const uint8_t* __restrict__ aslices, const uint8_t* __restrict__ bslices,
-    const uint64_t* __restrict__ rowbits, const uint64_t* __restrict__ colbits,
-    double* __restrict__ C, int64_t m, int64_t n, int64_t Mt, int64_t Nt, int64_t Kt, int S,
-    int beta, int window, int* __restrict__ status) {
+// One 128 x 128 tile of C and where its operand tiles live.
+struct OzTile {
+  const uint8_t* a;          // slice 1 of A tile-row tm, k-block 0
+  const uint8_t* b;          // slice 1 of B^T tile-row tn, k-block 0
+  size_t a_slice, b_slice;   // bytes from one slice plane to the next
+  int64_t Kt;                // 64-wide k-blocks
+  const uint64_t* rowbits;   // |A| row maxima of this problem
+  const uint64_t* colbits;   // |B| column maxima of this problem
+  double* C;
+  int64_t m, n;              // C is m x n, row-major
+  int64_t row0, col0;        // origin of the tile in C
+};
+
+// Tiles of one product.
+struct OzSingle {
+  const uint8_t* aslices;
+  const uint8_t* bslices;
+  const uint64_t* rowbits;
+  const uint64_t* colbits;
+  double* C;
+  int64_t m, n, Mt, Nt, Kt;
+  __device__ __forceinline__ int64_t count() const { return Mt * Nt; }
+  __device__ __forceinline__ OzTile tile(int64_t t) const {
+    int64_t tm, tn;
+    tile_coords(t, Mt, Nt, tm, tn);
+    OzTile j;
+    j.a_slice = static_cast<size_t>(Mt) * Kt * kOzTileBytes;
+    j.b_slice = static_cast<size_t>(Nt) * Kt * kOzTileBytes;
+    j.a = aslices + static_cast<size_t>(tm) * Kt * kOzTileBytes;
+    j.b = bslices + static_cast<size_t>(tn) * Kt * kOzTileBytes;
+    j.Kt = Kt;
+    j.rowbits = rowbits;
+    j.colbits = colbits;
+    j.C = C;
+    j.m = m;
+    j.n = n;
+    j.row0 = tm * kOzTileRows;
+    j.col0 = tn * kOzTileRows;
+    return j;
+  }
+};
+
+// Tiles of a grouped call: the device plan (grouped_plan_kernel) lists every
+// problem with prefix sums of its tile counts; tile t belongs to the last
+// problem whose first tile is <= t.
+struct OzGrouped {
+  const GroupedHeader* hdr;
+  const GroupedProblem* recs;
+  const uint8_t* ws;
+  __device__ __forceinline__ int64_t count() const { return hdr->valid ? hdr->tiles : 0; }
+  __device__ __forceinline__ OzTile tile(int64_t t) const {
+    const int64_t p = grouped_find(recs, hdr->count, t, &GroupedProblem::tile_begin);
+    const GroupedProblem& r = recs[p];
+    const int64_t local = t - r.tile_begin;
+    const int64_t tm = local / r.Nt, tn = local - (local / r.Nt) * r.Nt;
+    OzTile j;
+    j.a_slice = static_cast<size_t>(hdr->atiles) * kOzTileBytes;
+    j.b_slice = static_cast<size_t>(hdr->btiles) * kOzTileBytes;
+    j.a = ws + hdr->off_a + static_cast<size_t>(r.atile_begin + tm * r.Kt) * kOzTileBytes;
+    j.b = ws + hdr->off_b + static_cast<size_t>(r.btile_begin + tn * r.Kt) * kOzTileBytes;
+    j.Kt = r.Kt;
+    j.rowbits = reinterpret_cast<const uint64_t*>(ws + hdr->off_rowbits) + r.row_begin;
+    j.colbits = reinterpret_cast<const uint64_t*>(ws + hdr->off_colbits) + r.col_begin;
+    j.C = r.C;
+    j.m = r.m;
+    j.n = r.n;
+    j.row0 = tm * kOzTileRows;
+    j.col0 = tn * kOzTileRows;
+    return j;
+  }
+};
+
+// Persistent slice GEMM: every CTA walks tiles blockIdx.x, +gridDim.x, ...;
+// the three roles walk the same sequence and keep their pipeline state
+// (stage ring, accumulator double buffer) from one tile to the next, so the
+// epilogue of one tile overlaps the main loop of the next.
+//
+// Acc: type of the exact per-diagonal running sums (int or long long).
+// kFloat (BF16 comparison mode only): one slice of bf16-rounded values, the
+// FP32 accumulator covers all of k in one window and is converted to FP64
+// without scaling.
+template <typename Acc, bool kFloat, typename Tiles>
+__global__ void __launch_bounds__(kThreads, 1)
+    oz_gemm_kernel(const Tiles tiles, int S, int beta, int window, int* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   GemmSmem& sm = *reinterpret_cast<GemmSmem*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-
-  int64_t tm, tn;
-  tile_coords(blockIdx.x, Mt, Nt, tm, tn);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -255,11 +503,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm_kernel(
   tc_fence_after();
   const uint32_t tmem = sm.tmem_base;
   volatile int* abort_flag = &sm.abort_flag;
-
-  const size_t a_slice = static_cast<size_t>(Mt) * Kt * kOzTileBytes;
-  const size_t b_slice = static_cast<size_t>(Nt) * Kt * kOzTileBytes;
-  const uint8_t* a_rowtiles = aslices + static_cast<size_t>(tm) * Kt * kOzTileBytes;
-  const uint8_t* b_coltiles = bslices + static_cast<size_t>(tn) * Kt * kOzTileBytes;
+  const int64_t ntiles = tiles.count();
 
   if (warp == 0) {
     // ------------------------------------------------ producer (bulk copies)
@@ -267,22 +511,24 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm_kernel(
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int g = S + 1; g >= 2 && ok; --g) {
-        for (int64_t kb = 0; kb < Kt && ok; ++kb) {
-          for (int s = 1; s <= g - 1; ++s) {
-            const int t = g - s;
-            if (!mbar_wait_bounded(&sm.empty[stage], phase ^ 1u, abort_flag, status)) {
-              ok = false;
-              break;
-            }
-            mbar_arrive_expect_tx(&sm.full[stage], 2 * kOzTileBytes);
-            bulk_g2s(sm.a[stage], a_rowtiles + (s - 1) * a_slice + kb * kOzTileBytes,
-                     kOzTileBytes, &sm.full[stage]);
-            bulk_g2s(sm.b[stage], b_coltiles + (t - 1) * b_slice + kb * kOzTileBytes,
-                     kOzTileBytes, &sm.full[stage]);
-            if (++stage == kStages) {
-              stage = 0;
-              phase ^= 1u;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const OzTile j = tiles.tile(t);
+        for (int g = S + 1; g >= 2 && ok; --g) {
+          for (int64_t kb = 0; kb < j.Kt && ok; ++kb) {
+            for (int s = 1; s <= g - 1; ++s) {
+              if (!mbar_wait_bounded(&sm.empty[stage], phase ^ 1u, abort_flag, status)) {
+                ok = false;
+                break;
+              }
+              mbar_arrive_expect_tx(&sm.full[stage], 2 * kOzTileBytes);
+              bulk_g2s(sm.a[stage], j.a + (s - 1) * j.a_slice + kb * kOzTileBytes, kOzTileBytes,
+                       &sm.full[stage]);
+              bulk_g2s(sm.b[stage], j.b + (g - s - 1) * j.b_slice + kb * kOzTileBytes,
+                       kOzTileBytes, &sm.full[stage]);
+              if (++stage == kStages) {
+                stage = 0;
+                phase ^= 1u;
+              }
             }
           }
         }
@@ -308,48 +554,51 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm_kernel(
       bool acquired = false;
       int cnt = 0;
       bool ok = true;
-      for (int g = S + 1; g >= 2 && ok; --g) {
-        const int64_t nmma = Kt * kMmaPerStage * (g - 1);
-        int64_t done = 0;
-        for (int64_t kb = 0; kb < Kt && ok; ++kb) {
-          for (int s = 1; s <= g - 1; ++s) {
-            if (!mbar_wait_bounded(&sm.full[stage], phase, abort_flag, status)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t a_addr = smem_u32(sm.a[stage]);
-            const uint32_t b_addr = smem_u32(sm.b[stage]);
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int64_t Kt = tiles.tile(t).Kt;
+        for (int g = S + 1; g >= 2 && ok; --g) {
+          const int64_t nmma = Kt * kMmaPerStage * (g - 1);
+          int64_t done = 0;
+          for (int64_t kb = 0; kb < Kt && ok; ++kb) {
+            for (int s = 1; s <= g - 1; ++s) {
+              if (!mbar_wait_bounded(&sm.full[stage], phase, abort_flag, status)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t a_addr = smem_u32(sm.a[stage]);
+              const uint32_t b_addr = smem_u32(sm.b[stage]);
 #pragma unroll
-            for (int kk = 0; kk < kMmaPerStage; ++kk) {
-              if (!acquired) {
-                const uint32_t u = buf ? uses1 : uses0;
-                if (u > 0 &&
-                    !mbar_wait_bounded(&sm.accempty[buf], (u - 1u) & 1u, abort_flag, status)) {
-                  ok = false;
-                  break;
+              for (int kk = 0; kk < kMmaPerStage; ++kk) {
+                if (!acquired) {
+                  const uint32_t u = buf ? uses1 : uses0;
+                  if (u > 0 &&
+                      !mbar_wait_bounded(&sm.accempty[buf], (u - 1u) & 1u, abort_flag, status)) {
+                    ok = false;
+                    break;
+                  }
+                  tc_fence_after();
+                  if (buf) ++uses1; else ++uses0;
+                  acquired = true;
+                  cnt = 0;
                 }
-                tc_fence_after();
-                if (buf) ++uses1; else ++uses0;
-                acquired = true;
-                cnt = 0;
+                mma_bf16_ss(tmem + static_cast<uint32_t>(buf * kBN),
+                            sw128_kmajor_desc(a_addr + kk * 32),
+                            sw128_kmajor_desc(b_addr + kk * 32), idesc, cnt > 0 ? 1u : 0u);
+                ++cnt;
+                ++done;
+                if (cnt == window || done == nmma) {
+                  mma_commit(&sm.accfull[buf]);
+                  buf ^= 1;
+                  acquired = false;
+                }
               }
-              mma_bf16_ss(tmem + static_cast<uint32_t>(buf * kBN),
-                          sw128_kmajor_desc(a_addr + kk * 32), sw128_kmajor_desc(b_addr + kk * 32),
-                          idesc, cnt > 0 ? 1u : 0u);
-              ++cnt;
-              ++done;
-              if (cnt == window || done == nmma) {
-                mma_commit(&sm.accfull[buf]);
-                buf ^= 1;
-                acquired = false;
+              mma_commit(&sm.empty[stage]);
+              if (!ok) break;
+              if (++stage == kStages) {
+                stage = 0;
+                phase ^= 1u;
               }
-            }
-            mma_commit(&sm.empty[stage]);
-            if (!ok) break;
-            if (++stage == kStages) {
-              stage = 0;
-              phase ^= 1u;
             }
           }
         }
@@ -367,78 +616,91 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm_kernel(
     uint32_t fulls0 = 0u, fulls1 = 0u;  // windows drained from accumulator 0 / 1
     bool ok = true;
     Acc D[64];
-    for (int g = S + 1; g >= 2 && ok; --g) {
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const OzTile j = tiles.tile(t);
+      for (int g = S + 1; g >= 2 && ok; --g) {
 #pragma unroll
-      for (int i = 0; i < 64; ++i) D[i] = 0;
-      const int64_t nmma = Kt * kMmaPerStage * (g - 1);
-      const int64_t nwin = (nmma + window - 1) / window;
-      for (int64_t w = 0; w < nwin; ++w) {
-        if (!mbar_wait_bounded(&sm.accfull[buf], (buf ? fulls1 : fulls0) & 1u, abort_flag,
-                               status)) {
-          ok = false;
-          break;
-        }
-        if (buf) ++fulls1; else ++fulls0;
-        tc_fence_after();
-        const uint32_t t_win = t_lane + static_cast<uint32_t>(buf * kBN + half * 64);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          uint32_t r[32];
-          tmem_ld32(t_win + h * 32, r);
-          tmem_wait_ld();
-#pragma unroll
-          for (int i = 0; i < 32; ++i) D[h * 32 + i] += static_cast<Acc>(__float2int_rz(__uint_as_float(r[i])));
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sm.accempty[buf]);
-        buf ^= 1;
-      }
-      if (!ok) break;
-      // fold D_g into the FP64 running sum: acc = acc + D_g * 2^{-beta g}
-      const double wgt = pow2_normal(-beta * g);
-      const bool first = (g == S + 1);
-      const bool last = (g == 2);
-      const int64_t row = tm * kOzTileRows + row_in_tile;
-      int er = 0;
-      if (last && row < m) er = exponent_from_absbits(rowbits[row]);
-#pragma unroll
-      for (int ch = 0; ch < 8; ++ch) {
-        uint32_t r[16];
-        if (!first) {
-          tmem_ld16(t_acc + ch * 16, r);
-          tmem_wait_ld();
-        }
-        double v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const double term = __dmul_rn(static_cast<double>(D[ch * 8 + i]), wgt);  // exact
-          if (first) {
-            v[i] = term;
-          } else {
-            const double prev =
-                __hiloint2double(static_cast<int>(r[2 * i + 1]), static_cast<int>(r[2 * i]));
-            v[i] = __dadd_rn(prev, term);
+        for (int i = 0; i < 64; ++i) D[i] = 0;
+        const int64_t nmma = j.Kt * kMmaPerStage * (g - 1);
+        const int64_t nwin = (nmma + window - 1) / window;
+        for (int64_t w = 0; w < nwin; ++w) {
+          if (!mbar_wait_bounded(&sm.accfull[buf], (buf ? fulls1 : fulls0) & 1u, abort_flag,
+                                 status)) {
+            ok = false;
+            break;
           }
-        }
-        if (last) {
-          if (row < m) {
-            const int64_t col0 = tn * kBN + half * 64 + ch * 8;
-            double* crow = C + row * n;
+          if (buf) ++fulls1; else ++fulls0;
+          tc_fence_after();
+          const uint32_t t_win = t_lane + static_cast<uint32_t>(buf * kBN + half * 64);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const int64_t col = col0 + i;
-              if (col < n) crow[col] = ldexp_rn(v[i], er + exponent_from_absbits(colbits[col]));
+          for (int h = 0; h < 2; ++h) {
+            uint32_t r[32];
+            tmem_ld32(t_win + h * 32, r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              if constexpr (kFloat)
+                D[h * 32 + i] += static_cast<Acc>(__uint_as_float(r[i]));
+              else
+                D[h * 32 + i] += static_cast<Acc>(__float2int_rz(__uint_as_float(r[i])));
             }
           }
-        } else {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sm.accempty[buf]);
+          buf ^= 1;
+        }
+        if (!ok) break;
+        // fold D_g into the FP64 running sum: acc = acc + D_g * 2^{-beta g}
+        const double wgt = kFloat ? 1.0 : pow2_normal(-beta * g);
+        const bool first = (g == S + 1);
+        const bool last = (g == 2);
+        const int64_t row = j.row0 + row_in_tile;
+        int er = 0;
+        if (!kFloat && last && row < j.m) er = exponent_from_absbits(j.rowbits[row]);
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+          uint32_t r[16];
+          if (!first) {
+            tmem_ld16(t_acc + ch * 16, r);
+            tmem_wait_ld();
+          }
+          double v[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            r[2 * i] = static_cast<uint32_t>(__double2loint(v[i]));
-            r[2 * i + 1] = static_cast<uint32_t>(__double2hiint(v[i]));
+            const double term = __dmul_rn(static_cast<double>(D[ch * 8 + i]), wgt);  // exact
+            if (first) {
+              v[i] = term;
+            } else {
+              const double prev =
+                  __hiloint2double(static_cast<int>(r[2 * i + 1]), static_cast<int>(r[2 * i]));
+              v[i] = __dadd_rn(prev, term);
+            }
           }
-          tmem_st16(t_acc + ch * 16, r);
-          tmem_wait_st();
+          if (last) {
+            if (row < j.m) {
+              const int64_t col0 = j.col0 + half * 64 + ch * 8;
+              double* crow = j.C + row * j.n;
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const int64_t col = col0 + i;
+                if (col < j.n) {
+                  if constexpr (kFloat)
+                    crow[col] = v[i];
+                  else
+                    crow[col] = ldexp_rn(v[i], er + exponent_from_absbits(j.colbits[col]));
+                }
+              }
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              r[2 * i] = static_cast<uint32_t>(__double2loint(v[i]));
+              r[2 * i + 1] = static_cast<uint32_t>(__double2hiint(v[i]));
+            }
+            tmem_st16(t_acc + ch * 16, r);
+            tmem_wait_st();
+          }
         }
       }
     }
@@ -497,33 +759,80 @@ cudaError_t launch_ozaki_split(const double* A, const double* B, const OzakiDims
   return cudaGetLastError();
 }
 
+int g_sm_count = 0;
+
+int sm_count() {
+  if (g_sm_count == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sm_count <= 0) g_sm_count = 1;
+  }
+  return g_sm_count;
+}
+
+template <typename Acc, bool kFloat, typename Tiles>
+static cudaError_t launch_oz_gemm_t(const Tiles& tiles, int64_t grid, int S, int beta,
+                                    int window, int* status, cudaStream_t s) {
+  if (grid <= 0) return cudaSuccess;
+  auto kern = oz_gemm_kernel<Acc, kFloat, Tiles>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kGemmSmemBytes));
+  if (e != cudaSuccess) return e;
+  kern<<<static_cast<unsigned>(grid), kThreads, kGemmSmemBytes, s>>>(tiles, S, beta, window,
+                                                                      status);
+  return cudaGetLastError();
+}
+
+static bool narrow_sums(int S, int beta, int64_t Kt) {
+  // int32 running sums suffice while S (2^beta - 1)^2 * 64 Kt < 2^31
+  const long long dmax = (1ll << beta) - 1;
+  return static_cast<double>(S) * dmax * dmax * 64.0 * Kt < 2147483647.0;
+}
+
 cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
                               const uint64_t* rowbits, const uint64_t* colbits, double* C,
                               const OzakiDims& d, int* status, cudaStream_t s) {
   if (d.Mt == 0 || d.Nt == 0) return cudaSuccess;
   const int window = ozaki_window_mmas(d.beta);
-  // int32 running sums suffice while (S)(2^beta - 1)^2 * 64 Kt < 2^31
-  const long long dmax = (1ll << d.beta) - 1;
-  const bool narrow = static_cast<double>(d.S) * dmax * dmax * 64.0 * d.Kt < 2147483647.0;
-  const int64_t tiles = d.Mt * d.Nt;
-  cudaError_t e;
-  if (narrow) {
-    e = cudaFuncSetAttribute(oz_gemm_kernel<int>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kGemmSmemBytes));
-    if (e != cudaSuccess) return e;
-    oz_gemm_kernel<int><<<static_cast<unsigned>(tiles), kThreads, kGemmSmemBytes, s>>>(
-        aslices, bslices, rowbits, colbits, C, d.m, d.n, d.Mt, d.Nt, d.Kt, d.S, d.beta, window,
-        status);
-  } else {
-    e = cudaFuncSetAttribute(oz_gemm_kernel<long long>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kGemmSmemBytes));
-    if (e != cudaSuccess) return e;
-    oz_gemm_kernel<long long><<<static_cast<unsigned>(tiles), kThreads, kGemmSmemBytes, s>>>(
-        aslices, bslices, rowbits, colbits, C, d.m, d.n, d.Mt, d.Nt, d.Kt, d.S, d.beta, window,
-        status);
-  }
-  return cudaGetLastError();
+  OzSingle tiles{aslices, bslices, rowbits, colbits, C, d.m, d.n, d.Mt, d.Nt, d.Kt};
+  const int64_t count = d.Mt * d.Nt;
+  const int64_t grid = count < sm_count() ? count : sm_count();
+  if (narrow_sums(d.S, d.beta, d.Kt))
+    return launch_oz_gemm_t<int, false>(tiles, grid, d.S, d.beta, window, status, s);
+  return launch_oz_gemm_t<long long, false>(tiles, grid, d.S, d.beta, window, status, s);
+}
+
+cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t /*max_kt*/, int* status,
+                                 cudaStream_t s) {
+  const int sms = sm_count();
+  oz_grouped_rowmax_kernel<<<sms * 4, 256, 0, s>>>(ws, status);
+  oz_grouped_colmax_kernel<<<sms * 4, 256, 0, s>>>(ws, status);
+  oz_grouped_split_kernel<<<sms * 8, 256, 0, s>>>(ws, S, beta);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
+  const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
+  OzGrouped tiles{hdr, recs, ws};
+  // the host does not see the table: 64-bit running sums are safe for any k
+  return launch_oz_gemm_t<long long, false>(tiles, sms, S, beta, ozaki_window_mmas(beta), status,
+                                            s);
+}
+
+cudaError_t launch_bf16_gemm(const double* A, const double* B, double* C, const OzakiDims& d,
+                             uint8_t* aplane, uint8_t* bplane, int* status, cudaStream_t s) {
+  if (d.Mt == 0 || d.Nt == 0 || d.Kt == 0) return cudaSuccess;
+  bf16_tiles_kernel<<<dim3(static_cast<unsigned>(d.Kt), static_cast<unsigned>(d.Mt)), 256, 0, s>>>(
+      A, d.m, d.k, 0, d.Kt, aplane);
+  bf16_tiles_kernel<<<dim3(static_cast<unsigned>(d.Kt), static_cast<unsigned>(d.Nt)), 256, 0, s>>>(
+      B, d.k, d.n, 1, d.Kt, bplane);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  OzSingle tiles{aplane, bplane, nullptr, nullptr, C, d.m, d.n, d.Mt, d.Nt, d.Kt};
+  const int64_t count = d.Mt * d.Nt;
+  const int64_t grid = count < sm_count() ? count : sm_count();
+  const int whole_k = static_cast<int>(d.Kt * kMmaPerStage);
+  return launch_oz_gemm_t<float, true>(tiles, grid, 1, 8, whole_k, status, s);
 }
 
 cudaError_t launch_zero_fill(double* C, int64_t count, cudaStream_t s) {

@@ -202,17 +202,3 @@ extern "C" mxm_status mxm_peak_probe(int kind, double* tflops) {
   if (st == MXM_OK) *tflops = ops / (double(ms) * 1e-3) / 1e12;
   return st;
 }
-
-extern "C" mxm_status mxm_grouped_workspace_size(int64_t count, const mxm_problem* h_problems,
-                                                 int mode, int slices, size_t* bytes) {
-  (void)count; (void)h_problems; (void)mode; (void)slices;
-  if (bytes) *bytes = 0;
-  return MXM_ERR_UNSUPPORTED;
-}
-
-extern "C" mxm_status mxm_grouped(int64_t count, const mxm_problem* d_problems, int mode,
-                                  int slices, void* d_ws, size_t ws_bytes, void* stream) {
-  (void)count; (void)d_problems; (void)mode; (void)slices; (void)d_ws; (void)ws_bytes;
-  (void)stream;
-  return MXM_ERR_UNSUPPORTED;
-}

@@ -77,3 +77,27 @@ def test_workspace_size_is_host_arithmetic():
     assert ws >= tiles * 128 * 64 * 2
     assert ws < tiles * 128 * 64 * 2 + 8 * 1024
     assert mxm.mxm_workspace_size(1, 256, 128, 128, 0) == 0
+
+
+def test_grouped_workspace_size_on_host():
+    import numpy as np
+    rows = np.array([[0, 0, 0, 128, 64, 128], [0, 0, 0, 129, 65, 1], [0, 0, 0, 0, 5, 5]],
+                    dtype=np.int64)
+    lib = mxm.load()
+    size = ctypes.c_size_t(0)
+    st = lib.mxm_grouped_workspace_size(3, rows.ctypes.data, 1, 7, ctypes.byref(size))
+    assert st == mxm.MXM_OK
+    # A tiles: 1*1 + 2*2 ; B tiles: 1*1 + 1*2 ; 7 planes of 16 KiB each
+    assert size.value >= 7 * (5 + 3) * 16384
+    assert size.value < 7 * (5 + 3) * 16384 + 16 * 1024
+    st = lib.mxm_grouped_workspace_size(3, rows.ctypes.data, 0, 0, ctypes.byref(size))
+    assert st == mxm.MXM_OK and size.value >= (5 + 5) * 128 * 16 * 8
+    bad = rows.copy()
+    bad[0, 3] = -1
+    assert lib.mxm_grouped_workspace_size(3, bad.ctypes.data, 1, 7, ctypes.byref(size)) == \
+        mxm.MXM_ERR_INVALID_ARG
+    assert lib.mxm_grouped_workspace_size(3, rows.ctypes.data, 3, 7, ctypes.byref(size)) == \
+        mxm.MXM_ERR_UNSUPPORTED
+    assert lib.mxm_grouped(0, None, 1, 7, None, 0, None) == mxm.MXM_OK
+    assert lib.mxm_grouped(4, ctypes.c_void_p(0x1000), 1, 7, ctypes.c_void_p(0x10000), 16, None) == \
+        mxm.MXM_ERR_WORKSPACE_TOO_SMALL

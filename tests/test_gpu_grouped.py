@@ -1,0 +1,98 @@
+"""Grouped products (mxm_grouped): a device-resident table of uneven problems
+computed by one persistent launch sequence, also under CUDA-graph capture.
+Every product is checked against the oracle: the emulated modes
+bit-identical to the CPU emulator, native FP64 within 2 k u (|A||B|)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1211_1581_gb300 import inputs
+from helpers import assert_bitwise, assert_within_bound
+
+torch = pytest.importorskip("torch")
+from paper_1211_1581_gb300 import mxm  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def make_group(dims, seed=0, kind="uniform"):
+    hs, ds = [], []
+    for p, (m, k, n) in enumerate(dims):
+        A, B = inputs.gemm_operands(kind, m, k, n, seed=seed, cfg=100 + p)
+        hs.append((A, B))
+        ds.append((torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
+                   torch.full((m, n), float("nan"), dtype=torch.float64, device="cuda")))
+    return hs, ds
+
+
+def run_group(ds, mode, S, graph=False):
+    table_h = mxm.problem_table(ds)
+    ws_bytes = mxm.mxm_grouped_workspace_size(table_h, mode, S)
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device="cuda")
+    table_d = table_h.cuda()
+    if not graph:
+        mxm.mxm_grouped(table_d, mode, S, ws)
+    else:
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            mxm.mxm_grouped(table_d, mode, S, ws, stream=s)
+        for _, _, C in ds:
+            C.fill_(float("nan"))
+        g.replay()
+        g.replay()
+    torch.cuda.synchronize()
+    return mxm.mxm_get_device_status()
+
+
+DIMS = [(1, 1, 1), (17, 5, 33), (128, 64, 128), (129, 65, 131), (300, 200, 257), (16, 1024, 16),
+        (0, 5, 7), (5, 0, 7), (7, 9, 0), (1000, 33, 20), (64, 300, 500), (256, 256, 256)]
+
+
+@pytest.mark.parametrize("graph", [False, True])
+@pytest.mark.parametrize("mode,S", [(mxm.MODE_EMUL_I8, 7), (mxm.MODE_EMUL_BF16, 6),
+                                    (mxm.MODE_F64, 0)])
+def test_grouped_matches_oracle(mode, S, graph):
+    hs, ds = make_group(DIMS, kind="spread" if mode != mxm.MODE_F64 else "uniform")
+    assert run_group(ds, mode, S, graph=graph) == mxm.MXM_OK
+    for (A, B), (_, _, C) in zip(hs, ds):
+        got = C.cpu().numpy()
+        if mode == mxm.MODE_F64:
+            assert_within_bound(got, oracle.gemm_dot2(A, B), oracle.gemm_abs(A, B), A.shape[1],
+                                f"grouped f64 {A.shape}x{B.shape}")
+        else:
+            beta = 8 if mode == mxm.MODE_EMUL_BF16 else 7
+            assert_bitwise(got, oracle.ozaki_gemm(A, B, S=S, beta=beta),
+                           f"grouped emul {A.shape}x{B.shape}")
+
+
+def test_grouped_workspace_too_small_reported():
+    _, ds = make_group(DIMS[:4])
+    table_h = mxm.problem_table(ds)
+    need = mxm.mxm_grouped_workspace_size(table_h, mxm.MODE_EMUL_I8, 7)
+    ws = torch.empty(need // 2, dtype=torch.uint8, device="cuda")
+    mxm.mxm_grouped(table_h.cuda(), mxm.MODE_EMUL_I8, 7, ws)
+    torch.cuda.synchronize()
+    assert mxm.mxm_get_device_status() == mxm.MXM_ERR_WORKSPACE_TOO_SMALL
+    for _, _, C in ds:  # nothing was computed
+        assert torch.isnan(C).all()
+
+
+def test_grouped_2000_logu_sampled():
+    """The grouped workload: 2000 problems, each of m, k, n log-uniform in
+    [16, 1024] from seed 0; both modes; 24 problems checked in full."""
+    dims = inputs.grouped_problems(0, 2000)
+    hs, ds = make_group([tuple(int(v) for v in d) for d in dims])
+    rng = np.random.default_rng(5)
+    pick = rng.choice(len(dims), 24, replace=False)
+    for mode, S in ((mxm.MODE_EMUL_I8, 7), (mxm.MODE_F64, 0)):
+        assert run_group(ds, mode, S, graph=True) == mxm.MXM_OK
+        for p in pick:
+            A, B = hs[p]
+            got = ds[p][2].cpu().numpy()
+            if mode == mxm.MODE_F64:
+                assert_within_bound(got, oracle.gemm_dot2(A, B), oracle.gemm_abs(A, B),
+                                    A.shape[1], f"p={p}")
+            else:
+                assert_bitwise(got, oracle.ozaki_gemm(A, B, S=S), f"p={p}")
