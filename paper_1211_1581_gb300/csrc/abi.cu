@@ -8,7 +8,7 @@
 #include <mutex>
 #include <vector>
 
-#include "../../include/mxm.h"
+#include "mxm.h"
 #include "mxm_internal.h"
 #include "ptx.cuh"
 

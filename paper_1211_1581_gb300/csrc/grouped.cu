@@ -16,7 +16,7 @@
 #include <cstdint>
 #include <vector>
 
-#include "../../include/mxm.h"
+#include "mxm.h"
 #include "mxm_internal.h"
 
 namespace mxm {

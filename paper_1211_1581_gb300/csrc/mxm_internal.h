@@ -70,6 +70,9 @@ inline int ozaki_window_mmas(int beta) {
   return static_cast<int>((1ll << 24) / per_mma);
 }
 
+// The same bound in whole k-blocks of 64 (4 MMAs each), as the kernel counts.
+inline int ozaki_window_stages(int beta) { return ozaki_window_mmas(beta) / 4; }
+
 cudaError_t launch_ozaki_scale(const double* A, const double* B, const OzakiDims& d,
                                uint64_t* rowbits, uint64_t* colbits, int* status,
                                cudaStream_t s);

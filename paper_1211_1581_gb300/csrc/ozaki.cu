@@ -470,6 +470,7 @@ struct OzGrouped {
 // epilogue of one tile overlaps the main loop of the next.
 //
 // Acc: type of the exact per-diagonal running sums (int or long long).
+// window: k-blocks (stages of 4 MMAs) per accumulation window.
 // kFloat (BF16 comparison mode only): one slice of bf16-rounded values, the
 // FP32 accumulator covers all of k in one window and is converted to FP64
 // without scaling.
@@ -545,60 +546,60 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
+    // Kept lean: one wait per stage, four MMAs with precomputed descriptors
+    // (stage s of the ring is s * 16 KiB further, i.e. +1024 in the
+    // descriptor's address field; K steps of 16 bf16 = 32 bytes are +2), and
+    // windows counted in whole stages.
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16_f32(128, kBN);
+      const uint64_t adesc0 = sw128_kmajor_desc(smem_u32(sm.a[0]));
+      const uint64_t bdesc0 = sw128_kmajor_desc(smem_u32(sm.b[0]));
       int stage = 0;
       uint32_t phase = 0;
       int buf = 0;
       uint32_t uses0 = 0u, uses1 = 0u;  // windows started in accumulator 0 / 1
       bool acquired = false;
-      int cnt = 0;
+      int wcnt = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int64_t Kt = tiles.tile(t).Kt;
         for (int g = S + 1; g >= 2 && ok; --g) {
-          const int64_t nmma = Kt * kMmaPerStage * (g - 1);
-          int64_t done = 0;
-          for (int64_t kb = 0; kb < Kt && ok; ++kb) {
-            for (int s = 1; s <= g - 1; ++s) {
-              if (!mbar_wait_bounded(&sm.full[stage], phase, abort_flag, status)) {
+          const int64_t nst = Kt * (g - 1);
+          for (int64_t st = 0; st < nst; ++st) {
+            if (!mbar_wait_bounded(&sm.full[stage], phase, abort_flag, status)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            if (!acquired) {
+              const uint32_t u = buf ? uses1 : uses0;
+              if (u > 0 &&
+                  !mbar_wait_bounded(&sm.accempty[buf], (u - 1u) & 1u, abort_flag, status)) {
                 ok = false;
                 break;
               }
               tc_fence_after();
-              const uint32_t a_addr = smem_u32(sm.a[stage]);
-              const uint32_t b_addr = smem_u32(sm.b[stage]);
-#pragma unroll
-              for (int kk = 0; kk < kMmaPerStage; ++kk) {
-                if (!acquired) {
-                  const uint32_t u = buf ? uses1 : uses0;
-                  if (u > 0 &&
-                      !mbar_wait_bounded(&sm.accempty[buf], (u - 1u) & 1u, abort_flag, status)) {
-                    ok = false;
-                    break;
-                  }
-                  tc_fence_after();
-                  if (buf) ++uses1; else ++uses0;
-                  acquired = true;
-                  cnt = 0;
-                }
-                mma_bf16_ss(tmem + static_cast<uint32_t>(buf * kBN),
-                            sw128_kmajor_desc(a_addr + kk * 32),
-                            sw128_kmajor_desc(b_addr + kk * 32), idesc, cnt > 0 ? 1u : 0u);
-                ++cnt;
-                ++done;
-                if (cnt == window || done == nmma) {
-                  mma_commit(&sm.accfull[buf]);
-                  buf ^= 1;
-                  acquired = false;
-                }
-              }
-              mma_commit(&sm.empty[stage]);
-              if (!ok) break;
-              if (++stage == kStages) {
-                stage = 0;
-                phase ^= 1u;
-              }
+              if (buf) ++uses1; else ++uses0;
+              acquired = true;
+              wcnt = 0;
+            }
+            const uint64_t da = adesc0 + static_cast<uint64_t>(stage) * (kOzTileBytes >> 4);
+            const uint64_t db = bdesc0 + static_cast<uint64_t>(stage) * (kOzTileBytes >> 4);
+            const uint32_t d = tmem + static_cast<uint32_t>(buf * kBN);
+            mma_bf16_ss(d, da, db, idesc, wcnt > 0 ? 1u : 0u);
+            mma_bf16_ss(d, da + 2, db + 2, idesc, 1u);
+            mma_bf16_ss(d, da + 4, db + 4, idesc, 1u);
+            mma_bf16_ss(d, da + 6, db + 6, idesc, 1u);
+            mma_commit(&sm.empty[stage]);
+            ++wcnt;
+            if (wcnt == window || st + 1 == nst) {
+              mma_commit(&sm.accfull[buf]);
+              buf ^= 1;
+              acquired = false;
+            }
+            if (++stage == kStages) {
+              stage = 0;
+              phase ^= 1u;
             }
           }
         }
@@ -612,17 +613,31 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row_in_tile = quarter * 32 + lane;
     const uint32_t t_lane = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
     const uint32_t t_acc = t_lane + kAccCol + static_cast<uint32_t>(half * 128);
+    const double dmax2 = static_cast<double>(((1 << beta) - 1) * ((1 << beta) - 1));
     int buf = 0;
     uint32_t fulls0 = 0u, fulls1 = 0u;  // windows drained from accumulator 0 / 1
     bool ok = true;
     Acc D[64];
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const OzTile j = tiles.tile(t);
+      // Diagonals g >= gx are combined exactly in int64 (the partial sum
+      // Y = sum_g D_g 2^{beta (S+1-g)} stays below 2^52 by the bound
+      // |D_g| <= (g-1)(2^beta-1)^2 64 Kt): the FP64 fold of those steps is
+      // exact, so doing them in integers gives the same bits.
+      int gx = S + 1;
+      {
+        double yb = 0.0;
+        for (int g = S + 1; g >= 2; --g) {
+          yb += (g - 1) * dmax2 * 64.0 * static_cast<double>(j.Kt) * pow2_normal(beta * (S + 1 - g));
+          if (yb >= 4503599627370496.0) break;  // 2^52
+          gx = g;
+        }
+      }
       for (int g = S + 1; g >= 2 && ok; --g) {
 #pragma unroll
         for (int i = 0; i < 64; ++i) D[i] = 0;
-        const int64_t nmma = j.Kt * kMmaPerStage * (g - 1);
-        const int64_t nwin = (nmma + window - 1) / window;
+        const int64_t nst = j.Kt * (g - 1);
+        const int64_t nwin = (nst + window - 1) / window;
         for (int64_t w = 0; w < nwin; ++w) {
           if (!mbar_wait_bounded(&sm.accfull[buf], (buf ? fulls1 : fulls0) & 1u, abort_flag,
                                  status)) {
@@ -651,10 +666,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           buf ^= 1;
         }
         if (!ok) break;
-        // fold D_g into the FP64 running sum: acc = acc + D_g * 2^{-beta g}
-        const double wgt = kFloat ? 1.0 : pow2_normal(-beta * g);
         const bool first = (g == S + 1);
         const bool last = (g == 2);
+        const bool exact = !kFloat && g >= gx;  // int64 phase
         const int64_t row = j.row0 + row_in_tile;
         int er = 0;
         if (!kFloat && last && row < j.m) er = exponent_from_absbits(j.rowbits[row]);
@@ -668,13 +682,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           double v[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const double term = __dmul_rn(static_cast<double>(D[ch * 8 + i]), wgt);  // exact
-            if (first) {
-              v[i] = term;
+            if constexpr (kFloat) {
+              v[i] = static_cast<double>(D[ch * 8 + i]);
+            } else if (exact) {
+              // Y (int64, units of 2^{-beta (S+1)}) += D_g 2^{beta (S+1-g)}
+              long long y = first ? 0ll
+                                  : static_cast<long long>(
+                                        (static_cast<uint64_t>(r[2 * i + 1]) << 32) | r[2 * i]);
+              y += static_cast<long long>(D[ch * 8 + i]) * (1ll << (beta * (S + 1 - g)));
+              if (g == gx) {
+                v[i] = i64_times_pow2(y, -beta * (S + 1));  // exact: |y| < 2^52
+              } else {
+                r[2 * i] = static_cast<uint32_t>(y);
+                r[2 * i + 1] = static_cast<uint32_t>(static_cast<uint64_t>(y) >> 32);
+              }
             } else {
               const double prev =
                   __hiloint2double(static_cast<int>(r[2 * i + 1]), static_cast<int>(r[2 * i]));
-              v[i] = __dadd_rn(prev, term);
+              v[i] = __dadd_rn(prev, i64_times_pow2(static_cast<long long>(D[ch * 8 + i]), -beta * g));
             }
           }
           if (last) {
@@ -693,10 +718,12 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             }
           } else {
+            if (kFloat || !exact || g == gx) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              r[2 * i] = static_cast<uint32_t>(__double2loint(v[i]));
-              r[2 * i + 1] = static_cast<uint32_t>(__double2hiint(v[i]));
+              for (int i = 0; i < 8; ++i) {
+                r[2 * i] = static_cast<uint32_t>(__double2loint(v[i]));
+                r[2 * i + 1] = static_cast<uint32_t>(__double2hiint(v[i]));
+              }
             }
             tmem_st16(t_acc + ch * 16, r);
             tmem_wait_st();
@@ -794,7 +821,7 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
                               const uint64_t* rowbits, const uint64_t* colbits, double* C,
                               const OzakiDims& d, int* status, cudaStream_t s) {
   if (d.Mt == 0 || d.Nt == 0) return cudaSuccess;
-  const int window = ozaki_window_mmas(d.beta);
+  const int window = ozaki_window_stages(d.beta);
   OzSingle tiles{aslices, bslices, rowbits, colbits, C, d.m, d.n, d.Mt, d.Nt, d.Kt};
   const int64_t count = d.Mt * d.Nt;
   const int64_t grid = count < sm_count() ? count : sm_count();
@@ -815,8 +842,8 @@ cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t /*max_kt*
   const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
   OzGrouped tiles{hdr, recs, ws};
   // the host does not see the table: 64-bit running sums are safe for any k
-  return launch_oz_gemm_t<long long, false>(tiles, sms, S, beta, ozaki_window_mmas(beta), status,
-                                            s);
+  return launch_oz_gemm_t<long long, false>(tiles, sms, S, beta, ozaki_window_stages(beta),
+                                            status, s);
 }
 
 cudaError_t launch_bf16_gemm(const double* A, const double* B, double* C, const OzakiDims& d,
@@ -831,7 +858,8 @@ cudaError_t launch_bf16_gemm(const double* A, const double* B, double* C, const 
   OzSingle tiles{aplane, bplane, nullptr, nullptr, C, d.m, d.n, d.Mt, d.Nt, d.Kt};
   const int64_t count = d.Mt * d.Nt;
   const int64_t grid = count < sm_count() ? count : sm_count();
-  const int whole_k = static_cast<int>(d.Kt * kMmaPerStage);
+  // one window covers all of k (FP32 accumulation is the mode's semantics)
+  const int whole_k = static_cast<int>(d.Kt);
   return launch_oz_gemm_t<float, true>(tiles, grid, 1, 8, whole_k, status, s);
 }
 

@@ -8,7 +8,7 @@
 
 #include <cstdint>
 
-#include "../../include/mxm.h"
+#include "mxm.h"
 #include "mxm_internal.h"
 #include "ptx.cuh"
 

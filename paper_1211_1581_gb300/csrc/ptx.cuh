@@ -289,6 +289,19 @@ __device__ __forceinline__ double ldexp_rn(double x, int E) {
   return __longlong_as_double(static_cast<long long>(sign | r));
 }
 
+// y * 2^p exactly, for |y| < 2^53 and a normal result, built from the bits
+// (no FP64 arithmetic: int -> double conversion and power-of-two scaling).
+__device__ __forceinline__ double i64_times_pow2(long long y, int p) {
+  if (y == 0) return 0.0;
+  const uint64_t sign = y < 0 ? 0x8000000000000000ull : 0ull;
+  const uint64_t mag = y < 0 ? static_cast<uint64_t>(-y) : static_cast<uint64_t>(y);
+  const int e = 63 - __clzll(static_cast<long long>(mag));  // mag in [2^e, 2^{e+1})
+  const uint64_t mant = mag << (52 - e);
+  const uint64_t be = static_cast<uint64_t>(1023 + e + p);
+  return __longlong_as_double(
+      static_cast<long long>(sign | (be << 52) | (mant & 0x000FFFFFFFFFFFFFull)));
+}
+
 // 2^p as a double for -1022 <= p <= 1023.
 __device__ __forceinline__ double pow2_normal(int p) {
   return __longlong_as_double(static_cast<long long>(static_cast<uint64_t>(p + 1023) << 52));
