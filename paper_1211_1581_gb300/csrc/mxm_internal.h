@@ -18,12 +18,23 @@ constexpr int kStatusBounds = 8;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 
 // ---------------------------------------------------------------- Ozaki
-// Operand tiles of the slice GEMM: 128 rows x 64 bf16 (128 bytes per row),
-// 16 KiB, stored pre-swizzled (128-byte swizzle) so one bulk copy moves a
-// tile into shared memory in the layout tcgen05.mma reads.
+// Operand tiles of the slice GEMM: 128 rows x 128 bf16, 32 KiB, stored
+// pre-swizzled so that one bulk copy moves a tile into shared memory in the
+// layout tcgen05.mma reads: two 128-byte-swizzle atoms along k (k 0..63 and
+// 64..127, 16 KiB each), each with rows of 128 bytes in which the 16-byte
+// chunk c of row r sits at chunk position c ^ (r % 8).  (Bulk copies of
+// 32 KiB stream about twice as fast per SM as copies of 16 KiB.)
 constexpr int kOzTileRows = 128;
-constexpr int kOzTileK = 64;
+constexpr int kOzTileK = 128;
+constexpr int kOzAtomK = 64;
+constexpr int kOzAtomBytes = kOzTileRows * kOzAtomK * 2;
 constexpr int kOzTileBytes = kOzTileRows * kOzTileK * 2;
+constexpr int kOzChunksPerRow = kOzTileK / 8;
+
+// Byte offset of 16-byte chunk c (k = 8c .. 8c+7) of row r inside a tile.
+__host__ __device__ inline int oz_chunk_offset(int r, int c) {
+  return (c >> 3) * kOzAtomBytes + r * 128 + (((c & 7) ^ (r & 7)) << 4);
+}
 constexpr int kOzMaxSlices = 12;
 
 struct OzakiDims {
@@ -70,8 +81,9 @@ inline int ozaki_window_mmas(int beta) {
   return static_cast<int>((1ll << 24) / per_mma);
 }
 
-// The same bound in whole k-blocks of 64 (4 MMAs each), as the kernel counts.
-inline int ozaki_window_stages(int beta) { return ozaki_window_mmas(beta) / 4; }
+// The same bound in whole k-blocks (kOzTileK / 16 MMAs each), as the kernel
+// counts.
+inline int ozaki_window_stages(int beta) { return ozaki_window_mmas(beta) / (kOzTileK / 16); }
 
 cudaError_t launch_ozaki_scale(const double* A, const double* B, const OzakiDims& d,
                                uint64_t* rowbits, uint64_t* colbits, int* status,

@@ -170,8 +170,8 @@ __device__ __forceinline__ void split_a_tile(const double* __restrict__ A, int64
                                              const uint64_t* __restrict__ rowbits, int S,
                                              int beta, int64_t tm, int64_t tk, uint8_t* tile,
                                              size_t slice_stride) {
-  for (int p = threadIdx.x; p < kOzTileRows * 8; p += blockDim.x) {
-    const int c = p & 7, r = p >> 3;
+  for (int p = threadIdx.x; p < kOzTileRows * kOzChunksPerRow; p += blockDim.x) {
+    const int c = p % kOzChunksPerRow, r = p / kOzChunksPerRow;
     const int64_t row = tm * kOzTileRows + r;
     const int64_t k0 = tk * kOzTileK + c * 8;
     double v[8];
@@ -179,7 +179,7 @@ __device__ __forceinline__ void split_a_tile(const double* __restrict__ A, int64
     if (row < m) e = exponent_from_absbits(rowbits[row]);
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = (row < m && k0 + j < k) ? __ldg(A + row * k + k0 + j) : 0.0;
-    split_chunk_store(v, e, S, beta, tile + r * 128 + ((c ^ (r & 7)) << 4), slice_stride);
+    split_chunk_store(v, e, S, beta, tile + oz_chunk_offset(r, c), slice_stride);
   }
 }
 
@@ -189,8 +189,8 @@ __device__ __forceinline__ void split_b_tile(const double* __restrict__ B, int64
                                              const uint64_t* __restrict__ colbits, int S,
                                              int beta, int64_t tn, int64_t tk, uint8_t* tile,
                                              size_t slice_stride) {
-  for (int p = threadIdx.x; p < kOzTileRows * 8; p += blockDim.x) {
-    const int c = p & 7, r = p >> 3;
+  for (int p = threadIdx.x; p < kOzTileRows * kOzChunksPerRow; p += blockDim.x) {
+    const int c = p % kOzChunksPerRow, r = p / kOzChunksPerRow;
     const int64_t col = tn * kOzTileRows + r;
     const int64_t k0 = tk * kOzTileK + c * 8;
     double v[8];
@@ -198,7 +198,7 @@ __device__ __forceinline__ void split_b_tile(const double* __restrict__ B, int64
     if (col < n) f = exponent_from_absbits(colbits[col]);
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = (col < n && k0 + j < k) ? __ldg(B + (k0 + j) * n + col) : 0.0;
-    split_chunk_store(v, f, S, beta, tile + r * 128 + ((c ^ (r & 7)) << 4), slice_stride);
+    split_chunk_store(v, f, S, beta, tile + oz_chunk_offset(r, c), slice_stride);
   }
 }
 
@@ -333,8 +333,8 @@ __global__ void __launch_bounds__(256) bf16_tiles_kernel(const double* __restric
                                                          int64_t Kt, uint8_t* __restrict__ out) {
   const int64_t tk = blockIdx.x, tr = blockIdx.y;
   uint8_t* tile = out + (static_cast<size_t>(tr) * Kt + tk) * kOzTileBytes;
-  for (int p = threadIdx.x; p < kOzTileRows * 8; p += blockDim.x) {
-    const int c = p & 7, r = p >> 3;
+  for (int p = threadIdx.x; p < kOzTileRows * kOzChunksPerRow; p += blockDim.x) {
+    const int c = p % kOzChunksPerRow, r = p / kOzChunksPerRow;
     const int64_t row = tr * kOzTileRows + r;   // row of A, or column of B
     const int64_t k0 = tk * kOzTileK + c * 8;
     uint32_t packed[4];
@@ -350,13 +350,13 @@ __global__ void __launch_bounds__(256) bf16_tiles_kernel(const double* __restric
       }
       packed[j >> 1] = bf16_rne_bits(x0) | (bf16_rne_bits(x1) << 16);
     }
-    *reinterpret_cast<uint4*>(tile + r * 128 + ((c ^ (r & 7)) << 4)) =
+    *reinterpret_cast<uint4*>(tile + oz_chunk_offset(r, c)) =
         make_uint4(packed[0], packed[1], packed[2], packed[3]);
   }
 }
 
 // ---------------------------------------------------------------- steps 3-4
-constexpr int kStages = 6;
+constexpr int kStages = 3;
 constexpr int kThreads = 320;       // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 constexpr int kEpiWarps = 8;
 constexpr int kBN = 128;            // MMA N (columns of the C tile)
@@ -586,10 +586,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t da = adesc0 + static_cast<uint64_t>(stage) * (kOzTileBytes >> 4);
             const uint64_t db = bdesc0 + static_cast<uint64_t>(stage) * (kOzTileBytes >> 4);
             const uint32_t d = tmem + static_cast<uint32_t>(buf * kBN);
-            mma_bf16_ss(d, da, db, idesc, wcnt > 0 ? 1u : 0u);
-            mma_bf16_ss(d, da + 2, db + 2, idesc, 1u);
-            mma_bf16_ss(d, da + 4, db + 4, idesc, 1u);
-            mma_bf16_ss(d, da + 6, db + 6, idesc, 1u);
+#pragma unroll
+            for (int kk = 0; kk < kMmaPerStage; ++kk) {
+              // k step kk: atom kk / 4 (16 KiB = +1024), 32 bytes per step inside it (+2)
+              const uint64_t off = static_cast<uint64_t>((kk >> 2) * (kOzAtomBytes >> 4) + (kk & 3) * 2);
+              mma_bf16_ss(d, da + off, db + off, idesc, (kk > 0 || wcnt > 0) ? 1u : 0u);
+            }
             mma_commit(&sm.empty[stage]);
             ++wcnt;
             if (wcnt == window || st + 1 == nst) {
@@ -622,13 +624,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       const OzTile j = tiles.tile(t);
       // Diagonals g >= gx are combined exactly in int64 (the partial sum
       // Y = sum_g D_g 2^{beta (S+1-g)} stays below 2^52 by the bound
-      // |D_g| <= (g-1)(2^beta-1)^2 64 Kt): the FP64 fold of those steps is
+      // |D_g| <= (g-1)(2^beta-1)^2 128 Kt): the FP64 fold of those steps is
       // exact, so doing them in integers gives the same bits.
       int gx = S + 1;
       {
         double yb = 0.0;
         for (int g = S + 1; g >= 2; --g) {
-          yb += (g - 1) * dmax2 * 64.0 * static_cast<double>(j.Kt) * pow2_normal(beta * (S + 1 - g));
+          yb += (g - 1) * dmax2 * static_cast<double>(kOzTileK) * static_cast<double>(j.Kt) *
+                pow2_normal(beta * (S + 1 - g));
           if (yb >= 4503599627370496.0) break;  // 2^52
           gx = g;
         }
@@ -812,9 +815,9 @@ static cudaError_t launch_oz_gemm_t(const Tiles& tiles, int64_t grid, int S, int
 }
 
 static bool narrow_sums(int S, int beta, int64_t Kt) {
-  // int32 running sums suffice while S (2^beta - 1)^2 * 64 Kt < 2^31
+  // int32 running sums suffice while S (2^beta - 1)^2 * 128 Kt < 2^31
   const long long dmax = (1ll << beta) - 1;
-  return static_cast<double>(S) * dmax * dmax * 64.0 * Kt < 2147483647.0;
+  return static_cast<double>(S) * dmax * dmax * kOzTileK * Kt < 2147483647.0;
 }
 
 cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,

@@ -87,9 +87,9 @@ def test_grouped_workspace_size_on_host():
     size = ctypes.c_size_t(0)
     st = lib.mxm_grouped_workspace_size(3, rows.ctypes.data, 1, 7, ctypes.byref(size))
     assert st == mxm.MXM_OK
-    # A tiles: 1*1 + 2*2 ; B tiles: 1*1 + 1*2 ; 7 planes of 16 KiB each
-    assert size.value >= 7 * (5 + 3) * 16384
-    assert size.value < 7 * (5 + 3) * 16384 + 16 * 1024
+    # A tiles: 1*1 + 2*1 ; B tiles: 1*1 + 1*1 ; 7 planes of 32 KiB tiles
+    assert size.value >= 7 * (3 + 2) * 32768
+    assert size.value < 7 * (3 + 2) * 32768 + 16 * 1024
     st = lib.mxm_grouped_workspace_size(3, rows.ctypes.data, 0, 0, ctypes.byref(size))
     assert st == mxm.MXM_OK and size.value >= (5 + 5) * 128 * 16 * 8
     bad = rows.copy()
