@@ -62,7 +62,7 @@ def load_peaks():
 
 def default_slices(kind: str, beta: int) -> int:
     """Smallest slice count meeting 2ku|A||B| at n = 8192 on sampled entries
-    of each input kind (the tuner's result)."""
+    of each input kind, found with the oracle on sampled entries."""
     table = {("spread", 7): 7, ("spread", 8): 6, ("uniform", 7): 6, ("uniform", 8): 5}
     return table[(kind, beta)]
 

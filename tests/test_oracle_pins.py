@@ -358,7 +358,7 @@ def test_ozaki_high_slice_count_matches_dot2_closely():
         assert np.all(np.abs(C - d2) <= 8 * U * ab), (beta, S)
 
 
-def test_ozaki_within_north_star_bound_at_working_slices():
+def test_ozaki_within_acceptance_bound_at_working_slices():
     """The library's acceptance bound |C - C_dot2| <= 2 k u (|A||B|) holds at
     the slice counts used at scale: 7 slices of 7 bits (6 of 8 bits) for
     uniform entries, 8 of 7 bits (7 of 8 bits) when entries spread over 2^41;
