@@ -192,6 +192,27 @@ mxm_status mxm_debug_wait_timeout(uint64_t limit_ns, void* stream);
 mxm_status mxm_profile_enable(int on);
 mxm_status mxm_profile_read(double* ms, int max_phases, int64_t* calls);
 
+/*
+ * mxm_f64_emul_noalloc -- mxm_f64_emul (7-bit digits, `slices` slices) for
+ * callers that cannot allocate device memory, e.g. code inside a process
+ * whose allocator owns the device, loops that must never reach the driver's
+ * allocator, or plugins handed device pointers but no allocator.  The paper
+ * has no counterpart: this is a library convenience.  The result is the
+ * same as mxm_f64_emul's (bit for bit).  The call allocates nothing: its
+ * scratch is a fixed 64 MiB array in the library's device memory, present on
+ * every GPU that loads the library until the process exits.  The first call
+ * on a device looks up that array's device address (a runtime query, no
+ * allocation); make that first call before any stream capture.  A product
+ * whose scratch would exceed 64 MiB (e.g. beyond m = k = n = 1024 at 12
+ * slices, or 1536 at 7) returns MXM_ERR_WORKSPACE_TOO_SMALL and launches
+ * nothing.  All calls share the one array and it keeps the previous call's
+ * contents (the launch sequence clears what must start at zero): calls whose
+ * work overlaps on the GPU (other streams, other host threads) race, so
+ * serialise them.  Other conventions as mxm_f64_emul.
+ */
+mxm_status mxm_f64_emul_noalloc(const double* A, const double* B, double* C, int64_t m,
+                                int64_t k, int64_t n, int slices, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

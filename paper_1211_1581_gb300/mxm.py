@@ -50,6 +50,7 @@ SIGNATURES = {
     "mxm_debug_wait_timeout": (_I, [ctypes.c_uint64, _P]),
     "mxm_profile_enable": (_I, [_I]),
     "mxm_profile_read": (_I, [ctypes.POINTER(ctypes.c_double), _I, ctypes.POINTER(_I64)]),
+    "mxm_f64_emul_noalloc": (_I, [_P, _P, _P, _I64, _I64, _I64, _I, _P]),
 }
 
 _lib = None
@@ -133,6 +134,16 @@ def mxm_f64_emul(A, B, C, slices: int = 7, stream=None):
     m, k, n = _operands(A, B, C)
     _check(load().mxm_f64_emul(A.data_ptr(), B.data_ptr(), C.data_ptr(), m, k, n, int(slices),
                                _stream_ptr(stream)), "mxm_f64_emul")
+    return C
+
+
+def mxm_f64_emul_noalloc(A, B, C, slices: int = 7, stream=None):
+    """mxm_f64_emul with scratch from the library's fixed device array: no
+    allocation anywhere (for callers that cannot allocate); products whose
+    scratch exceeds the array raise MxmError(MXM_ERR_WORKSPACE_TOO_SMALL)."""
+    m, k, n = _operands(A, B, C)
+    _check(load().mxm_f64_emul_noalloc(A.data_ptr(), B.data_ptr(), C.data_ptr(), m, k, n,
+                                       int(slices), _stream_ptr(stream)), "mxm_f64_emul_noalloc")
     return C
 
 
