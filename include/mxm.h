@@ -204,7 +204,7 @@ mxm_status mxm_profile_read(double* ms, int max_phases, int64_t* calls);
  * on a device looks up that array's device address (a runtime query, no
  * allocation); make that first call before any stream capture.  A product
  * whose scratch would exceed 64 MiB (e.g. beyond m = k = n = 1024 at 12
- * slices, or 1536 at 7) returns MXM_ERR_WORKSPACE_TOO_SMALL and launches
+ * slices, or 1280 at 7) returns MXM_ERR_WORKSPACE_TOO_SMALL and launches
  * nothing.  All calls share the one array and it keeps the previous call's
  * contents (the launch sequence clears what must start at zero): calls whose
  * work overlaps on the GPU (other streams, other host threads) race, so

@@ -173,7 +173,8 @@ mxm_status run_gemm(int mode, const double* A, const double* B, double* C, int64
       e = launch_ozaki_split(A, B, d, rowbits, colbits, ws + L.aslices, ws + L.bslices, s);
     profile_mark(ce, 2, s);
     if (e == cudaSuccess)
-      e = launch_ozaki_gemm(ws + L.aslices, ws + L.bslices, rowbits, colbits, C, d, status, s);
+      e = launch_ozaki_gemm(ws + L.aslices, ws + L.bslices, rowbits, colbits, C, d,
+                            reinterpret_cast<uint64_t*>(ws + L.sums), status, s);
     profile_mark(ce, 3, s);
   } else if (mode == MXM_MODE_BF16_F32ACC) {
     const OzakiDims d = ozaki_dims(m, k, n, 1, 8);

@@ -55,7 +55,7 @@ inline OzakiDims ozaki_dims(int64_t m, int64_t k, int64_t n, int S, int beta) {
 
 // Workspace layout of one emulated product (offsets in bytes, 1 KiB aligned).
 struct OzakiLayout {
-  size_t rowbits, colbits, aslices, bslices, total;
+  size_t rowbits, colbits, aslices, bslices, sums, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -67,6 +67,10 @@ inline OzakiLayout ozaki_layout(const OzakiDims& d) {
   L.colbits = off; off = align_up(off + sizeof(uint64_t) * (size_t)(d.n > 0 ? d.n : 1), 1024);
   L.aslices = off; off = align_up(off + (size_t)d.S * d.Mt * d.Kt * kOzTileBytes, 1024);
   L.bslices = off; off = align_up(off + (size_t)d.S * d.Nt * d.Kt * kOzTileBytes, 1024);
+  // running sums of the recombination between diagonal pairs: per C tile
+  // 128 x 128 x 8 bytes, column-major inside the tile (so that a warp, which
+  // owns 32 consecutive rows, touches 256 contiguous bytes per column)
+  L.sums = off; off = align_up(off + (size_t)d.Mt * d.Nt * kOzTileRows * kOzTileRows * 8, 1024);
   L.total = off;
   return L;
 }
@@ -93,7 +97,7 @@ cudaError_t launch_ozaki_split(const double* A, const double* B, const OzakiDims
                                uint8_t* aslices, uint8_t* bslices, cudaStream_t s);
 cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
                               const uint64_t* rowbits, const uint64_t* colbits, double* C,
-                              const OzakiDims& d, int* status, cudaStream_t s);
+                              const OzakiDims& d, uint64_t* sums, int* status, cudaStream_t s);
 
 // ---------------------------------------------------------------- FP64
 constexpr int kF64BM = 128, kF64BN = 128, kF64BK = 16;

@@ -27,7 +27,7 @@
 namespace mxm {
 
 // Largest scratch one call may use (64 MiB; e.g. m = k = n = 1024 with up to
-// 12 slices, or m = k = n = 1536 with 7).
+// 12 slices, or m = k = n = 1280 with 7).
 constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
@@ -99,12 +99,13 @@ extern "C" mxm_status mxm_f64_emul_noalloc(const double* A, const double* B, dou
   uint64_t* rowbits = reinterpret_cast<uint64_t*>(ws + L.rowbits);
   uint64_t* colbits = reinterpret_cast<uint64_t*>(ws + L.colbits);
   // launch_ozaki_scale zeroes the column maxima before reducing into them;
-  // the row maxima and every digit-plane byte (padding included) are written
-  // before they are read.
+  // the row maxima, every digit-plane byte (padding included) and the
+  // running sums are written before they are read.
   cudaError_t e = launch_ozaki_scale(A, B, d, rowbits, colbits, status, s);
   if (e == cudaSuccess)
     e = launch_ozaki_split(A, B, d, rowbits, colbits, ws + L.aslices, ws + L.bslices, s);
   if (e == cudaSuccess)
-    e = launch_ozaki_gemm(ws + L.aslices, ws + L.bslices, rowbits, colbits, C, d, status, s);
+    e = launch_ozaki_gemm(ws + L.aslices, ws + L.bslices, rowbits, colbits, C, d,
+                            reinterpret_cast<uint64_t*>(ws + L.sums), status, s);
   return e == cudaSuccess ? MXM_OK : MXM_ERR_CUDA;
 }

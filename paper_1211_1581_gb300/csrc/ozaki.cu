@@ -397,12 +397,13 @@ struct OzTile {
   const uint8_t* a;          // slice 1 of A tile-row tm, k-block 0
   const uint8_t* b;          // slice 1 of B^T tile-row tn, k-block 0
   size_t a_slice, b_slice;   // bytes from one slice plane to the next
-  int64_t Kt;                // 64-wide k-blocks
+  int64_t Kt;                // k-blocks of kOzTileK
   const uint64_t* rowbits;   // |A| row maxima of this problem
   const uint64_t* colbits;   // |B| column maxima of this problem
   double* C;
   int64_t m, n;              // C is m x n, row-major
   int64_t row0, col0;        // origin of the tile in C
+  uint64_t* sums;            // 128 x 128 running sums, column-major (paired kernel)
 };
 
 // Tiles of one product.
@@ -413,6 +414,7 @@ struct OzSingle {
   const uint64_t* colbits;
   double* C;
   int64_t m, n, Mt, Nt, Kt;
+  uint64_t* sums;
   __device__ __forceinline__ int64_t count() const { return Mt * Nt; }
   __device__ __forceinline__ OzTile tile(int64_t t) const {
     int64_t tm, tn;
@@ -430,6 +432,8 @@ struct OzSingle {
     j.n = n;
     j.row0 = tm * kOzTileRows;
     j.col0 = tn * kOzTileRows;
+    j.sums = sums ? sums + static_cast<size_t>(tm * Nt + tn) * (kOzTileRows * kOzTileRows)
+                  : nullptr;
     return j;
   }
 };
@@ -460,6 +464,7 @@ struct OzGrouped {
     j.n = r.n;
     j.row0 = tm * kOzTileRows;
     j.col0 = tn * kOzTileRows;
+    j.sums = nullptr;
     return j;
   }
 };
@@ -742,6 +747,401 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) tmem_dealloc(tmem, kTmemCols);
 }
 
+// ---------------------------------------------------------------- steps 3-4, diagonals in pairs
+// The diagonals are taken two at a time, (g, g-1).  In every k-block, step
+// s = 1 .. g-1 brings one new A tile A_s and (for s <= g-2) one new B tile
+// B_{g-1-s}; A_s meets B_{g-s} (diagonal g, the B tile of the previous step)
+// and B_{g-1-s} (diagonal g-1).  So one A tile and one B tile per step feed
+// two digit-pair products: half the operand bytes per flop of taking one
+// diagonal at a time, which is what the bulk-copy feed of an SM allows.
+// Four TMEM accumulators (two diagonals x double buffer, 4 x 128 columns)
+// leave no room for the FP64 running sum, so the epilogue keeps it in C
+// itself between diagonal pairs (read-modify-write of its own elements).
+// An odd diagonal left over (g = 2 when S is odd) runs alone through the
+// same code.  Warpgroup 0 (warp 0: bulk copies, warps 1-2: MMA issue) gives
+// registers to warpgroups 1-2 (the epilogue: two diagonals of exact int32
+// sums).
+constexpr int kP2Threads = 384;
+constexpr int kP2Ring = 3;
+constexpr int kP2EpiWarps = 8;
+
+struct __align__(1024) Gemm2Smem {
+  uint8_t a[kP2Ring][kOzTileBytes];
+  uint8_t b[kP2Ring][kOzTileBytes];
+  uint64_t a_full[kP2Ring], a_empty[kP2Ring];
+  uint64_t b_full[kP2Ring], b_empty[kP2Ring];
+  uint64_t accfull[4], accempty[4];  // accumulator 2x + buffer; x = 0: diagonal g, 1: g-1
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+constexpr size_t kGemm2SmemBytes = sizeof(Gemm2Smem) + 1024;
+
+// 384 threads x 168 registers at launch = 128 x 80 (warpgroup 0) + 256 x 208
+__device__ __forceinline__ void regs_dec_80() {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 80;" ::: "memory");
+}
+__device__ __forceinline__ void regs_inc_208() {
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 208;" ::: "memory");
+}
+
+// One ring of shared-memory slots with full/empty barriers.
+struct Ring {
+  int slot = 0;
+  uint32_t phase = 0;
+  __device__ __forceinline__ void advance() {
+    if (++slot == kP2Ring) {
+      slot = 0;
+      phase ^= 1u;
+    }
+  }
+};
+
+// The fold of one diagonal g into a running sum held as 64 bits: an exact
+// int64 partial (units of 2^{-beta (S+1)}) while g >= gx, an FP64 value after.
+// The final scaling of one result, out of line for the same reason as
+// fold_step below.
+__device__ __noinline__ double final_scale(uint64_t st, int e) {
+  return ldexp_rn(__longlong_as_double(static_cast<long long>(st)), e);
+}
+
+// Out of line on purpose: inlined into the 128 call sites of the epilogue
+// it made the kernel's code far larger than the instruction caches.
+__device__ __noinline__ uint64_t fold_step(uint64_t st, int dval, int g, int gx, int S,
+                                           int beta) {
+  if (g >= gx) {
+    long long y = (g == S + 1) ? 0ll : static_cast<long long>(st);
+    y += static_cast<long long>(dval) * (1ll << (beta * (S + 1 - g)));
+    if (g == gx)
+      return static_cast<uint64_t>(__double_as_longlong(i64_times_pow2(y, -beta * (S + 1))));
+    return static_cast<uint64_t>(y);
+  }
+  const double acc = __longlong_as_double(static_cast<long long>(st));
+  const double term = i64_times_pow2(static_cast<long long>(dval), -beta * g);  // exact
+  return static_cast<uint64_t>(__double_as_longlong(__dadd_rn(acc, term)));
+}
+
+template <typename Tiles>
+__global__ void __launch_bounds__(kP2Threads, 1)
+    oz_gemm2_kernel(const Tiles tiles, int S, int beta, int window, int* __restrict__ status) {
+  extern __shared__ uint8_t smem_raw[];
+  Gemm2Smem& sm = *reinterpret_cast<Gemm2Smem*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kP2Ring; ++i) {
+      mbar_init(&sm.a_full[i], 1);
+      mbar_init(&sm.a_empty[i], 2);  // one arrival per MMA issuer
+      mbar_init(&sm.b_full[i], 1);
+      mbar_init(&sm.b_empty[i], 2);
+    }
+    for (int i = 0; i < 4; ++i) {
+      mbar_init(&sm.accfull[i], 1);
+      mbar_init(&sm.accempty[i], kP2EpiWarps);
+    }
+    sm.abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&sm.tmem_base, kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem_base;
+  volatile int* abort_flag = &sm.abort_flag;
+  const int64_t ntiles = tiles.count();
+  const int ngroups = (S + 1) / 2;
+
+  if (warp < 4) {
+    regs_dec_80();
+    if (warp == 0 && lane == 0) {
+      // ------------------------------------------------ producer (bulk copies)
+      Ring ra, rb;
+      bool ok = true;
+      auto load = [&](Ring& r, uint8_t (*buf)[kOzTileBytes], uint64_t* full, uint64_t* empty,
+                      const uint8_t* src) {
+        if (!mbar_wait_bounded(&empty[r.slot], r.phase ^ 1u, abort_flag, status)) return false;
+        mbar_arrive_expect_tx(&full[r.slot], kOzTileBytes);
+        bulk_g2s(buf[r.slot], src, kOzTileBytes, &full[r.slot]);
+        r.advance();
+        return true;
+      };
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const OzTile j = tiles.tile(t);
+        for (int q = 0; q < ngroups && ok; ++q) {
+          const int g = S + 1 - 2 * q;
+          for (int64_t kb = 0; kb < j.Kt && ok; ++kb) {
+            const size_t koff = static_cast<size_t>(kb) * kOzTileBytes;
+            ok = load(rb, sm.b, sm.b_full, sm.b_empty, j.b + (g - 2) * j.b_slice + koff);
+            for (int s = 1; s <= g - 1 && ok; ++s) {
+              ok = load(ra, sm.a, sm.a_full, sm.a_empty, j.a + (s - 1) * j.a_slice + koff);
+              if (ok && s <= g - 2)
+                ok = load(rb, sm.b, sm.b_full, sm.b_empty, j.b + (g - 2 - s) * j.b_slice + koff);
+            }
+          }
+        }
+      }
+      // tail: wait until every slot is released so no copy or commit lands
+      // after the block has exited
+      for (int i = 0; i < kP2Ring; ++i) {
+        if (!mbar_wait_bounded(&sm.a_empty[ra.slot], ra.phase ^ 1u, abort_flag, status)) break;
+        ra.advance();
+      }
+      for (int i = 0; i < kP2Ring; ++i) {
+        if (!mbar_wait_bounded(&sm.b_empty[rb.slot], rb.phase ^ 1u, abort_flag, status)) break;
+        rb.advance();
+      }
+    } else if ((warp == 1 || warp == 2) && lane == 0) {
+      // ------------------------------------------------ MMA issuers
+      // Two issuing threads: warp 1 issues the products of diagonal g (its
+      // accumulators 0/1), warp 2 those of diagonal g-1 (accumulators 2/3).
+      // One thread cannot issue 128 x 128 x 16 MMAs as fast as the tensor
+      // core retires them; two interleave and keep it busy.  Both walk the
+      // same stage sequence; every ring slot is released by two arrivals,
+      // one per issuer (a commit after its MMAs, or a plain arrival for a
+      // tile it does not read).
+      const int x = warp - 1;
+      const uint32_t idesc = idesc_bf16_f32(128, kBN);
+      const uint64_t adesc0 = sw128_kmajor_desc(smem_u32(sm.a[0]));
+      const uint64_t bdesc0 = sw128_kmajor_desc(smem_u32(sm.b[0]));
+      Ring ra, rb;
+      int buf = 0, cnt = 0;
+      bool acq = false;
+      uint32_t uses0 = 0u, uses1 = 0u;  // windows started in this issuer's two buffers
+      bool ok = true;
+      auto acquire = [&]() {
+        if (acq) return true;
+        const uint32_t u = buf ? uses1 : uses0;
+        const int a = 2 * x + buf;
+        if (u > 0 && !mbar_wait_bounded(&sm.accempty[a], (u - 1u) & 1u, abort_flag, status))
+          return false;
+        tc_fence_after();
+        if (buf) ++uses1; else ++uses0;
+        acq = true;
+        cnt = 0;
+        return true;
+      };
+      auto mma8 = [&](int aslot, int bslot) {
+        const uint64_t da = adesc0 + static_cast<uint64_t>(aslot) * (kOzTileBytes >> 4);
+        const uint64_t db = bdesc0 + static_cast<uint64_t>(bslot) * (kOzTileBytes >> 4);
+        const uint32_t d = tmem + static_cast<uint32_t>((2 * x + buf) * kBN);
+        const uint32_t acc0 = cnt > 0 ? 1u : 0u;
+#pragma unroll
+        for (int kk = 0; kk < kMmaPerStage; ++kk) {
+          const uint64_t off =
+              static_cast<uint64_t>((kk >> 2) * (kOzAtomBytes >> 4) + (kk & 3) * 2);
+          mma_bf16_ss(d, da + off, db + off, idesc, kk > 0 ? 1u : acc0);
+        }
+      };
+      auto finish = [&](bool last) {
+        if (++cnt == window || last) {
+          mma_commit(&sm.accfull[2 * x + buf]);
+          buf ^= 1;
+          acq = false;
+        }
+      };
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int64_t Kt = tiles.tile(t).Kt;
+        for (int q = 0; q < ngroups && ok; ++q) {
+          const int g = S + 1 - 2 * q;
+          const bool pair = g - 1 >= 2;
+          for (int64_t kb = 0; kb < Kt && ok; ++kb) {
+            if (!mbar_wait_bounded(&sm.b_full[rb.slot], rb.phase, abort_flag, status)) {
+              ok = false;
+              break;
+            }
+            int bprev = rb.slot;  // B_{g-1}: read by diagonal g only
+            rb.advance();
+            if (x == 1) mbar_arrive(&sm.b_empty[bprev]);
+            for (int s = 1; s <= g - 1; ++s) {
+              if (!mbar_wait_bounded(&sm.a_full[ra.slot], ra.phase, abort_flag, status)) {
+                ok = false;
+                break;
+              }
+              const int aslot = ra.slot;
+              ra.advance();
+              int bnew = -1;
+              if (s <= g - 2) {
+                if (!mbar_wait_bounded(&sm.b_full[rb.slot], rb.phase, abort_flag, status)) {
+                  ok = false;
+                  break;
+                }
+                bnew = rb.slot;
+                rb.advance();
+              }
+              tc_fence_after();
+              if (x == 0) {
+                // diagonal g: A_s x B_{g-s}
+                if (!acquire()) {
+                  ok = false;
+                  break;
+                }
+                mma8(aslot, bprev);
+                finish(kb == Kt - 1 && s == g - 1);
+                mma_commit(&sm.a_empty[aslot]);
+                mma_commit(&sm.b_empty[bprev]);
+              } else if (pair && s <= g - 2) {
+                // diagonal g-1: A_s x B_{g-1-s}
+                if (!acquire()) {
+                  ok = false;
+                  break;
+                }
+                mma8(aslot, bnew);
+                finish(kb == Kt - 1 && s == g - 2);
+                mma_commit(&sm.a_empty[aslot]);
+                mma_commit(&sm.b_empty[bnew]);
+              } else {
+                mbar_arrive(&sm.a_empty[aslot]);
+                if (bnew >= 0) mbar_arrive(&sm.b_empty[bnew]);
+              }
+              bprev = bnew;
+            }
+          }
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------ epilogue (8 warps)
+    regs_inc_208();
+    const int ew = warp - 4;
+    const int quarter = warp & 3;          // TMEM lanes this warp may access
+    const int half = ew >> 2;              // which 64 columns of the tile
+    const int row_in_tile = quarter * 32 + lane;
+    const uint32_t t_lane = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
+    const double dmax2 = static_cast<double>(((1 << beta) - 1) * ((1 << beta) - 1));
+    int buf0 = 0, buf1 = 0, cnt0 = 0, cnt1 = 0;
+    uint32_t fulls00 = 0u, fulls01 = 0u, fulls10 = 0u, fulls11 = 0u;
+    bool ok = true;
+    int D0[64], D1[64];
+    auto drain = [&](int x, int (&Dx)[64]) {
+      int& b = x ? buf1 : buf0;
+      uint32_t& f = x ? (b ? fulls11 : fulls10) : (b ? fulls01 : fulls00);
+      const int a = 2 * x + b;
+      if (!mbar_wait_bounded(&sm.accfull[a], f & 1u, abort_flag, status)) return false;
+      ++f;
+      tc_fence_after();
+      const uint32_t t_win = t_lane + static_cast<uint32_t>(a * kBN + half * 64);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t r[32];
+        tmem_ld32(t_win + h * 32, r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) Dx[h * 32 + i] += __float2int_rz(__uint_as_float(r[i]));
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.accempty[a]);
+      b ^= 1;
+      return true;
+    };
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const OzTile j = tiles.tile(t);
+      // diagonals g >= gx fold exactly in int64 (see oz_gemm_kernel)
+      int gx = S + 1;
+      {
+        double yb = 0.0;
+        for (int g = S + 1; g >= 2; --g) {
+          yb += (g - 1) * dmax2 * static_cast<double>(kOzTileK) * static_cast<double>(j.Kt) *
+                pow2_normal(beta * (S + 1 - g));
+          if (yb >= 4503599627370496.0) break;  // 2^52
+          gx = g;
+        }
+      }
+      const int64_t row = j.row0 + row_in_tile;
+      const bool row_ok = row < j.m;
+      const int64_t col0 = j.col0 + half * 64;
+      for (int q = 0; q < ngroups && ok; ++q) {
+        const int g = S + 1 - 2 * q;
+        const bool pair = g - 1 >= 2;
+#pragma unroll
+        for (int i = 0; i < 64; ++i) {
+          D0[i] = 0;
+          D1[i] = 0;
+        }
+        for (int64_t kb = 0; kb < j.Kt && ok; ++kb) {
+          for (int s = 1; s <= g - 1; ++s) {
+            if (++cnt0 == window || (kb == j.Kt - 1 && s == g - 1)) {
+              cnt0 = 0;
+              if (!drain(0, D0)) {
+                ok = false;
+                break;
+              }
+            }
+            if (pair && s <= g - 2) {
+              if (++cnt1 == window || (kb == j.Kt - 1 && s == g - 2)) {
+                cnt1 = 0;
+                if (!drain(1, D1)) {
+                  ok = false;
+                  break;
+                }
+              }
+            }
+          }
+        }
+        if (!ok) break;
+        // fold D_g (then D_{g-1}) into the running sum kept in C
+        const bool first = (q == 0);
+        const bool last = (g - (pair ? 1 : 0) == 2);
+        int er = 0;
+        if (last && row_ok) er = exponent_from_absbits(j.rowbits[row]);
+        // the running sums live in the tile's column-major scratch: for each
+        // column the warp's 32 lanes (32 consecutive rows) touch 256
+        // contiguous bytes.  8 columns per step of a rolled loop (the next 8
+        // loaded while these fold); the digit sums are rotated down by 8
+        // after each step so the loop body only names D[0..7]: a compact
+        // loop keeps the kernel inside the instruction caches.
+        uint64_t* tsum = j.sums + static_cast<size_t>(half * 64) * kOzTileRows + row_in_tile;
+        uint64_t cur[8], nxt[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) cur[i] = first ? 0ull : __ldcg(tsum + i * kOzTileRows);
+#pragma unroll 1
+        for (int ch = 0; ch < 8; ++ch) {
+          uint64_t* tch = tsum + static_cast<size_t>(ch * 8) * kOzTileRows;
+          if (ch < 7 && !first) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) nxt[i] = __ldcg(tch + (8 + i) * kOzTileRows);
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            cur[i] = fold_step(cur[i], D0[i], g, gx, S, beta);
+            if (pair) cur[i] = fold_step(cur[i], D1[i], g - 1, gx, S, beta);
+          }
+          if (last) {
+            const int64_t cbase = col0 + ch * 8;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int64_t col = cbase + i;
+              if (row_ok && col < j.n)
+                j.C[row * j.n + col] =
+                    final_scale(cur[i], er + exponent_from_absbits(__ldg(j.colbits + col)));
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) __stcg(tch + i * kOzTileRows, cur[i]);
+          }
+#pragma unroll
+          for (int i = 0; i < 56; ++i) {
+            D0[i] = D0[i + 8];
+            D1[i] = D1[i + 8];
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) cur[i] = first ? 0ull : nxt[i];
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+}
+
 __global__ void zero_fill_kernel(double* __restrict__ C, int64_t count) {
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -822,14 +1222,21 @@ static bool narrow_sums(int S, int beta, int64_t Kt) {
 
 cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
                               const uint64_t* rowbits, const uint64_t* colbits, double* C,
-                              const OzakiDims& d, int* status, cudaStream_t s) {
+                              const OzakiDims& d, uint64_t* sums, int* status, cudaStream_t s) {
   if (d.Mt == 0 || d.Nt == 0) return cudaSuccess;
   const int window = ozaki_window_stages(d.beta);
-  OzSingle tiles{aslices, bslices, rowbits, colbits, C, d.m, d.n, d.Mt, d.Nt, d.Kt};
+  OzSingle tiles{aslices, bslices, rowbits, colbits, C, d.m, d.n, d.Mt, d.Nt, d.Kt, sums};
   const int64_t count = d.Mt * d.Nt;
   const int64_t grid = count < sm_count() ? count : sm_count();
-  if (narrow_sums(d.S, d.beta, d.Kt))
-    return launch_oz_gemm_t<int, false>(tiles, grid, d.S, d.beta, window, status, s);
+  if (narrow_sums(d.S, d.beta, d.Kt)) {
+    auto kern = oz_gemm2_kernel<OzSingle>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kGemm2SmemBytes));
+    if (e != cudaSuccess) return e;
+    kern<<<static_cast<unsigned>(grid), kP2Threads, kGemm2SmemBytes, s>>>(tiles, d.S, d.beta,
+                                                                          window, status);
+    return cudaGetLastError();
+  }
   return launch_oz_gemm_t<long long, false>(tiles, grid, d.S, d.beta, window, status, s);
 }
 
@@ -858,7 +1265,7 @@ cudaError_t launch_bf16_gemm(const double* A, const double* B, double* C, const 
       B, d.k, d.n, 1, d.Kt, bplane);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  OzSingle tiles{aplane, bplane, nullptr, nullptr, C, d.m, d.n, d.Mt, d.Nt, d.Kt};
+  OzSingle tiles{aplane, bplane, nullptr, nullptr, C, d.m, d.n, d.Mt, d.Nt, d.Kt, nullptr};
   const int64_t count = d.Mt * d.Nt;
   const int64_t grid = count < sm_count() ? count : sm_count();
   // one window covers all of k (FP32 accumulation is the mode's semantics)

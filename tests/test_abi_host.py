@@ -71,11 +71,13 @@ def test_workspace_size_is_host_arithmetic():
     # FP64: zero-padded 128x16 tiles of A and B
     assert mxm.mxm_workspace_size(0, 128, 16, 128) == 2 * 128 * 16 * 8
     assert mxm.mxm_workspace_size(0, 0, 16, 128) == 0
-    # emulated: exponents + S slices of 128x64 bf16 tiles of A and of B^T
+    # emulated: exponents + S slices of 128x128 bf16 tiles of A and of B^T
+    # (Mt = 2, Nt = 1, Kt = 1) + a 128x128 FP64 running-sum tile per C tile
     ws = mxm.mxm_workspace_size(1, 256, 128, 128, 7)
-    tiles = 7 * (2 * 2 + 1 * 2)
-    assert ws >= tiles * 128 * 64 * 2
-    assert ws < tiles * 128 * 64 * 2 + 8 * 1024
+    tiles = 7 * (2 * 1 + 1 * 1)
+    sums = 2 * 128 * 128 * 8
+    assert ws >= tiles * 128 * 128 * 2 + sums
+    assert ws < tiles * 128 * 128 * 2 + sums + 8 * 1024
     assert mxm.mxm_workspace_size(1, 256, 128, 128, 0) == 0
 
 
