@@ -60,6 +60,26 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def profiled_traffic():
+    """DRAM bytes per launch of the product kernel from the committed ncu
+    summary, if the kernel sources still hash as they did at capture."""
+    import hashlib
+    import re
+    summary = os.path.join(ROOT, "profiles", "oz_gemm2_n8192_dram.md")
+    if not os.path.exists(summary):
+        return None
+    text = open(summary).read()
+    mt = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
+    mh = re.search(r"kernel_sources_sha256:\s*([0-9a-f]{64})", text)
+    if not mt or not mh:
+        return None
+    h = hashlib.sha256()
+    for rel in ("csrc/ozaki.cu", "csrc/ptx.cuh", "csrc/mxm_internal.h"):
+        with open(os.path.join(ROOT, "paper_1211_1581_gb300", rel), "rb") as fh:
+            h.update(fh.read())
+    return int(mt.group(1)) if h.hexdigest() == mh.group(1) else None
+
+
 def default_slices(kind: str, beta: int) -> int:
     """Smallest slice count meeting 2ku|A||B| at n = 8192 on sampled entries
     of each input kind, found with the oracle on sampled entries."""
@@ -247,7 +267,8 @@ def run_ours(args):
     roofline = {"bound": "tensor", "kernel": "oz_gemm_kernel", "achieved": round(achieved, 1),
                 "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                 "peak_source": f"bf16_tflops_sustained of {peak_src} (MEASURED_PEAKS.json)",
-                "traffic": None,
+                "traffic": profiled_traffic() if (n == 8192 and S == 7) else None,
+                "traffic_unit": "bytes per launch (dram read + write, ncu)",
                 "algorithmic": f"{pairs} digit-pair products x 2mnk bf16 flops per launch",
                 "phase_ms_per_step": {"scale": round(phase_ms[0] / max(calls, 1), 4),
                                       "split": round(phase_ms[1] / max(calls, 1), 4),
