@@ -264,7 +264,7 @@ def run_ours(args):
     gemm_ms = phase_ms[2] / max(calls, 1)
     achieved = pairs * flops / (gemm_ms * 1e-3) / 1e12
     peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-    roofline = {"bound": "tensor", "kernel": "oz_gemm_kernel", "achieved": round(achieved, 1),
+    roofline = {"bound": "tensor", "kernel": "oz_gemm2_kernel", "achieved": round(achieved, 1),
                 "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                 "peak_source": f"bf16_tflops_sustained of {peak_src} (MEASURED_PEAKS.json)",
                 "traffic": profiled_traffic() if (n == 8192 and S == 7) else None,

@@ -762,14 +762,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 // registers to warpgroups 1-2 (the epilogue: two diagonals of exact int32
 // sums).
 constexpr int kP2Threads = 384;
-constexpr int kP2Ring = 3;
+constexpr int kP2RingA = 3;  // an A tile serves one step
+constexpr int kP2RingB = 4;  // a B tile serves two steps: one more slot of look-ahead
 constexpr int kP2EpiWarps = 8;
 
 struct __align__(1024) Gemm2Smem {
-  uint8_t a[kP2Ring][kOzTileBytes];
-  uint8_t b[kP2Ring][kOzTileBytes];
-  uint64_t a_full[kP2Ring], a_empty[kP2Ring];
-  uint64_t b_full[kP2Ring], b_empty[kP2Ring];
+  uint8_t a[kP2RingA][kOzTileBytes];
+  uint8_t b[kP2RingB][kOzTileBytes];
+  uint64_t a_full[kP2RingA], a_empty[kP2RingA];
+  uint64_t b_full[kP2RingB], b_empty[kP2RingB];
   uint64_t accfull[4], accempty[4];  // accumulator 2x + buffer; x = 0: diagonal g, 1: g-1
   uint32_t tmem_base;
   int abort_flag;
@@ -785,12 +786,13 @@ __device__ __forceinline__ void regs_inc_208() {
   asm volatile("setmaxnreg.inc.sync.aligned.u32 208;" ::: "memory");
 }
 
-// One ring of shared-memory slots with full/empty barriers.
+// One ring of N shared-memory slots with full/empty barriers.
+template <int N>
 struct Ring {
   int slot = 0;
   uint32_t phase = 0;
   __device__ __forceinline__ void advance() {
-    if (++slot == kP2Ring) {
+    if (++slot == N) {
       slot = 0;
       phase ^= 1u;
     }
@@ -831,9 +833,11 @@ __global__ void __launch_bounds__(kP2Threads, 1)
   const int lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kP2Ring; ++i) {
+    for (int i = 0; i < kP2RingA; ++i) {
       mbar_init(&sm.a_full[i], 1);
       mbar_init(&sm.a_empty[i], 2);  // one arrival per MMA issuer
+    }
+    for (int i = 0; i < kP2RingB; ++i) {
       mbar_init(&sm.b_full[i], 1);
       mbar_init(&sm.b_empty[i], 2);
     }
@@ -860,9 +864,10 @@ __global__ void __launch_bounds__(kP2Threads, 1)
     regs_dec_80();
     if (warp == 0 && lane == 0) {
       // ------------------------------------------------ producer (bulk copies)
-      Ring ra, rb;
+      Ring<kP2RingA> ra;
+      Ring<kP2RingB> rb;
       bool ok = true;
-      auto load = [&](Ring& r, uint8_t (*buf)[kOzTileBytes], uint64_t* full, uint64_t* empty,
+      auto load = [&](auto& r, uint8_t (*buf)[kOzTileBytes], uint64_t* full, uint64_t* empty,
                       const uint8_t* src) {
         if (!mbar_wait_bounded(&empty[r.slot], r.phase ^ 1u, abort_flag, status)) return false;
         mbar_arrive_expect_tx(&full[r.slot], kOzTileBytes);
@@ -887,11 +892,11 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       }
       // tail: wait until every slot is released so no copy or commit lands
       // after the block has exited
-      for (int i = 0; i < kP2Ring; ++i) {
+      for (int i = 0; i < kP2RingA; ++i) {
         if (!mbar_wait_bounded(&sm.a_empty[ra.slot], ra.phase ^ 1u, abort_flag, status)) break;
         ra.advance();
       }
-      for (int i = 0; i < kP2Ring; ++i) {
+      for (int i = 0; i < kP2RingB; ++i) {
         if (!mbar_wait_bounded(&sm.b_empty[rb.slot], rb.phase ^ 1u, abort_flag, status)) break;
         rb.advance();
       }
@@ -908,7 +913,8 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       const uint32_t idesc = idesc_bf16_f32(128, kBN);
       const uint64_t adesc0 = sw128_kmajor_desc(smem_u32(sm.a[0]));
       const uint64_t bdesc0 = sw128_kmajor_desc(smem_u32(sm.b[0]));
-      Ring ra, rb;
+      Ring<kP2RingA> ra;
+      Ring<kP2RingB> rb;
       int buf = 0, cnt = 0;
       bool acq = false;
       uint32_t uses0 = 0u, uses1 = 0u;  // windows started in this issuer's two buffers
