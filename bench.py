@@ -151,18 +151,26 @@ def dist_setup(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     elif torch.cuda.is_available():
         torch.cuda.set_device(0)
     return world, rank, local
 
 
+def _reduce_device():
+    """Device of the tensors the collectives reduce: CUDA under NCCL, the
+    host under gloo (the CPU multi-process path)."""
+    import torch.distributed as dist
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
 def barrier(world):
     if world > 1:
         import torch
         import torch.distributed as dist
-        t = torch.zeros(1, device="cuda")
+        t = torch.zeros(1, device=_reduce_device())
         dist.all_reduce(t)
 
 
@@ -171,9 +179,24 @@ def max_over_ranks(v, world):
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_operands(kind, n, rank):
+    """The problem rank `rank` multiplies: its own seeded n x n pair (stream
+    configuration 2 + rank), so replicas share no data and need no exchange;
+    rank 0's pair is the single-GPU workload."""
+    from paper_1211_1581_gb300 import inputs
+    return inputs.gemm_operands(kind, n, n, n, seed=0, cfg=2 + rank)
+
+
+def aggregate_rate(world, flops_per_step, steps, ms_max):
+    """Whole-job throughput in TFLOP/s: every rank runs `steps` independent
+    products of `flops_per_step` flops (replicas, weak scaling), and the
+    job takes the slowest rank's time `ms_max`."""
+    return world * flops_per_step * steps / (ms_max * 1e-3) / 1e12
 
 
 # ------------------------------------------------------------------ CPU oracle leg
@@ -220,7 +243,7 @@ def run_ours(args):
     peaks, peak_src = load_peaks()
     mxm.load()
 
-    A_h, B_h = inputs.gemm_operands(args.kind, n, n, n, seed=0, cfg=2 + rank)
+    A_h, B_h = rank_operands(args.kind, n, rank)
     A = torch.from_numpy(A_h).cuda()
     B = torch.from_numpy(B_h).cuda()
     C = torch.empty((n, n), dtype=torch.float64, device="cuda")
@@ -258,7 +281,7 @@ def run_ours(args):
     ms_total = max_over_ranks(ms_total, world)
     ms_step = ms_total / args.steps
     flops = 2.0 * n * n * n
-    value = world * flops * args.steps / (ms_total * 1e-3) / 1e12
+    value = aggregate_rate(world, flops, args.steps, ms_total)
 
     pairs = S * (S + 1) // 2
     gemm_ms = phase_ms[2] / max(calls, 1)
@@ -395,14 +418,11 @@ def run_reference(args):
     """The reference arm: the CPU oracle (the plain definition, naive FP64
     loop with OpenMP over rows) on a bounded band of rows of the same
     workload; rank 0 only."""
-    import numpy as np
-
-    from paper_1211_1581_gb300 import inputs
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     n = args.n
-    A_h, B_h = inputs.gemm_operands(args.kind, n, n, n, seed=0, cfg=2)
+    A_h, B_h = rank_operands(args.kind, n, 0)
     per = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     vals = []
     threads = rows = 0

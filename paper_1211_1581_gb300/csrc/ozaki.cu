@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(256) bf16_tiles_kernel(const double* __restric
 
 // ---------------------------------------------------------------- steps 3-4
 constexpr int kStages = 3;
-constexpr int kThreads = 320;       // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int kThreads = 384;       // warp 0 copies, warp 1 MMA, warps 4..11 epilogue
 constexpr int kEpiWarps = 8;
 constexpr int kBN = 128;            // MMA N (columns of the C tile)
 constexpr uint32_t kTmemCols = 512;
@@ -469,6 +469,27 @@ struct OzGrouped {
   }
 };
 
+// The final scaling of one result, out of line (like fold_step below) to
+// keep the epilogues compact: the instruction caches are small, and code
+// repeated for every element of a tile row overflowed them.
+__device__ __noinline__ double final_scale(uint64_t st, int e) {
+  return ldexp_rn(__longlong_as_double(static_cast<long long>(st)), e);
+}
+
+__device__ __noinline__ uint64_t fold_step(uint64_t st, long long dval, int g, int gx, int S,
+                                           int beta) {
+  if (g >= gx) {
+    long long y = (g == S + 1) ? 0ll : static_cast<long long>(st);
+    y += dval * (1ll << (beta * (S + 1 - g)));
+    if (g == gx)
+      return static_cast<uint64_t>(__double_as_longlong(i64_times_pow2(y, -beta * (S + 1))));
+    return static_cast<uint64_t>(y);
+  }
+  const double acc = __longlong_as_double(static_cast<long long>(st));
+  const double term = i64_times_pow2(dval, -beta * g);  // exact
+  return static_cast<uint64_t>(__double_as_longlong(__dadd_rn(acc, term)));
+}
+
 // Persistent slice GEMM: every CTA walks tiles blockIdx.x, +gridDim.x, ...;
 // the three roles walk the same sequence and keep their pipeline state
 // (stage ring, accumulator double buffer) from one tile to the next, so the
@@ -479,6 +500,15 @@ struct OzGrouped {
 // kFloat (BF16 comparison mode only): one slice of bf16-rounded values, the
 // FP32 accumulator covers all of k in one window and is converted to FP64
 // without scaling.
+// Register split of the 384-thread slice GEMMs (setmaxnreg acts per
+// warpgroup): 384 threads x 168 registers at launch = 128 x 80 (warpgroup 0) + 256 x 208
+__device__ __forceinline__ void regs_dec_80() {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 80;" ::: "memory");
+}
+__device__ __forceinline__ void regs_inc_208() {
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 208;" ::: "memory");
+}
+
 template <typename Acc, bool kFloat, typename Tiles>
 __global__ void __launch_bounds__(kThreads, 1)
     oz_gemm_kernel(const Tiles tiles, int S, int beta, int window, int* __restrict__ status) {
@@ -511,6 +541,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = &sm.abort_flag;
   const int64_t ntiles = tiles.count();
 
+  if (warp < 4) regs_dec_80();  // warps 2, 3 idle
   if (warp == 0) {
     // ------------------------------------------------ producer (bulk copies)
     if (lane == 0) {
@@ -612,9 +643,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-  } else {
+  } else if (warp >= 4) {
     // ------------------------------------------------ epilogue (8 warps)
-    const int ew = warp - 2;
+    regs_inc_208();
+    const int ew = warp - 4;
     const int quarter = warp & 3;          // TMEM lanes this warp may access
     const int half = ew >> 2;              // which 64 columns of the tile
     const int row_in_tile = quarter * 32 + lane;
@@ -676,38 +708,27 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) break;
         const bool first = (g == S + 1);
         const bool last = (g == 2);
-        const bool exact = !kFloat && g >= gx;  // int64 phase
         const int64_t row = j.row0 + row_in_tile;
         int er = 0;
         if (!kFloat && last && row < j.m) er = exponent_from_absbits(j.rowbits[row]);
-#pragma unroll
+        // 8 columns per step of a rolled loop; D is rotated down by 8 after
+        // each step so the body only names D[0..7] (compact code)
+#pragma unroll 1
         for (int ch = 0; ch < 8; ++ch) {
           uint32_t r[16];
           if (!first) {
             tmem_ld16(t_acc + ch * 16, r);
             tmem_wait_ld();
           }
-          double v[8];
+          uint64_t st[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             if constexpr (kFloat) {
-              v[i] = static_cast<double>(D[ch * 8 + i]);
-            } else if (exact) {
-              // Y (int64, units of 2^{-beta (S+1)}) += D_g 2^{beta (S+1-g)}
-              long long y = first ? 0ll
-                                  : static_cast<long long>(
-                                        (static_cast<uint64_t>(r[2 * i + 1]) << 32) | r[2 * i]);
-              y += static_cast<long long>(D[ch * 8 + i]) * (1ll << (beta * (S + 1 - g)));
-              if (g == gx) {
-                v[i] = i64_times_pow2(y, -beta * (S + 1));  // exact: |y| < 2^52
-              } else {
-                r[2 * i] = static_cast<uint32_t>(y);
-                r[2 * i + 1] = static_cast<uint32_t>(static_cast<uint64_t>(y) >> 32);
-              }
+              st[i] = static_cast<uint64_t>(__double_as_longlong(static_cast<double>(D[i])));
             } else {
-              const double prev =
-                  __hiloint2double(static_cast<int>(r[2 * i + 1]), static_cast<int>(r[2 * i]));
-              v[i] = __dadd_rn(prev, i64_times_pow2(static_cast<long long>(D[ch * 8 + i]), -beta * g));
+              const uint64_t prev =
+                  first ? 0ull : ((static_cast<uint64_t>(r[2 * i + 1]) << 32) | r[2 * i]);
+              st[i] = fold_step(prev, static_cast<long long>(D[i]), g, gx, S, beta);
             }
           }
           if (last) {
@@ -719,23 +740,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int64_t col = col0 + i;
                 if (col < j.n) {
                   if constexpr (kFloat)
-                    crow[col] = v[i];
+                    crow[col] = __longlong_as_double(static_cast<long long>(st[i]));
                   else
-                    crow[col] = ldexp_rn(v[i], er + exponent_from_absbits(j.colbits[col]));
+                    crow[col] = final_scale(st[i], er + exponent_from_absbits(j.colbits[col]));
                 }
               }
             }
           } else {
-            if (kFloat || !exact || g == gx) {
 #pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                r[2 * i] = static_cast<uint32_t>(__double2loint(v[i]));
-                r[2 * i + 1] = static_cast<uint32_t>(__double2hiint(v[i]));
-              }
+            for (int i = 0; i < 8; ++i) {
+              r[2 * i] = static_cast<uint32_t>(st[i]);
+              r[2 * i + 1] = static_cast<uint32_t>(st[i] >> 32);
             }
             tmem_st16(t_acc + ch * 16, r);
             tmem_wait_st();
           }
+#pragma unroll
+          for (int i = 0; i < 56; ++i) D[i] = D[i + 8];
         }
       }
     }
@@ -778,14 +799,6 @@ struct __align__(1024) Gemm2Smem {
 
 constexpr size_t kGemm2SmemBytes = sizeof(Gemm2Smem) + 1024;
 
-// 384 threads x 168 registers at launch = 128 x 80 (warpgroup 0) + 256 x 208
-__device__ __forceinline__ void regs_dec_80() {
-  asm volatile("setmaxnreg.dec.sync.aligned.u32 80;" ::: "memory");
-}
-__device__ __forceinline__ void regs_inc_208() {
-  asm volatile("setmaxnreg.inc.sync.aligned.u32 208;" ::: "memory");
-}
-
 // One ring of N shared-memory slots with full/empty barriers.
 template <int N>
 struct Ring {
@@ -801,28 +814,6 @@ struct Ring {
 
 // The fold of one diagonal g into a running sum held as 64 bits: an exact
 // int64 partial (units of 2^{-beta (S+1)}) while g >= gx, an FP64 value after.
-// The final scaling of one result, out of line for the same reason as
-// fold_step below.
-__device__ __noinline__ double final_scale(uint64_t st, int e) {
-  return ldexp_rn(__longlong_as_double(static_cast<long long>(st)), e);
-}
-
-// Out of line on purpose: inlined into the 128 call sites of the epilogue
-// it made the kernel's code far larger than the instruction caches.
-__device__ __noinline__ uint64_t fold_step(uint64_t st, int dval, int g, int gx, int S,
-                                           int beta) {
-  if (g >= gx) {
-    long long y = (g == S + 1) ? 0ll : static_cast<long long>(st);
-    y += static_cast<long long>(dval) * (1ll << (beta * (S + 1 - g)));
-    if (g == gx)
-      return static_cast<uint64_t>(__double_as_longlong(i64_times_pow2(y, -beta * (S + 1))));
-    return static_cast<uint64_t>(y);
-  }
-  const double acc = __longlong_as_double(static_cast<long long>(st));
-  const double term = i64_times_pow2(static_cast<long long>(dval), -beta * g);  // exact
-  return static_cast<uint64_t>(__double_as_longlong(__dadd_rn(acc, term)));
-}
-
 template <typename Tiles>
 __global__ void __launch_bounds__(kP2Threads, 1)
     oz_gemm2_kernel(const Tiles tiles, int S, int beta, int window, int* __restrict__ status) {

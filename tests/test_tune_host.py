@@ -1,0 +1,74 @@
+"""Host logic of the engine / slice-count tuner (no GPU): the scan, the
+choice and the JSON cache."""
+import json
+
+import pytest
+
+from paper_1211_1581_gb300 import mxm, tune
+
+
+def fake_measure(need, cost, calls):
+    """err_ratio falls by 2^7 per slice and reaches tol at `need[mode]`
+    slices; time = cost[mode] * pairs (native FP64: a fixed cost)."""
+    def measure(mode, s):
+        calls.append((mode, s))
+        if mode == mxm.MODE_F64:
+            return 0.5, cost[mode]
+        err = 2.0 ** (7 * (need[mode] - s))
+        return err, cost[mode] * s * (s + 1) / 2
+    return measure
+
+
+def test_select_fastest_accurate():
+    calls = []
+    m = fake_measure({mxm.MODE_EMUL_I8: 7, mxm.MODE_EMUL_BF16: 6},
+                     {mxm.MODE_F64: 100.0, mxm.MODE_EMUL_I8: 1.0, mxm.MODE_EMUL_BF16: 1.5}, calls)
+    c = tune.select(m, tol=1.0)
+    # i8: 28 pairs x 1.0 = 28; bf16: 21 pairs x 1.5 = 31.5; f64 100
+    assert (c.mode, c.slices, c.ms) == (mxm.MODE_EMUL_I8, 7, 28.0)
+    # each emulated scan stopped at its first accurate count
+    assert [s for (mo, s) in calls if mo == mxm.MODE_EMUL_I8] == list(range(1, 8))
+    assert [s for (mo, s) in calls if mo == mxm.MODE_EMUL_BF16] == list(range(1, 7))
+    assert len(c.measured) == len(calls)
+
+
+def test_select_native_wins_when_faster():
+    calls = []
+    m = fake_measure({mxm.MODE_EMUL_I8: 9, mxm.MODE_EMUL_BF16: 8},
+                     {mxm.MODE_F64: 20.0, mxm.MODE_EMUL_I8: 1.0, mxm.MODE_EMUL_BF16: 1.0}, calls)
+    c = tune.select(m, tol=1.0)
+    assert (c.mode, c.slices) == (mxm.MODE_F64, 0) and c.name == "f64"
+
+
+def test_select_tolerance_moves_the_count():
+    m = fake_measure({mxm.MODE_EMUL_I8: 7, mxm.MODE_EMUL_BF16: 6},
+                     {mxm.MODE_F64: 1e9, mxm.MODE_EMUL_I8: 1.0, mxm.MODE_EMUL_BF16: 9.0}, [])
+    assert tune.select(m, tol=1.0).slices == 7
+    assert tune.select(m, tol=2.0 ** 7).slices == 6  # one slice fewer is 2^7 worse
+
+
+def test_select_raises_when_nothing_is_accurate():
+    def never(mode, s):
+        return float("inf"), 1.0
+    with pytest.raises(RuntimeError):
+        tune.select(never, tol=1.0, max_slices=3)
+
+
+def test_shape_class_and_key():
+    assert tune.shape_class(8192, 8192, 8192) == "m13k13n13"
+    assert tune.shape_class(8193, 1, 1000) == "m14k0n10"
+    assert tune.shape_class(0, 2, 3) == "m0k1n2"
+    assert tune.cache_key("GB300", "spread", 100, 200, 300, 1.0) == "GB300|spread|m7k8n9|tol=1"
+
+
+def test_cache_round_trip(tmp_path):
+    path = tmp_path / "sub" / "tune.json"
+    c = tune.TuneCache(str(path))
+    assert c.get("x") is None
+    choice = tune.Choice(mode=mxm.MODE_EMUL_I8, slices=7, ms=21.5, err_ratio=0.01,
+                         measured=[[1, 7, 0.01, 21.5]])
+    c.put("x", choice)
+    again = tune.TuneCache(str(path))
+    assert again.get("x") == choice
+    assert json.loads(path.read_text())["x"]["slices"] == 7
+    assert [p.name for p in path.parent.iterdir()] == ["tune.json"]  # no temporary left
