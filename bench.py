@@ -49,6 +49,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-check", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--suite", action="store_true",
+                   help="instead of the benchmark line: one JSON line per case of the "
+                        "workload suite (FP64 sweep, slice counts and modes, rectangular "
+                        "shapes, grouped batch under a CUDA graph)")
     return p.parse_args()
 
 
@@ -297,20 +301,17 @@ def run_ours(args):
                                       "split": round(phase_ms[1] / max(calls, 1), 4),
                                       "product": round(gemm_ms, 4)}}
 
-    # ---- accuracy on sampled entries (oracle, CPU)
+    # ---- accuracy of the last timed result, every entry, on the device:
+    # against the 12-slice 8-bit-digit split, in units of k u (|A||B|)_ij
     check = None
     if not args.no_check and rank == 0:
-        import oracle
-        rng = np.random.default_rng(1)
-        ii = rng.integers(0, n, 128)
-        jj = rng.integers(0, n, 128)
-        got = C.cpu().numpy()[ii, jj]
-        ref_emul = oracle.ozaki_entries(A_h, B_h, ii, jj, S=S, beta=beta)
-        d2, ab = oracle.entries_dot2_abs(A_h, B_h, ii, jj)
-        ratio = float(np.max(np.abs(got - d2) / (2 * n * U * ab)))
-        check = {"entries": int(ii.size), "bit_identical_to_oracle_emulation":
-                 bool(np.array_equal(got, ref_emul)), "max_err_over_2ku_AB": ratio,
-                 "max_rel_err_vs_dot2": float(np.max(np.abs(got - d2) / np.abs(d2)))}
+        from paper_1211_1581_gb300 import tune
+        ref, bnd = tune.accuracy_reference(A, B, stream)
+        check = {"entries": n * n, "max_err_over_ku_AB": tune.error_ratio(C, ref, bnd),
+                 "reference": "12-slice 8-bit-digit split (truncation 2^-96 below the row and "
+                              "column maxima); |A||B| by the native FP64 product"}
+        del ref, bnd
+        torch.cuda.empty_cache()
 
     # ---- other modes at the same size
     modes = {}
@@ -414,6 +415,116 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ workload suite
+def _timed_ms(fn, reps, stream):
+    """Mean device time of ``fn`` over ``reps`` runs after one warm-up run,
+    CUDA events on ``stream``."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_suite(args):
+    """The workload suite: every case prints one JSON line with its time,
+    FP64-equivalent TFLOP/s (2mnk/t) and error in units of k u (|A||B|)_ij
+    against the 12-slice 8-bit-digit split (all entries)."""
+    import numpy as np
+    import torch
+
+    from paper_1211_1581_gb300 import inputs, mxm, tune
+    torch.cuda.set_device(0)
+    mxm.load()
+    stream = torch.cuda.current_stream()
+    dmma = mxm.mxm_peak_probe(1)
+    peaks, _ = load_peaks()
+    names = {mxm.MODE_F64: "f64", mxm.MODE_EMUL_I8: "emul_i8", mxm.MODE_EMUL_BF16: "emul_bf16",
+             mxm.MODE_F32: "f32", mxm.MODE_BF16_F32ACC: "bf16_f32acc"}
+
+    def emit(**d):
+        print(json.dumps(dict(suite=True, **d)), flush=True)
+
+    def one(case, kind, m, k, n, runs, reps=3, seed=0, cfg=2, tuned=False):
+        A_h, B_h = inputs.gemm_operands(kind, m, k, n, seed=seed, cfg=cfg)
+        A = torch.from_numpy(A_h).cuda()
+        B = torch.from_numpy(B_h).cuda()
+        C = torch.empty((m, n), dtype=torch.float64, device="cuda")
+        ref, bnd = tune.accuracy_reference(A, B, stream)
+        flops = 2.0 * m * n * k
+        for mode, S in runs:
+            ms = _timed_ms(lambda: tune._run(mode, S, A, B, C, stream), reps, stream)
+            st = mxm.mxm_get_device_status()
+            d = {"case": case, "inputs": kind, "m": m, "k": k, "n": n, "mode": names[mode],
+                 "slices": S or None, "ms": round(ms, 4),
+                 "tflops": round(flops / (ms * 1e-3) / 1e12, 3),
+                 "err_over_ku_AB": tune.error_ratio(C, ref, bnd), "status": st}
+            if mode == mxm.MODE_F64:
+                d["frac_of_dmma_probe"] = round(flops / (ms * 1e-3) / 1e12 / dmma, 4)
+            emit(**d)
+        if tuned:
+            with tempfile.TemporaryDirectory() as td:
+                c = tune.tune(A, B, tag=kind, cache=tune.TuneCache(os.path.join(td, "t.json")))
+            emit(case=case, inputs=kind, m=m, k=k, n=n, tuner_choice=c.name,
+                 slices=c.slices or None, ms=round(c.ms, 4), err_over_ku_AB=c.err_ratio)
+        del A, B, C, ref, bnd
+        torch.cuda.empty_cache()
+
+    # native FP64 sweep (uniform entries), against the measured DMMA rate
+    for n in (1024, 2048, 4096, 8192, 16384):
+        one("f64_sweep", "uniform", n, n, n, [(mxm.MODE_F64, 0)], reps=3 if n <= 4096 else 1)
+    # emulated FP64 per slice count, with the comparison modes beside it
+    for n in (4096, 8192):
+        runs = ([(mxm.MODE_EMUL_I8, S) for S in range(5, 10)] +
+                [(mxm.MODE_EMUL_BF16, S) for S in range(4, 9)] +
+                [(mxm.MODE_F32, 0), (mxm.MODE_BF16_F32ACC, 0), (mxm.MODE_F64, 0)])
+        one("emul_slices", "spread", n, n, n, runs, reps=3 if n == 4096 else 2)
+    # rectangular shapes, both engines and the tuner's choice
+    for (m, k, n) in ((16384, 256, 16384), (128, 65536, 128), (32768, 1024, 64)):
+        one("rectangular", "uniform", m, k, n,
+            [(mxm.MODE_F64, 0), (mxm.MODE_EMUL_I8, 6), (mxm.MODE_EMUL_BF16, 5)], tuned=True)
+    # grouped: 2000 problems, m, k, n log-uniform in [16, 1024], one launch
+    # sequence captured in a CUDA graph and replayed
+    dims = [tuple(int(v) for v in d) for d in inputs.grouped_problems(0, 2000)]
+    ds = []
+    for p, (m, k, n) in enumerate(dims):
+        A_h, B_h = inputs.gemm_operands("uniform", m, k, n, seed=0, cfg=100 + p)
+        ds.append((torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda(),
+                   torch.empty((m, n), dtype=torch.float64, device="cuda")))
+    flops = sum(2.0 * m * k * n for m, k, n in dims)
+    big = max(range(len(dims)), key=lambda p: dims[p][0] * dims[p][1] * dims[p][2])
+    with tempfile.TemporaryDirectory() as td:
+        c = tune.tune(ds[big][0], ds[big][1], tag="uniform",
+                      cache=tune.TuneCache(os.path.join(td, "t.json")))
+    s_i8 = [r for r in c.measured if r[0] == mxm.MODE_EMUL_I8][-1][1]
+    table_h = mxm.problem_table(ds)
+    table_d = table_h.cuda()
+    check = np.random.default_rng(5).choice(len(dims), 24, replace=False)
+    refs = [tune.accuracy_reference(ds[p][0], ds[p][1], stream) for p in check]
+    for mode, S in ((mxm.MODE_F64, 0), (mxm.MODE_EMUL_I8, s_i8)):
+        ws = torch.empty(max(1, mxm.mxm_grouped_workspace_size(table_h, mode, S)),
+                         dtype=torch.uint8, device="cuda")
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            mxm.mxm_grouped(table_d, mode, S, ws, stream=side)
+        ms = _timed_ms(g.replay, 3, stream)
+        st = mxm.mxm_get_device_status()
+        err = max(tune.error_ratio(ds[p][2], r, b) for p, (r, b) in zip(check, refs))
+        emit(case="grouped", inputs="uniform", problems=len(dims), mode=names[mode],
+             slices=S or None, slices_from="tuner scan on the largest problem" if S else None,
+             ms=round(ms, 4), tflops=round(flops / (ms * 1e-3) / 1e12, 3),
+             err_over_ku_AB_24_checked=err, status=st, graph=True)
+        del ws, g
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle (the plain definition, naive FP64
     loop with OpenMP over rows) on a bounded band of rows of the same
@@ -453,6 +564,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.suite:
+        run_suite(args)
     else:
         run_ours(args)
 

@@ -120,10 +120,10 @@ def _run(mode, slices, A, B, C, stream):
         mxm.mxm_gemm(mode, A, B, C, slices=slices, stream=stream)
 
 
-def device_measure(A, B, reps: int = 3, stream=None):
-    """The measuring function ``select`` calls, on the GPU: error ratio
-    against the 12-slice 8-bit-digit split, time by CUDA events on
-    ``stream`` (median of ``reps`` after one warm-up run)."""
+def accuracy_reference(A, B, stream=None):
+    """(ref, bound): the 12-slice 8-bit-digit split of A.B and the
+    classical FP64 bound k u (|A||B|)_ij (|A||B| by the native FP64
+    product of |A| and |B|), both on the device."""
     import torch
     stream = stream or torch.cuda.current_stream()
     m, k = A.shape
@@ -132,7 +132,26 @@ def device_measure(A, B, reps: int = 3, stream=None):
     _run(REFERENCE[0], REFERENCE[1], A, B, ref, stream)
     absprod = torch.empty_like(ref)
     mxm.mxm_f64(A.abs(), B.abs(), absprod, stream=stream)
-    bound = (max(k, 1) * U) * absprod
+    return ref, (max(k, 1) * U) * absprod
+
+
+def error_ratio(C, ref, bound) -> float:
+    """max_ij |C - ref|_ij / bound_ij; where the bound is 0 (an exactly
+    zero |A||B| entry) anything but equality is an infinite ratio."""
+    diff = (C - ref).abs()
+    zero = bound == 0
+    if bool((diff[zero] != 0).any()):
+        return math.inf
+    return (diff[~zero] / bound[~zero]).max().item() if bool((~zero).any()) else 0.0
+
+
+def device_measure(A, B, reps: int = 3, stream=None):
+    """The measuring function ``select`` calls, on the GPU: error ratio
+    against the 12-slice 8-bit-digit split, time by CUDA events on
+    ``stream`` (median of ``reps`` after one warm-up run)."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    ref, bound = accuracy_reference(A, B, stream)
     C = torch.empty_like(ref)
 
     def measure(mode, slices):
@@ -149,13 +168,7 @@ def device_measure(A, B, reps: int = 3, stream=None):
         st = mxm.mxm_get_device_status(stream)
         if st != mxm.MXM_OK:
             raise mxm.MxmError(st, "tune")
-        diff = (C - ref).abs()
-        exact_zero = bound == 0
-        if bool((diff[exact_zero] != 0).any()):
-            return math.inf, sorted(times)[len(times) // 2]
-        ratio = (diff[~exact_zero] / bound[~exact_zero]).max().item() if bool(
-            (~exact_zero).any()) else 0.0
-        return ratio, sorted(times)[len(times) // 2]
+        return error_ratio(C, ref, bound), sorted(times)[len(times) // 2]
 
     return measure
 
