@@ -142,7 +142,8 @@ int mode_beta(int mode) { return mode == MXM_MODE_EMUL_BF16 ? 8 : 7; }
 size_t workspace_bytes(int mode, int64_t m, int64_t k, int64_t n, int slices) {
   if (m <= 0 || n <= 0 || k <= 0) return 0;
   if (mode == MXM_MODE_F64) return f64_workspace(f64_dims(m, k, n));
-  if (emul_mode(mode)) return ozaki_layout(ozaki_dims(m, k, n, slices, mode_beta(mode))).total;
+  if (emul_mode(mode))
+    return ozaki_layout(ozaki_dims_splitk(m, k, n, slices, mode_beta(mode))).total;
   if (mode == MXM_MODE_BF16_F32ACC) return ozaki_layout(ozaki_dims(m, k, n, 1, 8)).total;
   return 0;
 }
@@ -162,7 +163,7 @@ mxm_status run_gemm(int mode, const double* A, const double* B, double* C, int64
     if (e == cudaSuccess) e = launch_f64_gemm(ws, C, d, status, s);
     profile_mark(ce, 3, s);
   } else if (emul_mode(mode)) {
-    const OzakiDims d = ozaki_dims(m, k, n, slices, mode_beta(mode));
+    const OzakiDims d = ozaki_dims_splitk(m, k, n, slices, mode_beta(mode));
     const OzakiLayout L = ozaki_layout(d);
     uint64_t* rowbits = reinterpret_cast<uint64_t*>(ws + L.rowbits);
     uint64_t* colbits = reinterpret_cast<uint64_t*>(ws + L.colbits);

@@ -124,26 +124,51 @@ __device__ __forceinline__ void tile_coords(int64_t tile, int64_t Mt, int64_t Nt
 }
 
 struct F64Tile {
-  const double* a;   // packed A tile-row, k-block 0
-  const double* b;   // packed B^T tile-row, k-block 0
-  int64_t Kt;
-  double* C;
-  int64_t m, n, row0, col0;
+  const double* a;   // packed A tile-row, first k-block of this unit
+  const double* b;   // packed B^T tile-row, first k-block of this unit
+  int64_t Kt;        // k-blocks of this unit
+  double* C;         // output (C, or a partial tile under split-k)
+  int64_t m, n, ldc, row0, col0;
 };
 
+// Work unit t: C tile t / splits, k range t % splits (consecutive CTAs take
+// the k ranges of one tile).  Without split-k the unit writes C with edge
+// masks; with it, a full 128 x 128 partial tile (the packed operands are
+// zero-padded, so the padding rows and columns are zeros).
 struct F64Single {
   const double* apack;
   const double* bpack;
   double* C;
-  int64_t m, n, Mt, Nt, Kt;
-  __device__ __forceinline__ int64_t count() const { return Mt * Nt; }
+  double* partials;
+  int64_t m, n, Mt, Nt, Kt, splits;
+  __device__ __forceinline__ int64_t count() const { return Mt * Nt * splits; }
   __device__ __forceinline__ F64Tile tile(int64_t t) const {
+    const int64_t tile = t / splits, sp = t - tile * splits;
     int64_t tm, tn;
-    tile_coords(t, Mt, Nt, tm, tn);
-    return F64Tile{apack + tm * Kt * (BM * BK), bpack + tn * Kt * (BN * BK), Kt, C, m, n,
-                   tm * BM, tn * BN};
+    tile_coords(tile, Mt, Nt, tm, tn);
+    const int64_t kb0 = Kt * sp / splits, kb1 = Kt * (sp + 1) / splits;
+    const double* a = apack + (tm * Kt + kb0) * (BM * BK);
+    const double* b = bpack + (tn * Kt + kb0) * (BN * BK);
+    if (splits == 1) return F64Tile{a, b, kb1 - kb0, C, m, n, n, tm * BM, tn * BN};
+    double* p = partials + ((sp * Mt + tm) * Nt + tn) * (BM * BN);
+    return F64Tile{a, b, kb1 - kb0, p, BM, BN, BN, 0, 0};
   }
 };
+
+// C[row][col] = sum over splits s (in order) of the partial tiles.
+__global__ void __launch_bounds__(256) f64_splitk_reduce_kernel(const double* __restrict__ P,
+                                                                double* __restrict__ C,
+                                                                int64_t m, int64_t n, int64_t Mt,
+                                                                int64_t Nt, int64_t splits) {
+  const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= m * n) return;
+  const int64_t row = idx / n, col = idx - (idx / n) * n;
+  const int64_t off = ((row / BM) * Nt + col / BN) * (BM * BN) + (row % BM) * BN + col % BN;
+  const int64_t stride = Mt * Nt * (BM * BN);
+  double acc = 0.0;
+  for (int64_t s = 0; s < splits; ++s) acc += __ldcs(P + s * stride + off);
+  C[idx] = acc;
+}
 
 struct F64Grouped {
   const uint8_t* ws;
@@ -160,7 +185,7 @@ struct F64Grouped {
     const double* apack = reinterpret_cast<const double*>(ws + hdr->off_a);
     const double* bpack = reinterpret_cast<const double*>(ws + hdr->off_b);
     return F64Tile{apack + (p.atile_begin + tm * p.Kt) * (BM * BK),
-                   bpack + (p.btile_begin + tn * p.Kt) * (BN * BK), p.Kt, p.C, p.m, p.n,
+                   bpack + (p.btile_begin + tn * p.Kt) * (BN * BK), p.Kt, p.C, p.m, p.n, p.n,
                    tm * BM, tn * BN};
   }
 };
@@ -277,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int half = 0; half < 2; ++half) {
         const int64_t row = j.row0 + wm * 32 + mi * 16 + g + half * 8;
         if (row >= j.m) continue;
-        double* crow = j.C + row * j.n;
+        double* crow = j.C + row * j.ldc;
 #pragma unroll
         for (int ni = 0; ni < 8; ++ni) {
           const int64_t col = j.col0 + wn * 64 + ni * 8 + 2 * t4;
@@ -319,15 +344,21 @@ static cudaError_t launch_f64_gemm_t(const Tiles& tiles, int64_t grid, int* stat
   return cudaGetLastError();
 }
 
-cudaError_t launch_f64_gemm(const uint8_t* ws, double* C, const F64Dims& d, int* status,
+cudaError_t launch_f64_gemm(uint8_t* ws, double* C, const F64Dims& d, int* status,
                             cudaStream_t s) {
   if (d.Mt == 0 || d.Nt == 0) return cudaSuccess;
   const double* apack = reinterpret_cast<const double*>(ws);
   const double* bpack = apack + d.Mt * d.Kt * (BM * BK);
-  F64Single tiles{apack, bpack, C, d.m, d.n, d.Mt, d.Nt, d.Kt};
-  const int64_t count = d.Mt * d.Nt;
+  double* partials = reinterpret_cast<double*>(ws + f64_partials_offset(d));
+  F64Single tiles{apack, bpack, C, partials, d.m, d.n, d.Mt, d.Nt, d.Kt, d.splits};
+  const int64_t count = d.Mt * d.Nt * d.splits;
   const int64_t grid = count < sm_count() ? count : sm_count();
-  return launch_f64_gemm_t(tiles, grid, status, s);
+  cudaError_t e = launch_f64_gemm_t(tiles, grid, status, s);
+  if (e != cudaSuccess || d.splits == 1) return e;
+  const int64_t total = d.m * d.n;
+  f64_splitk_reduce_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
+      partials, C, d.m, d.n, d.Mt, d.Nt, d.splits);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_f64_grouped(uint8_t* ws, int* status, cudaStream_t s) {

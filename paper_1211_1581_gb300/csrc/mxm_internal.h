@@ -17,6 +17,23 @@ constexpr int kStatusBounds = 8;
 // Every bounded wait inside a kernel gives up after this long.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 
+// Split-k for products with fewer C tiles than SMs: the k-blocks of every
+// tile are cut into `splits` contiguous ranges, each computed by its own
+// CTA into a partial tile; a second kernel adds the partials in split order
+// (a fixed order: the result does not depend on timing).  The number of
+// work units aimed at is a constant (two per SM of a 152-SM GB300), not the
+// device's SM count, so that a product's rounding does not depend on the
+// device it runs on; every range keeps at least `min_blocks` k-blocks.
+constexpr int64_t kSplitKUnits = 304;
+
+inline int64_t splitk_count(int64_t tiles, int64_t Kt, int64_t min_blocks) {
+  if (tiles <= 0 || tiles >= kSplitKUnits / 2) return 1;
+  int64_t s = kSplitKUnits / tiles;
+  const int64_t cap = Kt / min_blocks;
+  if (s > cap) s = cap;
+  return s > 1 ? s : 1;
+}
+
 // ---------------------------------------------------------------- Ozaki
 // Operand tiles of the slice GEMM: 128 rows x 128 bf16, 32 KiB, stored
 // pre-swizzled so that one bulk copy moves a tile into shared memory in the
@@ -39,8 +56,9 @@ constexpr int kOzMaxSlices = 12;
 
 struct OzakiDims {
   int64_t m, k, n;
-  int64_t Mt, Nt, Kt;  // tiles of 128 rows of A, 128 columns of B, 64 of k
+  int64_t Mt, Nt, Kt;  // tiles of 128 rows of A, 128 columns of B, 128 of k
   int S, beta;
+  int64_t splits;      // k ranges per C tile (1: no split-k)
 };
 
 inline OzakiDims ozaki_dims(int64_t m, int64_t k, int64_t n, int S, int beta) {
@@ -50,6 +68,17 @@ inline OzakiDims ozaki_dims(int64_t m, int64_t k, int64_t n, int S, int beta) {
   d.Nt = (n + kOzTileRows - 1) / kOzTileRows;
   d.Kt = (k + kOzTileK - 1) / kOzTileK;
   d.S = S; d.beta = beta;
+  d.splits = 1;
+  return d;
+}
+
+// The same with split-k where the product has fewer C tiles than SMs (each
+// k range at least 4 k-blocks of 128): the per-range digit-pair sums D_g
+// are exact integers, added exactly, so the result is bit-identical to the
+// unsplit product.
+inline OzakiDims ozaki_dims_splitk(int64_t m, int64_t k, int64_t n, int S, int beta) {
+  OzakiDims d = ozaki_dims(m, k, n, S, beta);
+  d.splits = splitk_count(d.Mt * d.Nt, d.Kt, 4);
   return d;
 }
 
@@ -69,8 +98,14 @@ inline OzakiLayout ozaki_layout(const OzakiDims& d) {
   L.bslices = off; off = align_up(off + (size_t)d.S * d.Nt * d.Kt * kOzTileBytes, 1024);
   // running sums of the recombination between diagonal pairs: per C tile
   // 128 x 128 x 8 bytes, column-major inside the tile (so that a warp, which
-  // owns 32 consecutive rows, touches 256 contiguous bytes per column)
-  L.sums = off; off = align_up(off + (size_t)d.Mt * d.Nt * kOzTileRows * kOzTileRows * 8, 1024);
+  // owns 32 consecutive rows, touches 256 contiguous bytes per column).
+  // Under split-k the region holds instead the int64 partial sums D_g of
+  // every k range: [splits][Mt x Nt tiles][S diagonals] x 128 x 128,
+  // column-major inside the tile.
+  const size_t tile8 = (size_t)kOzTileRows * kOzTileRows * 8;
+  const size_t sums = d.splits > 1 ? (size_t)d.splits * d.Mt * d.Nt * d.S * tile8
+                                   : (size_t)d.Mt * d.Nt * tile8;
+  L.sums = off; off = align_up(off + sums, 1024);
   L.total = off;
   return L;
 }
@@ -105,6 +140,7 @@ constexpr int kF64TileBytes = kF64BM * kF64BK * 8;  // 16 KiB (BM == BN)
 
 struct F64Dims {
   int64_t m, k, n, Mt, Nt, Kt;
+  int64_t splits;  // k ranges per C tile (1: no split)
 };
 
 inline F64Dims f64_dims(int64_t m, int64_t k, int64_t n) {
@@ -113,16 +149,24 @@ inline F64Dims f64_dims(int64_t m, int64_t k, int64_t n) {
   d.Mt = (m + kF64BM - 1) / kF64BM;
   d.Nt = (n + kF64BN - 1) / kF64BN;
   d.Kt = (k + kF64BK - 1) / kF64BK;
+  d.splits = splitk_count(d.Mt * d.Nt, d.Kt, 8);
   return d;
 }
 
-inline size_t f64_workspace(const F64Dims& d) {
+// Packed operand tiles, then (split-k only) the partial C tiles:
+// splits x Mt x Nt tiles of 128 x 128 doubles, row-major inside a tile.
+inline size_t f64_partials_offset(const F64Dims& d) {
   return align_up((size_t)(d.Mt + d.Nt) * d.Kt * kF64TileBytes, 1024);
+}
+inline size_t f64_workspace(const F64Dims& d) {
+  const size_t partials =
+      d.splits > 1 ? (size_t)d.splits * d.Mt * d.Nt * kF64BM * kF64BN * sizeof(double) : 0;
+  return align_up(f64_partials_offset(d) + partials, 1024);
 }
 
 cudaError_t launch_f64_pack(const double* A, const double* B, const F64Dims& d, uint8_t* ws,
                             cudaStream_t s);
-cudaError_t launch_f64_gemm(const uint8_t* ws, double* C, const F64Dims& d, int* status,
+cudaError_t launch_f64_gemm(uint8_t* ws, double* C, const F64Dims& d, int* status,
                             cudaStream_t s);
 
 cudaError_t launch_zero_fill(double* C, int64_t count, cudaStream_t s);

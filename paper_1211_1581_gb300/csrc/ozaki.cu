@@ -404,6 +404,7 @@ struct OzTile {
   int64_t m, n;              // C is m x n, row-major
   int64_t row0, col0;        // origin of the tile in C
   uint64_t* sums;            // 128 x 128 running sums, column-major (paired kernel)
+  uint64_t* partial;         // split-k: this range's D_g, [S - 1 diagonals][128 x 128]
 };
 
 // Tiles of one product.
@@ -414,17 +415,22 @@ struct OzSingle {
   const uint64_t* colbits;
   double* C;
   int64_t m, n, Mt, Nt, Kt;
-  uint64_t* sums;
-  __device__ __forceinline__ int64_t count() const { return Mt * Nt; }
+  uint64_t* sums;     // running sums (paired kernel), or the split-k partials
+  int64_t splits;     // k ranges per C tile; > 1: units write partials
+  int S;
+  __device__ __forceinline__ int64_t count() const { return Mt * Nt * splits; }
+  // Unit t: C tile t / splits, k range t % splits.
   __device__ __forceinline__ OzTile tile(int64_t t) const {
+    const int64_t tt = t / splits, sp = t - tt * splits;
     int64_t tm, tn;
-    tile_coords(t, Mt, Nt, tm, tn);
+    tile_coords(tt, Mt, Nt, tm, tn);
+    const int64_t kb0 = Kt * sp / splits, kb1 = Kt * (sp + 1) / splits;
     OzTile j;
     j.a_slice = static_cast<size_t>(Mt) * Kt * kOzTileBytes;
     j.b_slice = static_cast<size_t>(Nt) * Kt * kOzTileBytes;
-    j.a = aslices + static_cast<size_t>(tm) * Kt * kOzTileBytes;
-    j.b = bslices + static_cast<size_t>(tn) * Kt * kOzTileBytes;
-    j.Kt = Kt;
+    j.a = aslices + static_cast<size_t>(tm * Kt + kb0) * kOzTileBytes;
+    j.b = bslices + static_cast<size_t>(tn * Kt + kb0) * kOzTileBytes;
+    j.Kt = kb1 - kb0;
     j.rowbits = rowbits;
     j.colbits = colbits;
     j.C = C;
@@ -432,8 +438,14 @@ struct OzSingle {
     j.n = n;
     j.row0 = tm * kOzTileRows;
     j.col0 = tn * kOzTileRows;
-    j.sums = sums ? sums + static_cast<size_t>(tm * Nt + tn) * (kOzTileRows * kOzTileRows)
-                  : nullptr;
+    const size_t tile_words = kOzTileRows * kOzTileRows;
+    if (splits > 1) {
+      j.sums = nullptr;
+      j.partial = sums + (static_cast<size_t>(sp * Mt + tm) * Nt + tn) * S * tile_words;
+    } else {
+      j.sums = sums ? sums + static_cast<size_t>(tm * Nt + tn) * tile_words : nullptr;
+      j.partial = nullptr;
+    }
     return j;
   }
 };
@@ -465,9 +477,28 @@ struct OzGrouped {
     j.row0 = tm * kOzTileRows;
     j.col0 = tn * kOzTileRows;
     j.sums = nullptr;
+    j.partial = nullptr;
     return j;
   }
 };
+
+// First diagonal of the FP64 phase of the fold: diagonals g >= the returned
+// value are combined exactly in int64 (the partial sum
+// Y = sum_g D_g 2^{beta (S+1-g)} stays below 2^52 by the bound
+// |D_g| <= (g-1)(2^beta-1)^2 128 Kt, so the FP64 fold of those steps is
+// exact and doing them in integers gives the same bits).
+__device__ __forceinline__ int oz_exact_from(int S, int beta, int64_t Kt) {
+  const double dmax = static_cast<double>((1 << beta) - 1);
+  int gx = S + 1;
+  double yb = 0.0;
+  for (int g = S + 1; g >= 2; --g) {
+    yb += (g - 1) * dmax * dmax * static_cast<double>(kOzTileK) * static_cast<double>(Kt) *
+          pow2_normal(beta * (S + 1 - g));
+    if (yb >= 4503599627370496.0) break;  // 2^52
+    gx = g;
+  }
+  return gx;
+}
 
 // The final scaling of one result, out of line (like fold_step below) to
 // keep the epilogues compact: the instruction caches are small, and code
@@ -490,16 +521,6 @@ __device__ __noinline__ uint64_t fold_step(uint64_t st, long long dval, int g, i
   return static_cast<uint64_t>(__double_as_longlong(__dadd_rn(acc, term)));
 }
 
-// Persistent slice GEMM: every CTA walks tiles blockIdx.x, +gridDim.x, ...;
-// the three roles walk the same sequence and keep their pipeline state
-// (stage ring, accumulator double buffer) from one tile to the next, so the
-// epilogue of one tile overlaps the main loop of the next.
-//
-// Acc: type of the exact per-diagonal running sums (int or long long).
-// window: k-blocks (stages of 4 MMAs) per accumulation window.
-// kFloat (BF16 comparison mode only): one slice of bf16-rounded values, the
-// FP32 accumulator covers all of k in one window and is converted to FP64
-// without scaling.
 // Register split of the 384-thread slice GEMMs (setmaxnreg acts per
 // warpgroup): 384 threads x 168 registers at launch = 128 x 80 (warpgroup 0) + 256 x 208
 __device__ __forceinline__ void regs_dec_80() {
@@ -509,6 +530,18 @@ __device__ __forceinline__ void regs_inc_208() {
   asm volatile("setmaxnreg.inc.sync.aligned.u32 208;" ::: "memory");
 }
 
+// Persistent slice GEMM: every CTA walks tiles blockIdx.x, +gridDim.x, ...;
+// the three roles walk the same sequence and keep their pipeline state
+// (stage ring, accumulator double buffer) from one tile to the next, so the
+// epilogue of one tile overlaps the main loop of the next.
+//
+// Acc: type of the exact per-diagonal running sums (int or long long).
+// window: k-blocks (stages of 8 MMAs) per accumulation window.
+// Under split-k (OzSingle with splits > 1) a unit is one k range of a C
+// tile and the epilogue stores each diagonal's exact D_g instead of folding.
+// kFloat (BF16 comparison mode only): one slice of bf16-rounded values, the
+// FP32 accumulator covers all of k in one window and is converted to FP64
+// without scaling.
 template <typename Acc, bool kFloat, typename Tiles>
 __global__ void __launch_bounds__(kThreads, 1)
     oz_gemm_kernel(const Tiles tiles, int S, int beta, int window, int* __restrict__ status) {
@@ -652,27 +685,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row_in_tile = quarter * 32 + lane;
     const uint32_t t_lane = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
     const uint32_t t_acc = t_lane + kAccCol + static_cast<uint32_t>(half * 128);
-    const double dmax2 = static_cast<double>(((1 << beta) - 1) * ((1 << beta) - 1));
     int buf = 0;
     uint32_t fulls0 = 0u, fulls1 = 0u;  // windows drained from accumulator 0 / 1
     bool ok = true;
     Acc D[64];
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const OzTile j = tiles.tile(t);
-      // Diagonals g >= gx are combined exactly in int64 (the partial sum
-      // Y = sum_g D_g 2^{beta (S+1-g)} stays below 2^52 by the bound
-      // |D_g| <= (g-1)(2^beta-1)^2 128 Kt): the FP64 fold of those steps is
-      // exact, so doing them in integers gives the same bits.
-      int gx = S + 1;
-      {
-        double yb = 0.0;
-        for (int g = S + 1; g >= 2; --g) {
-          yb += (g - 1) * dmax2 * static_cast<double>(kOzTileK) * static_cast<double>(j.Kt) *
-                pow2_normal(beta * (S + 1 - g));
-          if (yb >= 4503599627370496.0) break;  // 2^52
-          gx = g;
-        }
-      }
+      const int gx = oz_exact_from(S, beta, j.Kt);
       for (int g = S + 1; g >= 2 && ok; --g) {
 #pragma unroll
         for (int i = 0; i < 64; ++i) D[i] = 0;
@@ -706,6 +725,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           buf ^= 1;
         }
         if (!ok) break;
+        if (!kFloat && j.partial != nullptr) {
+          // split-k: this range's exact D_g, column-major in the tile (a
+          // warp's 32 lanes store 256 contiguous bytes per column)
+          uint64_t* p = j.partial + static_cast<size_t>(g - 2) * (kOzTileRows * kOzTileRows) +
+                        static_cast<size_t>(half * 64) * kOzTileRows + row_in_tile;
+#pragma unroll
+          for (int i = 0; i < 64; ++i)
+            __stcg(reinterpret_cast<unsigned long long*>(p + i * kOzTileRows),
+                   static_cast<unsigned long long>(static_cast<long long>(D[i])));
+          continue;
+        }
         const bool first = (g == S + 1);
         const bool last = (g == 2);
         const int64_t row = j.row0 + row_in_tile;
@@ -1009,7 +1039,6 @@ __global__ void __launch_bounds__(kP2Threads, 1)
     const int half = ew >> 2;              // which 64 columns of the tile
     const int row_in_tile = quarter * 32 + lane;
     const uint32_t t_lane = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
-    const double dmax2 = static_cast<double>(((1 << beta) - 1) * ((1 << beta) - 1));
     int buf0 = 0, buf1 = 0, cnt0 = 0, cnt1 = 0;
     uint32_t fulls00 = 0u, fulls01 = 0u, fulls10 = 0u, fulls11 = 0u;
     bool ok = true;
@@ -1039,16 +1068,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const OzTile j = tiles.tile(t);
       // diagonals g >= gx fold exactly in int64 (see oz_gemm_kernel)
-      int gx = S + 1;
-      {
-        double yb = 0.0;
-        for (int g = S + 1; g >= 2; --g) {
-          yb += (g - 1) * dmax2 * static_cast<double>(kOzTileK) * static_cast<double>(j.Kt) *
-                pow2_normal(beta * (S + 1 - g));
-          if (yb >= 4503599627370496.0) break;  // 2^52
-          gx = g;
-        }
-      }
+      const int gx = oz_exact_from(S, beta, j.Kt);
       const int64_t row = j.row0 + row_in_tile;
       const bool row_ok = row < j.m;
       const int64_t col0 = j.col0 + half * 64;
@@ -1211,6 +1231,36 @@ static cudaError_t launch_oz_gemm_t(const Tiles& tiles, int64_t grid, int S, int
   return cudaGetLastError();
 }
 
+// Split-k recombination (steps 3-4 after a split product): D_g of every C
+// element is the exact int64 sum of the k ranges' partials, added in range
+// order; then the fold and the final scaling of the slice GEMM's epilogue,
+// with the exact phase taken from the full k.  Thread idx walks the
+// elements column by column (consecutive threads: consecutive rows, i.e.
+// contiguous partials in the column-major tiles).
+__global__ void __launch_bounds__(256) oz_splitk_fold_kernel(
+    const uint64_t* __restrict__ P, const uint64_t* __restrict__ rowbits,
+    const uint64_t* __restrict__ colbits, double* __restrict__ C, int64_t m, int64_t n,
+    int64_t Mt, int64_t Nt, int64_t Kt, int64_t splits, int S, int beta) {
+  const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= m * n) return;
+  const int64_t col = idx / m, row = idx - (idx / m) * m;
+  constexpr int64_t kTileWords = kOzTileRows * kOzTileRows;
+  const int64_t tile = (row / kOzTileRows) * Nt + col / kOzTileRows;
+  const uint64_t* p = P + tile * S * kTileWords + (col % kOzTileRows) * kOzTileRows +
+                      row % kOzTileRows;
+  const int64_t range_stride = Mt * Nt * S * kTileWords;
+  const int gx = oz_exact_from(S, beta, Kt);
+  uint64_t st = 0;
+  for (int g = S + 1; g >= 2; --g) {
+    long long dval = 0;
+    const uint64_t* q = p + static_cast<int64_t>(g - 2) * kTileWords;
+    for (int64_t sp = 0; sp < splits; ++sp) dval += static_cast<long long>(__ldcs(q + sp * range_stride));
+    st = fold_step(st, dval, g, gx, S, beta);
+  }
+  C[row * n + col] =
+      final_scale(st, exponent_from_absbits(rowbits[row]) + exponent_from_absbits(colbits[col]));
+}
+
 static bool narrow_sums(int S, int beta, int64_t Kt) {
   // int32 running sums suffice while S (2^beta - 1)^2 * 128 Kt < 2^31
   const long long dmax = (1ll << beta) - 1;
@@ -1222,9 +1272,21 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
                               const OzakiDims& d, uint64_t* sums, int* status, cudaStream_t s) {
   if (d.Mt == 0 || d.Nt == 0) return cudaSuccess;
   const int window = ozaki_window_stages(d.beta);
-  OzSingle tiles{aslices, bslices, rowbits, colbits, C, d.m, d.n, d.Mt, d.Nt, d.Kt, sums};
-  const int64_t count = d.Mt * d.Nt;
+  const int64_t splits = d.splits > 1 ? d.splits : 1;
+  OzSingle tiles{aslices, bslices, rowbits, colbits, C,      d.m, d.n,
+                 d.Mt,    d.Nt,    d.Kt,    sums,    splits, d.S};
+  const int64_t count = d.Mt * d.Nt * splits;
   const int64_t grid = count < sm_count() ? count : sm_count();
+  if (splits > 1) {
+    // one diagonal at a time, each k range's D_g to the partials, then the fold
+    cudaError_t e =
+        launch_oz_gemm_t<long long, false>(tiles, grid, d.S, d.beta, window, status, s);
+    if (e != cudaSuccess) return e;
+    const int64_t total = d.m * d.n;
+    oz_splitk_fold_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
+        sums, rowbits, colbits, C, d.m, d.n, d.Mt, d.Nt, d.Kt, splits, d.S, d.beta);
+    return cudaGetLastError();
+  }
   if (narrow_sums(d.S, d.beta, d.Kt)) {
     auto kern = oz_gemm2_kernel<OzSingle>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1262,7 +1324,7 @@ cudaError_t launch_bf16_gemm(const double* A, const double* B, double* C, const 
       B, d.k, d.n, 1, d.Kt, bplane);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  OzSingle tiles{aplane, bplane, nullptr, nullptr, C, d.m, d.n, d.Mt, d.Nt, d.Kt, nullptr};
+  OzSingle tiles{aplane, bplane, nullptr, nullptr, C, d.m, d.n, d.Mt, d.Nt, d.Kt, nullptr, 1, 1};
   const int64_t count = d.Mt * d.Nt;
   const int64_t grid = count < sm_count() ? count : sm_count();
   // one window covers all of k (FP32 accumulation is the mode's semantics)

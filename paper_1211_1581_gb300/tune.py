@@ -173,6 +173,22 @@ def device_measure(A, B, reps: int = 3, stream=None):
     return measure
 
 
+def grouped_slices(problems, mode: int = mxm.MODE_EMUL_I8, tol: float = 1.0,
+                   measure_for=None) -> int:
+    """Slice count for one grouped call (a single count serves every
+    problem): the largest of the smallest accurate counts of ``problems``
+    [(A, B), ...], a sample the caller picks.  Short-k problems need the
+    most slices: the truncation error scales with the row / column maxima
+    while k u |A||B| shrinks with k.  ``measure_for(A, B)`` builds the
+    measuring function (default: ``device_measure`` with one timed run)."""
+    measure_for = measure_for or (lambda A, B: device_measure(A, B, reps=1))
+    need = 1
+    for A, B in problems:
+        c = select(measure_for(A, B), tol, modes=(mode,))
+        need = max(need, c.slices)
+    return need
+
+
 def tune(A, B, tag: str = "default", tol: float = 1.0, cache: TuneCache | None = None,
          reps: int = 3, stream=None) -> Choice:
     """Measure every candidate on A, B and store the choice under

@@ -81,6 +81,23 @@ def test_workspace_size_is_host_arithmetic():
     assert mxm.mxm_workspace_size(1, 256, 128, 128, 0) == 0
 
 
+def test_splitk_workspace_size():
+    """Products with fewer C tiles than half the 304 split-k units cut k
+    into ranges (FP64: at least 8 k-blocks of 16 each; emulated: at least 4
+    k-blocks of 128) and add room for the partial tiles."""
+    # FP64, m = n = 128, k = 65536: 1 tile, Kt = 4096 -> 304 ranges
+    packs = 2 * 4096 * 128 * 16 * 8
+    assert mxm.mxm_workspace_size(0, 128, 65536, 128) == packs + 304 * 128 * 128 * 8
+    # FP64 with 152 or more tiles is not split
+    assert mxm.mxm_workspace_size(0, 152 * 128, 1024, 128) == (152 + 1) * 64 * 128 * 16 * 8
+    # emulated, S = 6, m = n = 128, k = 65536: Kt = 512 -> 128 ranges, each
+    # holding S diagonals' int64 128 x 128 partials
+    ws = mxm.mxm_workspace_size(1, 128, 65536, 128, 6)
+    planes = 6 * 2 * 512 * 128 * 128 * 2
+    partials = 128 * 6 * 128 * 128 * 8
+    assert planes + partials <= ws < planes + partials + 8 * 1024
+
+
 def test_grouped_workspace_size_on_host():
     import numpy as np
     rows = np.array([[0, 0, 0, 128, 64, 128], [0, 0, 0, 129, 65, 1], [0, 0, 0, 0, 5, 5]],

@@ -154,3 +154,26 @@ def test_emul_n8192_sampled(kind, S):
     assert_bitwise(C[ii, jj], oracle.ozaki_entries(A, B, ii, jj, S=S, beta=7), "n=8192")
     d2, ab = oracle.entries_dot2_abs(A, B, ii, jj)
     assert_within_bound(C[ii, jj], d2, ab, n, "n=8192 bound")
+
+
+# Split-k of the emulated product: the exact per-range D_g are added exactly
+# before the fold, so the result stays bit-identical to the CPU emulator
+# (1 tile x 8 ranges; 4 tiles x 4 ranges with a ragged last k-block).
+@pytest.mark.parametrize("mode,S", [(mxm.MODE_EMUL_I8, 7), (mxm.MODE_EMUL_BF16, 6)])
+@pytest.mark.parametrize("shape", [(128, 4096, 128), (130, 2125, 200)])
+def test_emul_splitk_bit_identical(mode, S, shape):
+    m, k, n = shape
+    A, B = inputs.gemm_operands("spread", m, k, n, seed=0, cfg=9)
+    C = run_emul(A, B, S, mode)
+    assert_bitwise(C, oracle.ozaki_gemm(A, B, S=S, beta=BETA[mode]), f"split-k {shape}")
+
+
+def test_emul_splitk_64_tiles_sampled():
+    """m = k = n = 1024 (64 C tiles, 2 k ranges each), sampled entries."""
+    n = 1024
+    A, B = inputs.gemm_operands("spread", n, n, n, seed=0, cfg=10)
+    C = run_emul(A, B, 7)
+    rng = np.random.default_rng(10)
+    ii = rng.integers(0, n, 300)
+    jj = rng.integers(0, n, 300)
+    assert_bitwise(C[ii, jj], oracle.ozaki_entries(A, B, ii, jj, S=7, beta=7), "n=1024")

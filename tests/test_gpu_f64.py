@@ -104,3 +104,30 @@ def test_f64_rectangular_sampled():
         jj = rng.integers(0, n, 300)
         d2, ab = oracle.entries_dot2_abs(A, B, ii, jj)
         assert_within_bound(C[ii, jj], d2, ab, k, f"f64 {(m, k, n)}")
+
+
+# Split-k: products with fewer C tiles than SMs cut k into ranges computed by
+# separate CTAs and added in range order (1 tile x 32 ranges; 3 tiles x 23
+# ranges with a ragged last k-block; 64 tiles x 4 ranges).
+@pytest.mark.parametrize("shape", [(128, 4096, 128), (257, 3001, 65), (1024, 1024, 1024)])
+def test_f64_splitk_within_bound(shape):
+    m, k, n = shape
+    A, B = inputs.gemm_operands("uniform", m, k, n, seed=0, cfg=7)
+    C = run_f64(A, B)
+    if m * n <= 300 * 300:
+        assert_within_bound(C, oracle.gemm_dot2(A, B), oracle.gemm_abs(A, B), k, f"{shape}")
+    else:
+        rng = np.random.default_rng(k)
+        ii = rng.integers(0, m, 400)
+        jj = rng.integers(0, n, 400)
+        d2, ab = oracle.entries_dot2_abs(A, B, ii, jj)
+        assert_within_bound(C[ii, jj], d2, ab, k, f"{shape}")
+
+
+def test_f64_splitk_exact_integers_and_deterministic():
+    """Integers in [-8, 8] with k = 4096: every partial sum is an integer
+    below 2^18, so any summation order (split or not) is exact."""
+    A, B = inputs.gemm_operands("int8", 100, 4096, 90, seed=0, cfg=8)
+    C = run_f64(A, B)
+    assert_bitwise(C, oracle.gemm_naive(A, B), "split-k integers")
+    assert_bitwise(run_f64(A, B), C, "split-k run to run")

@@ -81,18 +81,21 @@ def test_grouped_workspace_too_small_reported():
 
 def test_grouped_2000_logu_sampled():
     """The grouped workload: 2000 problems, each of m, k, n log-uniform in
-    [16, 1024] from seed 0; both modes; 24 problems checked in full."""
+    [16, 1024] from seed 0; both modes; 24 problems checked in full plus the
+    three with the shortest k.  S = 8: with uniform entries the truncation
+    error relative to k u |A||B| grows as 1/k, and at k = 16 seven slices
+    leave ~4 k u |A||B|, outside the bound; eight meet it."""
     dims = inputs.grouped_problems(0, 2000)
     hs, ds = make_group([tuple(int(v) for v in d) for d in dims])
     rng = np.random.default_rng(5)
-    pick = rng.choice(len(dims), 24, replace=False)
-    for mode, S in ((mxm.MODE_EMUL_I8, 7), (mxm.MODE_F64, 0)):
+    pick = list(rng.choice(len(dims), 24, replace=False))
+    pick += sorted(range(len(dims)), key=lambda p: dims[p][1])[:3]
+    for mode, S in ((mxm.MODE_EMUL_I8, 8), (mxm.MODE_F64, 0)):
         assert run_group(ds, mode, S, graph=True) == mxm.MXM_OK
         for p in pick:
             A, B = hs[p]
             got = ds[p][2].cpu().numpy()
-            if mode == mxm.MODE_F64:
-                assert_within_bound(got, oracle.gemm_dot2(A, B), oracle.gemm_abs(A, B),
-                                    A.shape[1], f"p={p}")
-            else:
+            if mode != mxm.MODE_F64:
                 assert_bitwise(got, oracle.ozaki_gemm(A, B, S=S), f"p={p}")
+            assert_within_bound(got, oracle.gemm_dot2(A, B), oracle.gemm_abs(A, B),
+                                A.shape[1], f"p={p} mode={mode}")

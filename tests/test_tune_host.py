@@ -72,3 +72,16 @@ def test_cache_round_trip(tmp_path):
     assert again.get("x") == choice
     assert json.loads(path.read_text())["x"]["slices"] == 7
     assert [p.name for p in path.parent.iterdir()] == ["tune.json"]  # no temporary left
+
+
+def test_grouped_slices_takes_the_worst_problem():
+    # problem "p" needs need[p] slices; the grouped count is the maximum
+    need = {"short": 8, "long": 6, "mid": 7}
+
+    def measure_for(A, B):
+        def measure(mode, s):
+            return 2.0 ** (7 * (need[A] - s)), float(s)
+        return measure
+    probs = [("long", None), ("short", None), ("mid", None)]
+    assert tune.grouped_slices(probs, measure_for=measure_for) == 8
+    assert tune.grouped_slices(probs[:1], measure_for=measure_for) == 6
