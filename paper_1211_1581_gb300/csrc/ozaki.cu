@@ -975,7 +975,12 @@ __global__ void __launch_bounds__(kP2Threads, 1)
         acq = true;
         return true;
       };
+      // A thread that issued nothing into a window (one-step windows) still
+      // waits for the drain of the buffer's previous window before it
+      // commits: otherwise it could run two windows ahead and put two
+      // arrivals into one phase of the window barrier.
       auto window_end = [&](int x) {
+        if (!acquire(x)) return false;
         int& b = x ? buf1 : buf0;
         const int a = 2 * x + b;
         mma_commit(&sm.accfull[a]);
@@ -983,6 +988,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
         par ^= 1u << a;
         b ^= 1;
         (x ? acq1 : acq0) = false;
+        return true;
       };
       auto mma8 = [&](int x, int aslot, int bslot) {
         const uint64_t da = adesc0 + static_cast<uint64_t>(aslot) * (kOzTileBytes >> 4);
@@ -1046,11 +1052,17 @@ __global__ void __launch_bounds__(kP2Threads, 1)
               }
               if (++cnt0 == window || (kb == Kt - 1 && s == g - 1)) {
                 cnt0 = 0;
-                window_end(0);
+                if (!window_end(0)) {
+                  ok = false;
+                  break;
+                }
               }
               if (has1 && (++cnt1 == window || (kb == Kt - 1 && s == g - 2))) {
                 cnt1 = 0;
-                window_end(1);
+                if (!window_end(1)) {
+                  ok = false;
+                  break;
+                }
               }
               bprev = bnew;
               bprev_ph = bnew_ph;

@@ -177,3 +177,20 @@ def test_emul_splitk_64_tiles_sampled():
     ii = rng.integers(0, n, 300)
     jj = rng.integers(0, n, 300)
     assert_bitwise(C[ii, jj], oracle.ozaki_entries(A, B, ii, jj, S=7, beta=7), "n=1024")
+
+
+@pytest.mark.parametrize("S", [4, 7])
+@pytest.mark.parametrize("shape", [(2048, 128, 2048), (1024, 64, 1536)])
+def test_emul_one_kblock_many_tiles(shape, S):
+    """k within one k-block and more C tiles than SMs: every diagonal's
+    windows are one to seven steps long (one-step windows included), many
+    per CTA; sampled entries bit-identical to the CPU emulator, two runs
+    bit-identical to each other."""
+    m, k, n = shape
+    A, B = inputs.gemm_operands("spread", m, k, n, seed=0, cfg=11)
+    C = run_emul(A, B, S)
+    assert_bitwise(run_emul(A, B, S), C, "run to run")
+    rng = np.random.default_rng(m + n + S)
+    ii = rng.integers(0, m, 400)
+    jj = rng.integers(0, n, 400)
+    assert_bitwise(C[ii, jj], oracle.ozaki_entries(A, B, ii, jj, S=S, beta=7), f"{shape} S={S}")
