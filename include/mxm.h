@@ -114,8 +114,13 @@ mxm_status mxm_gemm(int mode, const double* A, const double* B, double* C, int64
 /*
  * mxm_gemm_host -- mxm_gemm on HOST buffers: copies A and B to the device,
  * computes, copies C back, and returns after C is in host memory (the
- * stream is synchronised).  Pinned host memory makes the copies faster.
- * Device buffers come from the library's workspace.
+ * stream is synchronised).  Device buffers come from the library's
+ * workspace.  For the emulated modes, products whose panels of about m/8
+ * rows still fill the GPU are pipelined: B first, then the panels of A are
+ * copied in, computed and their rows of C copied out while the next panels
+ * compute (two library-owned copy streams and a second compute stream);
+ * the result is bit-identical to mxm_gemm.  Pinned host memory is needed
+ * for the copies to overlap; pageable memory works but serialises them.
  */
 mxm_status mxm_gemm_host(int mode, const double* hA, const double* hB, double* hC, int64_t m,
                          int64_t k, int64_t n, int slices, void* stream);

@@ -28,6 +28,9 @@ struct DeviceState {
   size_t ws_bytes = 0;
   bool ws_owned = true;        // allocated by the library
   int sm_count = 0;
+  cudaStream_t h2d = nullptr;  // streams of the pipelined host path: copies in,
+  cudaStream_t d2h = nullptr;  // copies out, and a second compute stream
+  cudaStream_t c1 = nullptr;
 };
 
 std::mutex g_mutex;
@@ -266,6 +269,125 @@ mxm_status mxm_f64_emul(const double* A, const double* B, double* C, int64_t m, 
   return mxm_gemm(MXM_MODE_EMUL_I8, A, B, C, m, k, n, slices, stream);
 }
 
+// Host-buffer product of the emulated modes, pipelined over panels of rows
+// of A: B is copied, scaled and split once; the panels of A are copied in
+// order on one copy stream, the panels of C copied back on another, and the
+// panels' scale, split and slice GEMM alternate between two compute streams
+// (the caller's and the library's) with a workspace each, so that the
+// persistent GEMM of one panel starts on the SMs the previous one frees.
+// Rows of A are scaled and split independently (the scale of row i is its
+// own maximum) and the column scales come from all of B, so the panels give
+// the same bits as one call over all rows.
+constexpr int64_t kHostPanels = 8;
+
+// Rows per panel (a multiple of the 128-row tile), or 0 when the product is
+// too small for a panel to fill the GPU.
+static int64_t host_panel_rows(int64_t m, int64_t n, int sms) {
+  const int64_t h = align_up((m + kHostPanels - 1) / kHostPanels, size_t(kOzTileRows));
+  const int64_t tiles = (h / kOzTileRows) * ((n + kOzTileRows - 1) / kOzTileRows);
+  if (h >= m || tiles < sms) return 0;
+  return h;
+}
+
+static mxm_status gemm_host_panels(DeviceState* ds, int mode, const double* hA, const double* hB,
+                                   double* hC, int64_t m, int64_t k, int64_t n, int slices,
+                                   int64_t h, cudaStream_t s) {
+  const int beta = mode_beta(mode);
+  const OzakiDims dp = ozaki_dims(h, k, n, slices, beta);  // the largest panel, no split-k
+  const OzakiLayout L = ozaki_layout(dp);
+  // per compute stream: row scales, A planes, running sums of one panel
+  const size_t rb_bytes = align_up(sizeof(uint64_t) * size_t(h), 1024);
+  const size_t ap_bytes = L.bslices - L.aslices;
+  const size_t sm_bytes = L.total - L.sums;
+  const size_t per_buf = rb_bytes + ap_bytes + sm_bytes;
+  const size_t shared_bytes = (L.aslices - L.colbits) + (L.sums - L.bslices);  // colbits, B planes
+  const size_t ab = align_up(sizeof(double) * size_t(m) * size_t(k), 1024);
+  const size_t bb = align_up(sizeof(double) * size_t(k) * size_t(n), 1024);
+  const size_t cb = align_up(sizeof(double) * size_t(m) * size_t(n), 1024);
+  mxm_status st = ensure_workspace(ds, ab + bb + cb + shared_bytes + 2 * per_buf, s);
+  if (st != MXM_OK) return st;
+  if (ds->h2d == nullptr && cudaStreamCreateWithFlags(&ds->h2d, cudaStreamNonBlocking) != cudaSuccess)
+    return cuda_fail();
+  if (ds->d2h == nullptr && cudaStreamCreateWithFlags(&ds->d2h, cudaStreamNonBlocking) != cudaSuccess)
+    return cuda_fail();
+  if (ds->c1 == nullptr && cudaStreamCreateWithFlags(&ds->c1, cudaStreamNonBlocking) != cudaSuccess)
+    return cuda_fail();
+  uint8_t* base = static_cast<uint8_t*>(ds->ws);
+  double* dA = reinterpret_cast<double*>(base);
+  double* dB = reinterpret_cast<double*>(base + ab);
+  double* dC = reinterpret_cast<double*>(base + ab + bb);
+  uint8_t* w = base + ab + bb + cb;
+  uint64_t* colbits = reinterpret_cast<uint64_t*>(w);
+  uint8_t* bplanes = w + (L.aslices - L.colbits);
+  uint8_t* bufs = w + shared_bytes;
+  const int64_t P = (m + h - 1) / h;
+  // events: B copied, B split, then per panel: A copied, C computed; done
+  std::vector<cudaEvent_t> ev(2 * P + 3, nullptr);
+  mxm_status rc = MXM_OK;
+  auto fail = [&]() { rc = cuda_fail(); };
+  for (auto& e : ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      e = nullptr;
+      fail();
+    }
+  cudaEvent_t eB = ev[0], eBs = ev[1], eDone = ev[2];
+  cudaStream_t cs[2] = {s, ds->c1};
+  if (rc == MXM_OK &&
+      (cudaMemcpyAsync(dB, hB, sizeof(double) * size_t(k) * size_t(n), cudaMemcpyHostToDevice,
+                       ds->h2d) != cudaSuccess ||
+       cudaEventRecord(eB, ds->h2d) != cudaSuccess || cudaStreamWaitEvent(s, eB, 0) != cudaSuccess))
+    fail();
+  if (rc == MXM_OK) {
+    const OzakiDims db = ozaki_dims(0, k, n, slices, beta);
+    if (launch_ozaki_scale(nullptr, dB, db, nullptr, colbits, ds->status, s) != cudaSuccess ||
+        launch_ozaki_split(nullptr, dB, db, nullptr, colbits, nullptr, bplanes, s) !=
+            cudaSuccess ||
+        cudaEventRecord(eBs, s) != cudaSuccess || cudaStreamWaitEvent(ds->c1, eBs, 0) != cudaSuccess)
+      fail();
+  }
+  for (int64_t p = 0; p < P && rc == MXM_OK; ++p) {
+    const int64_t r0 = p * h, hp = (m - r0) < h ? (m - r0) : h;
+    if (cudaMemcpyAsync(dA + r0 * k, hA + r0 * k, sizeof(double) * size_t(hp) * size_t(k),
+                        cudaMemcpyHostToDevice, ds->h2d) != cudaSuccess ||
+        cudaEventRecord(ev[3 + p], ds->h2d) != cudaSuccess)
+      fail();
+  }
+  for (int64_t p = 0; p < P && rc == MXM_OK; ++p) {
+    const int64_t r0 = p * h, hp = (m - r0) < h ? (m - r0) : h;
+    cudaStream_t c = cs[p & 1];
+    uint8_t* buf = bufs + (p & 1) * per_buf;
+    uint64_t* rowbits = reinterpret_cast<uint64_t*>(buf);
+    uint8_t* aplanes = buf + rb_bytes;
+    uint64_t* sums = reinterpret_cast<uint64_t*>(buf + rb_bytes + ap_bytes);
+    const OzakiDims da = ozaki_dims(hp, k, 0, slices, beta);
+    const OzakiDims dg = ozaki_dims(hp, k, n, slices, beta);
+    if (cudaStreamWaitEvent(c, ev[3 + p], 0) != cudaSuccess ||
+        launch_ozaki_scale(dA + r0 * k, nullptr, da, rowbits, nullptr, ds->status, c) !=
+            cudaSuccess ||
+        launch_ozaki_split(dA + r0 * k, nullptr, da, rowbits, nullptr, aplanes, nullptr, c) !=
+            cudaSuccess ||
+        launch_ozaki_gemm(aplanes, bplanes, rowbits, colbits, dC + r0 * n, dg, sums, ds->status,
+                          c) != cudaSuccess ||
+        cudaEventRecord(ev[3 + P + p], c) != cudaSuccess ||
+        cudaStreamWaitEvent(ds->d2h, ev[3 + P + p], 0) != cudaSuccess ||
+        cudaMemcpyAsync(hC + r0 * n, dC + r0 * n, sizeof(double) * size_t(hp) * size_t(n),
+                        cudaMemcpyDeviceToHost, ds->d2h) != cudaSuccess)
+      fail();
+  }
+  // the caller's stream ends after the last copy back; every stream is
+  // drained before the events go
+  if (rc == MXM_OK && (cudaEventRecord(eDone, ds->d2h) != cudaSuccess ||
+                       cudaStreamWaitEvent(s, eDone, 0) != cudaSuccess))
+    fail();
+  if (cudaStreamSynchronize(s) != cudaSuccess) fail();
+  cudaStreamSynchronize(ds->c1);
+  cudaStreamSynchronize(ds->h2d);
+  cudaStreamSynchronize(ds->d2h);
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  return rc;
+}
+
 mxm_status mxm_gemm_host(int mode, const double* hA, const double* hB, double* hC, int64_t m,
                          int64_t k, int64_t n, int slices, void* stream) {
   mxm_status st = check_mode(mode, slices);
@@ -277,6 +399,10 @@ mxm_status mxm_gemm_host(int mode, const double* hA, const double* hB, double* h
   std::lock_guard<std::mutex> lock(g_mutex);
   DeviceState* ds = nullptr;
   if ((st = current_state(&ds)) != MXM_OK) return st;
+  if (emul_mode(mode) && k > 0) {
+    const int64_t h = host_panel_rows(m, n, ds->sm_count);
+    if (h > 0) return gemm_host_panels(ds, mode, hA, hB, hC, m, k, n, slices, h, s);
+  }
   const size_t ab = align_up(sizeof(double) * size_t(m) * size_t(k), 1024);
   const size_t bb = align_up(sizeof(double) * size_t(k) * size_t(n), 1024);
   const size_t cb = align_up(sizeof(double) * size_t(m) * size_t(n), 1024);

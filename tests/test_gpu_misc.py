@@ -65,3 +65,33 @@ def test_caller_workspace():
 def test_peak_probes_run(kind):
     v = mxm.mxm_peak_probe(kind)
     assert v > 0.0
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("mode,S", [(mxm.MODE_EMUL_I8, 7), (mxm.MODE_EMUL_BF16, 6)])
+def test_host_entry_point_panels(mode, S, pinned):
+    """Products large enough for the pipelined host path (A and C moved in
+    panels of rows while earlier panels compute): 8 panels of 384 rows, the
+    last one 312 rows; bit-identical to the device call and, on sampled
+    entries, to the CPU emulator."""
+    m, k, n = 3000, 300, 6500
+    A, B = inputs.gemm_operands("spread", m, k, n, seed=0, cfg=12)
+    if pinned:
+        Ah = torch.from_numpy(A).pin_memory()
+        Bh = torch.from_numpy(B).pin_memory()
+        Ch = torch.empty((m, n), dtype=torch.float64).pin_memory()
+        mxm.mxm_gemm_host(mode, Ah, Bh, Ch, slices=S)
+        Ch = Ch.numpy()
+    else:
+        Ch = np.empty((m, n))
+        mxm.mxm_gemm_host(mode, A, B, Ch, slices=S)
+    assert mxm.mxm_get_device_status() == mxm.MXM_OK
+    Cd = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    mxm.mxm_gemm(mode, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), Cd, slices=S)
+    assert_bitwise(Ch, Cd.cpu().numpy(), "panels vs device")
+    rng = np.random.default_rng(13)
+    ii = rng.integers(0, m, 300)
+    jj = rng.integers(0, n, 300)
+    ii[:3] = [0, 2999, 2688]  # first row, last row, first row of the last panel
+    beta = 7 if mode == mxm.MODE_EMUL_I8 else 8
+    assert_bitwise(Ch[ii, jj], oracle.ozaki_entries(A, B, ii, jj, S=S, beta=beta), "panels vs oracle")
