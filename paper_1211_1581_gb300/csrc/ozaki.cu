@@ -1132,6 +1132,14 @@ __global__ void __launch_bounds__(kP2Threads, 1)
           D1[i] = 0;
         }
         for (int64_t kb = 0; kb < j.Kt && ok; ++kb) {
+          if (kb == j.Kt - 1 && q > 0) {
+            // the fold at the end of this k-block reads the tile's running
+            // sums: bring them into L2 while the last windows finish
+            const uint64_t* ps =
+                j.sums + static_cast<size_t>(half * 64) * kOzTileRows + row_in_tile;
+#pragma unroll 1
+            for (int i = 0; i < 64; ++i) prefetch_l2(ps + i * kOzTileRows);
+          }
           for (int s = 1; s <= g - 1; ++s) {
             if (++cnt0 == window || (kb == j.Kt - 1 && s == g - 1)) {
               cnt0 = 0;
