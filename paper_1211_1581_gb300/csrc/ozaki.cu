@@ -164,12 +164,64 @@ __device__ __forceinline__ void split_chunk_store(const double (&x)[8], int e, i
   }
 }
 
-// One 128 x 64 tile (tm, tk) of A (m x k, row-major) -> its S digit tiles,
-// `slice_stride` bytes apart.
+// The same for beta * S <= 64: the fraction |x| 2^-e is first put in one
+// 64-bit fixed-point word F = floor(|x| 2^{beta S - e}) (one shift), then
+// digit s is the field F >> beta (S - s) (a shift uniform over the warp) and
+// its bf16 pattern is the upper half of the FP32 pattern of the integer
+// (exact: at most 8 significant bits).
+__device__ __forceinline__ void split_chunk_store_w64(const double (&x)[8], int e, int S,
+                                                      int beta, uint8_t* dst,
+                                                      size_t slice_stride) {
+  uint64_t F[8];
+  uint32_t sg[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x[j]));
+    const int be = static_cast<int>((b >> 52) & 0x7FF);
+    const uint64_t mant = b & 0x000FFFFFFFFFFFFFull;
+    const uint64_t M = be ? (mant | 0x0010000000000000ull) : mant;
+    const int sh = (be ? be - 1075 : -1074) - e + beta * S;
+    F[j] = sh >= 0 ? (sh < 64 ? M << sh : 0ull) : (-sh < 64 ? M >> -sh : 0ull);
+    sg[j] = static_cast<uint32_t>(b >> 63) << 15;
+  }
+  const uint32_t mask = (1u << beta) - 1u;
+  for (int s = 1; s <= S; ++s) {
+    const int p = beta * (S - s);
+    uint32_t packed[4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      uint32_t bits2[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t mag = static_cast<uint32_t>(F[j + h] >> p) & mask;
+        const uint32_t hi = __float_as_uint(__uint2float_rn(mag)) >> 16;
+        bits2[h] = mag ? (hi | sg[j + h]) : 0u;
+      }
+      packed[j >> 1] = bits2[0] | (bits2[1] << 16);
+    }
+    *reinterpret_cast<uint4*>(dst + static_cast<size_t>(s - 1) * slice_stride) =
+        make_uint4(packed[0], packed[1], packed[2], packed[3]);
+  }
+}
+
+__device__ __forceinline__ void split_chunk(const double (&x)[8], int e, int S, int beta,
+                                            uint8_t* dst, size_t slice_stride) {
+  if (beta * S <= 64)
+    split_chunk_store_w64(x, e, S, beta, dst, slice_stride);
+  else
+    split_chunk_store(x, e, S, beta, dst, slice_stride);
+}
+
+// One 128 x 128 tile (tm, tk) of A (m x k, row-major) -> its S digit tiles,
+// `slice_stride` bytes apart.  A thread takes 8 consecutive k of one row
+// (consecutive threads: consecutive chunks of a row, so the loads and the
+// 16-byte stores are contiguous); rows of even k are read as 16-byte pairs.
 __device__ __forceinline__ void split_a_tile(const double* __restrict__ A, int64_t m, int64_t k,
                                              const uint64_t* __restrict__ rowbits, int S,
                                              int beta, int64_t tm, int64_t tk, uint8_t* tile,
                                              size_t slice_stride) {
+  const bool pairs = ((k & 1) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+#pragma unroll 2
   for (int p = threadIdx.x; p < kOzTileRows * kOzChunksPerRow; p += blockDim.x) {
     const int c = p % kOzChunksPerRow, r = p / kOzChunksPerRow;
     const int64_t row = tm * kOzTileRows + r;
@@ -177,28 +229,52 @@ __device__ __forceinline__ void split_a_tile(const double* __restrict__ A, int64
     double v[8];
     int e = 0;
     if (row < m) e = exponent_from_absbits(rowbits[row]);
+    const double* src = A + row * k + k0;
+    if (row < m && pairs && k0 + 8 <= k) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = (row < m && k0 + j < k) ? __ldg(A + row * k + k0 + j) : 0.0;
-    split_chunk_store(v, e, S, beta, tile + oz_chunk_offset(r, c), slice_stride);
+      for (int j = 0; j < 8; j += 2) {
+        const double2 t = __ldg(reinterpret_cast<const double2*>(src + j));
+        v[j] = t.x;
+        v[j + 1] = t.y;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = (row < m && k0 + j < k) ? __ldg(src + j) : 0.0;
+    }
+    split_chunk(v, e, S, beta, tile + oz_chunk_offset(r, c), slice_stride);
   }
 }
 
-// One tile (tn, tk) of B^T, i.e. 128 columns j x 64 k of B (k x n,
-// row-major) -> its S digit tiles: both MMA operands are K-major.
+// One tile (tn, tk) of B^T, i.e. 128 columns j x 128 k of B (k x n,
+// row-major) -> its S digit tiles: both MMA operands are K-major.  The tile
+// is read in four passes of 32 rows of B (coalesced along the rows) through
+// shared memory, then every thread takes 8 consecutive k of one column.
+constexpr int kSplitBRows = 32;
 __device__ __forceinline__ void split_b_tile(const double* __restrict__ B, int64_t k, int64_t n,
                                              const uint64_t* __restrict__ colbits, int S,
                                              int beta, int64_t tn, int64_t tk, uint8_t* tile,
-                                             size_t slice_stride) {
-  for (int p = threadIdx.x; p < kOzTileRows * kOzChunksPerRow; p += blockDim.x) {
-    const int c = p % kOzChunksPerRow, r = p / kOzChunksPerRow;
-    const int64_t col = tn * kOzTileRows + r;
-    const int64_t k0 = tk * kOzTileK + c * 8;
-    double v[8];
-    int f = 0;
-    if (col < n) f = exponent_from_absbits(colbits[col]);
+                                             size_t slice_stride,
+                                             double (*sb)[kOzTileRows + 1]) {
+  const int64_t col0 = tn * kOzTileRows;
+  for (int pass = 0; pass < kOzTileK / kSplitBRows; ++pass) {
+    const int64_t l0 = tk * kOzTileK + pass * kSplitBRows;
+    for (int p = threadIdx.x; p < kSplitBRows * kOzTileRows; p += blockDim.x) {
+      const int lr = p / kOzTileRows, cc = p % kOzTileRows;
+      const int64_t l = l0 + lr, col = col0 + cc;
+      sb[lr][cc] = (l < k && col < n) ? __ldg(B + l * n + col) : 0.0;
+    }
+    __syncthreads();
+    constexpr int kChunks = kSplitBRows / 8;  // chunks of 8 k per column in a pass
+    for (int p = threadIdx.x; p < kOzTileRows * kChunks; p += blockDim.x) {
+      const int r = p % kOzTileRows, cl = p / kOzTileRows;
+      const int64_t col = col0 + r;
+      const int f = col < n ? exponent_from_absbits(colbits[col]) : 0;
+      double v[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = (col < n && k0 + j < k) ? __ldg(B + (k0 + j) * n + col) : 0.0;
-    split_chunk_store(v, f, S, beta, tile + oz_chunk_offset(r, c), slice_stride);
+      for (int j = 0; j < 8; ++j) v[j] = sb[cl * 8 + j][r];
+      split_chunk(v, f, S, beta, tile + oz_chunk_offset(r, pass * kChunks + cl), slice_stride);
+    }
+    __syncthreads();
   }
 }
 
@@ -216,10 +292,11 @@ __global__ void __launch_bounds__(256) oz_split_a_kernel(
 __global__ void __launch_bounds__(256) oz_split_b_kernel(
     const double* __restrict__ B, int64_t k, int64_t n, const uint64_t* __restrict__ colbits,
     int S, int beta, int64_t Nt, int64_t Kt, uint8_t* __restrict__ bslices) {
+  __shared__ double sb[kSplitBRows][kOzTileRows + 1];
   const int64_t tk = blockIdx.x, tn = blockIdx.y;
   split_b_tile(B, k, n, colbits, S, beta, tn, tk,
                bslices + (static_cast<size_t>(tn) * Kt + tk) * kOzTileBytes,
-               static_cast<size_t>(Nt) * Kt * kOzTileBytes);
+               static_cast<size_t>(Nt) * Kt * kOzTileBytes, sb);
 }
 
 // ---------------------------------------------------------------- grouped steps 1-2
@@ -280,7 +357,8 @@ __global__ void __launch_bounds__(256) oz_grouped_split_kernel(uint8_t* __restri
   const uint64_t* rowbits = reinterpret_cast<const uint64_t*>(ws + hdr->off_rowbits);
   const uint64_t* colbits = reinterpret_cast<const uint64_t*>(ws + hdr->off_colbits);
   const int64_t na = hdr->atiles, nb = hdr->btiles;
-  for (int64_t t = blockIdx.x; t < na + nb; t += gridDim.x) {
+  __shared__ double sb[kSplitBRows][kOzTileRows + 1];
+  for (int64_t t = blockIdx.x; t < na + nb; t += gridDim.x) {  // block-uniform branch
     if (t < na) {
       const GroupedProblem& p = recs[grouped_find(recs, hdr->count, t, &GroupedProblem::atile_begin)];
       const int64_t local = t - p.atile_begin;
@@ -293,7 +371,7 @@ __global__ void __launch_bounds__(256) oz_grouped_split_kernel(uint8_t* __restri
       const int64_t local = tb - p.btile_begin;
       split_b_tile(p.B, p.k, p.n, colbits + p.col_begin, S, beta, local / p.Kt, local % p.Kt,
                    ws + hdr->off_b + static_cast<size_t>(tb) * kOzTileBytes,
-                   static_cast<size_t>(nb) * kOzTileBytes);
+                   static_cast<size_t>(nb) * kOzTileBytes, sb);
     }
   }
 }
