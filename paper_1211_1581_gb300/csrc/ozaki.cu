@@ -302,6 +302,8 @@ __global__ void __launch_bounds__(256) oz_split_b_kernel(
 // ---------------------------------------------------------------- grouped steps 1-2
 // The same scale and split over every problem of a grouped call, items
 // located through the device plan.
+// A warp takes a contiguous run of rows (one binary search for the first,
+// then the owning problem only moves forward).
 __global__ void oz_grouped_rowmax_kernel(const uint8_t* __restrict__ ws, int* __restrict__ status) {
   const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
   if (!hdr->valid) return;
@@ -309,9 +311,14 @@ __global__ void oz_grouped_rowmax_kernel(const uint8_t* __restrict__ ws, int* __
   uint64_t* rowbits = reinterpret_cast<uint64_t*>(const_cast<uint8_t*>(ws) + hdr->off_rowbits);
   const int lane = threadIdx.x & 31;
   const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
-  for (int64_t r = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-       r < hdr->rows; r += warps) {
-    const GroupedProblem& p = recs[grouped_find(recs, hdr->count, r, &GroupedProblem::row_begin)];
+  const int64_t w = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t per = (hdr->rows + warps - 1) / warps;
+  const int64_t r0 = w * per, r1 = (r0 + per) < hdr->rows ? (r0 + per) : hdr->rows;
+  if (r0 >= r1) return;
+  int64_t pi = grouped_find(recs, hdr->count, r0, &GroupedProblem::row_begin);
+  for (int64_t r = r0; r < r1; ++r) {
+    while (pi + 1 < hdr->count && recs[pi + 1].row_begin <= r) ++pi;
+    const GroupedProblem& p = recs[pi];
     const double* a = p.A + (r - p.row_begin) * p.k;
     uint64_t mx = 0;
     for (int64_t l = lane; l < p.k; l += 32) {
@@ -326,6 +333,8 @@ __global__ void oz_grouped_rowmax_kernel(const uint8_t* __restrict__ ws, int* __
   }
 }
 
+// A warp takes a contiguous run of 32-column groups (as above); four
+// independent maxima keep four loads of the column walk in flight.
 __global__ void oz_grouped_colmax_kernel(const uint8_t* __restrict__ ws, int* __restrict__ status) {
   const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
   if (!hdr->valid) return;
@@ -333,17 +342,36 @@ __global__ void oz_grouped_colmax_kernel(const uint8_t* __restrict__ ws, int* __
   uint64_t* colbits = reinterpret_cast<uint64_t*>(const_cast<uint8_t*>(ws) + hdr->off_colbits);
   const int lane = threadIdx.x & 31;
   const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
-  for (int64_t gi = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-       gi < hdr->cgroups; gi += warps) {
-    const GroupedProblem& p =
-        recs[grouped_find(recs, hdr->count, gi, &GroupedProblem::cgrp_begin)];
+  const int64_t w = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t per = (hdr->cgroups + warps - 1) / warps;
+  const int64_t g0 = w * per, g1 = (g0 + per) < hdr->cgroups ? (g0 + per) : hdr->cgroups;
+  if (g0 >= g1) return;
+  int64_t pi = grouped_find(recs, hdr->count, g0, &GroupedProblem::cgrp_begin);
+  for (int64_t gi = g0; gi < g1; ++gi) {
+    while (pi + 1 < hdr->count && recs[pi + 1].cgrp_begin <= gi) ++pi;
+    const GroupedProblem& p = recs[pi];
     const int64_t col = (gi - p.cgrp_begin) * 32 + lane;
     if (col >= p.n) continue;
-    uint64_t mx = 0;
-    for (int64_t l = 0; l < p.k; ++l) {
-      const uint64_t b = static_cast<uint64_t>(__double_as_longlong(__ldg(p.B + l * p.n + col))) & kAbsMask;
-      mx = mx > b ? mx : b;
+    const double* bc = p.B + col;
+    uint64_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+    int64_t l = 0;
+    for (; l + 4 <= p.k; l += 4) {
+      const uint64_t b0 = static_cast<uint64_t>(__double_as_longlong(__ldg(bc + l * p.n))) & kAbsMask;
+      const uint64_t b1 = static_cast<uint64_t>(__double_as_longlong(__ldg(bc + (l + 1) * p.n))) & kAbsMask;
+      const uint64_t b2 = static_cast<uint64_t>(__double_as_longlong(__ldg(bc + (l + 2) * p.n))) & kAbsMask;
+      const uint64_t b3 = static_cast<uint64_t>(__double_as_longlong(__ldg(bc + (l + 3) * p.n))) & kAbsMask;
+      m0 = m0 > b0 ? m0 : b0;
+      m1 = m1 > b1 ? m1 : b1;
+      m2 = m2 > b2 ? m2 : b2;
+      m3 = m3 > b3 ? m3 : b3;
     }
+    for (; l < p.k; ++l) {
+      const uint64_t b = static_cast<uint64_t>(__double_as_longlong(__ldg(bc + l * p.n))) & kAbsMask;
+      m0 = m0 > b ? m0 : b;
+    }
+    m0 = m0 > m1 ? m0 : m1;
+    m2 = m2 > m3 ? m2 : m3;
+    const uint64_t mx = m0 > m2 ? m0 : m2;
     colbits[p.col_begin + col] = mx;
     if (mx >= kInfBits) atomicOr(status, kStatusNonFinite);
   }
