@@ -18,11 +18,17 @@
 // Products are integers of magnitude <= (2^beta - 1)^2; an accumulator that
 // receives at most `window` MMAs (16 products per row each) stays below 2^24
 // and is therefore exact.  The epilogue warps drain each window into exact
-// integer registers, so D_g is exact over all of k, and then fold D_g into an
-// FP64 running sum kept in tensor memory, in the order of step 4.
+// integer registers, so D_g is exact over all of k, and then fold D_g into a
+// running sum in the order of step 4 (exactly in int64 while the partial sum
+// stays below 2^52, in FP64 after).
 //
 // Kernels: oz_rowmax / oz_colmax (step 1, HBM-bound), oz_split_a / oz_split_b
-// (step 2, HBM-bound; write pre-swizzled bf16 tiles), oz_gemm (steps 3-4).
+// (step 2; write pre-swizzled bf16 tiles), oz_gemm2 (steps 3-4: diagonals in
+// pairs sharing operand tiles, int32 window sums, running sums in a
+// workspace scratch; the main kernel), oz_gemm (steps 3-4 one diagonal at a
+// time with int64 sums and the running sum in tensor memory: long k, split-k
+// units, grouped calls, the BF16 comparison mode), oz_splitk_fold (step 4
+// after a split-k product), and the grouped variants of steps 1-2.
 #include <cuda_runtime.h>
 
 #include <cstdint>
