@@ -968,14 +968,14 @@ __global__ void __launch_bounds__(kP2Threads, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < kP2RingA; ++i) {
       mbar_init(&sm.a_full[i], 1);
-      mbar_init(&sm.a_empty[i], 1);  // the step's issuer
+      mbar_init(&sm.a_empty[i], 2);  // one arrival per MMA issuer
     }
     for (int i = 0; i < kP2RingB; ++i) {
       mbar_init(&sm.b_full[i], 1);
-      mbar_init(&sm.b_empty[i], 2);  // the issuers of the two steps that read it
+      mbar_init(&sm.b_empty[i], 2);
     }
     for (int i = 0; i < 4; ++i) {
-      mbar_init(&sm.accfull[i], 2);  // both issuers, at the end of every window
+      mbar_init(&sm.accfull[i], 1);
       mbar_init(&sm.accempty[i], kP2EpiWarps);
     }
     sm.abort_flag = 0;
@@ -992,22 +992,6 @@ __global__ void __launch_bounds__(kP2Threads, 1)
   volatile int* abort_flag = &sm.abort_flag;
   const int64_t ntiles = tiles.count();
   const int ngroups = (S + 1) / 2;
-  // Every MMA accumulates (the issuers share accumulators, so none may
-  // overwrite): the accumulators start at zero, and the epilogue zeroes
-  // each one again when it drains it.
-  if (warp >= 4) {
-    const uint32_t zq = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) +
-                        static_cast<uint32_t>(((warp - 4) >> 2) * 256);
-    uint32_t z[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) z[i] = 0u;
-#pragma unroll 1
-    for (int c = 0; c < 256; c += 32) tmem_st32(zq + c, z);
-    tmem_wait_st();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
 
   if (warp < 4) {
     regs_dec_80();
@@ -1051,66 +1035,52 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       }
     } else if ((warp == 1 || warp == 2) && lane == 0) {
       // ------------------------------------------------ MMA issuers
-      // Two issuing threads take the steps in turn (warp 1 the even steps
-      // of the sequence, warp 2 the odd ones); the owner of a step issues
-      // all its products, A_s x B_{g-s} (diagonal g) and A_s x B_{g-1-s}
-      // (diagonal g-1): 16 MMAs for one round of waits and commits, while
-      // the other thread does its own round.  Both feed the same
-      // accumulators (2x + buffer for diagonal x = 0: g, 1: g-1): the
-      // digit-pair sums are exact integers, so the order in which the two
-      // threads' MMAs land does not matter.  Both walk the whole sequence
-      // so that ring positions and windows agree; at the end of a window
-      // both commit to its barrier (its MMAs are the two threads' own).
-      const uint32_t w = static_cast<uint32_t>(warp - 1);
+      // Two issuing threads: warp 1 issues the products of diagonal g (its
+      // accumulators 0/1), warp 2 those of diagonal g-1 (accumulators 2/3).
+      // One thread cannot issue 128 x 128 x 16 MMAs as fast as the tensor
+      // core retires them; two interleave and keep it busy.  Both walk the
+      // same stage sequence; every ring slot is released by two arrivals,
+      // one per issuer (a commit after its MMAs, or a plain arrival for a
+      // tile it does not read).
+      const int x = warp - 1;
       const uint32_t idesc = idesc_bf16_f32(128, kBN);
       const uint64_t adesc0 = sw128_kmajor_desc(smem_u32(sm.a[0]));
       const uint64_t bdesc0 = sw128_kmajor_desc(smem_u32(sm.b[0]));
       Ring<kP2RingA> ra;
       Ring<kP2RingB> rb;
-      int buf0 = 0, buf1 = 0, cnt0 = 0, cnt1 = 0;
-      bool acq0 = false, acq1 = false;
-      // per accumulator a: bit a of `used` once a window has ended in it,
-      // bit a of `par` the parity of the windows ended in it
-      uint32_t used = 0u, par = 0u;
-      uint32_t step = 0u;
+      int buf = 0, cnt = 0;
+      bool acq = false;
+      uint32_t uses0 = 0u, uses1 = 0u;  // windows started in this issuer's two buffers
       bool ok = true;
-      // wait until the buffer of diagonal x is drained (the window before it)
-      auto acquire = [&](int x) {
-        bool& acq = x ? acq1 : acq0;
+      auto acquire = [&]() {
         if (acq) return true;
-        const int a = 2 * x + (x ? buf1 : buf0);
-        // the drain of the last window that ended in a
-        if (((used >> a) & 1u) &&
-            !mbar_wait_bounded(&sm.accempty[a], ((par >> a) & 1u) ^ 1u, abort_flag, status))
+        const uint32_t u = buf ? uses1 : uses0;
+        const int a = 2 * x + buf;
+        if (u > 0 && !mbar_wait_bounded(&sm.accempty[a], (u - 1u) & 1u, abort_flag, status))
           return false;
         tc_fence_after();
+        if (buf) ++uses1; else ++uses0;
         acq = true;
+        cnt = 0;
         return true;
       };
-      // A thread that issued nothing into a window (one-step windows) still
-      // waits for the drain of the buffer's previous window before it
-      // commits: otherwise it could run two windows ahead and put two
-      // arrivals into one phase of the window barrier.
-      auto window_end = [&](int x) {
-        if (!acquire(x)) return false;
-        int& b = x ? buf1 : buf0;
-        const int a = 2 * x + b;
-        mma_commit(&sm.accfull[a]);
-        used |= 1u << a;
-        par ^= 1u << a;
-        b ^= 1;
-        (x ? acq1 : acq0) = false;
-        return true;
-      };
-      auto mma8 = [&](int x, int aslot, int bslot) {
+      auto mma8 = [&](int aslot, int bslot) {
         const uint64_t da = adesc0 + static_cast<uint64_t>(aslot) * (kOzTileBytes >> 4);
         const uint64_t db = bdesc0 + static_cast<uint64_t>(bslot) * (kOzTileBytes >> 4);
-        const uint32_t d = tmem + static_cast<uint32_t>((2 * x + (x ? buf1 : buf0)) * kBN);
+        const uint32_t d = tmem + static_cast<uint32_t>((2 * x + buf) * kBN);
+        const uint32_t acc0 = cnt > 0 ? 1u : 0u;
 #pragma unroll
         for (int kk = 0; kk < kMmaPerStage; ++kk) {
           const uint64_t off =
               static_cast<uint64_t>((kk >> 2) * (kOzAtomBytes >> 4) + (kk & 3) * 2);
-          mma_bf16_ss(d, da + off, db + off, idesc, 1u);
+          mma_bf16_ss(d, da + off, db + off, idesc, kk > 0 ? 1u : acc0);
+        }
+      };
+      auto finish = [&](bool last) {
+        if (++cnt == window || last) {
+          mma_commit(&sm.accfull[2 * x + buf]);
+          buf ^= 1;
+          acq = false;
         }
       };
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -1119,67 +1089,55 @@ __global__ void __launch_bounds__(kP2Threads, 1)
           const int g = S + 1 - 2 * q;
           const bool pair = g - 1 >= 2;
           for (int64_t kb = 0; kb < Kt && ok; ++kb) {
-            // B_{g-1}: read by the first step of the k-block only
-            int bprev = rb.slot;
-            uint32_t bprev_ph = rb.phase;
-            bool bprev_first = true;
+            if (!mbar_wait_bounded(&sm.b_full[rb.slot], rb.phase, abort_flag, status)) {
+              ok = false;
+              break;
+            }
+            int bprev = rb.slot;  // B_{g-1}: read by diagonal g only
             rb.advance();
+            if (x == 1) mbar_arrive(&sm.b_empty[bprev]);
             for (int s = 1; s <= g - 1; ++s) {
-              const bool own = (step & 1u) == w;
+              if (!mbar_wait_bounded(&sm.a_full[ra.slot], ra.phase, abort_flag, status)) {
+                ok = false;
+                break;
+              }
               const int aslot = ra.slot;
-              const uint32_t aph = ra.phase;
               ra.advance();
-              const bool has1 = pair && s <= g - 2;  // diagonal g-1 has a product
               int bnew = -1;
-              uint32_t bnew_ph = 0u;
-              if (has1) {
+              if (s <= g - 2) {
+                if (!mbar_wait_bounded(&sm.b_full[rb.slot], rb.phase, abort_flag, status)) {
+                  ok = false;
+                  break;
+                }
                 bnew = rb.slot;
-                bnew_ph = rb.phase;
                 rb.advance();
               }
-              if (own) {
-                if (!mbar_wait_bounded(&sm.a_full[aslot], aph, abort_flag, status) ||
-                    !mbar_wait_bounded(&sm.b_full[bprev], bprev_ph, abort_flag, status) ||
-                    (has1 && !mbar_wait_bounded(&sm.b_full[bnew], bnew_ph, abort_flag, status))) {
+              tc_fence_after();
+              if (x == 0) {
+                // diagonal g: A_s x B_{g-s}
+                if (!acquire()) {
                   ok = false;
                   break;
                 }
-                tc_fence_after();
-                if (!acquire(0) || (has1 && !acquire(1))) {
-                  ok = false;
-                  break;
-                }
-                mma8(0, aslot, bprev);
-                if (has1) mma8(1, aslot, bnew);
+                mma8(aslot, bprev);
+                finish(kb == Kt - 1 && s == g - 1);
                 mma_commit(&sm.a_empty[aslot]);
                 mma_commit(&sm.b_empty[bprev]);
-                if (has1) mma_commit(&sm.b_empty[bnew]);
-              } else if (bprev_first) {
-                // the k-block's first B tile: read by the other thread only
-                if (!mbar_wait_bounded(&sm.b_full[bprev], bprev_ph, abort_flag, status)) {
+              } else if (pair && s <= g - 2) {
+                // diagonal g-1: A_s x B_{g-1-s}
+                if (!acquire()) {
                   ok = false;
                   break;
                 }
-                mbar_arrive(&sm.b_empty[bprev]);
-              }
-              if (++cnt0 == window || (kb == Kt - 1 && s == g - 1)) {
-                cnt0 = 0;
-                if (!window_end(0)) {
-                  ok = false;
-                  break;
-                }
-              }
-              if (has1 && (++cnt1 == window || (kb == Kt - 1 && s == g - 2))) {
-                cnt1 = 0;
-                if (!window_end(1)) {
-                  ok = false;
-                  break;
-                }
+                mma8(aslot, bnew);
+                finish(kb == Kt - 1 && s == g - 2);
+                mma_commit(&sm.a_empty[aslot]);
+                mma_commit(&sm.b_empty[bnew]);
+              } else {
+                mbar_arrive(&sm.a_empty[aslot]);
+                if (bnew >= 0) mbar_arrive(&sm.b_empty[bnew]);
               }
               bprev = bnew;
-              bprev_ph = bnew_ph;
-              bprev_first = false;
-              ++step;
             }
           }
         }
@@ -1212,15 +1170,6 @@ __global__ void __launch_bounds__(kP2Threads, 1)
         tmem_wait_ld();
 #pragma unroll
         for (int i = 0; i < 32; ++i) Dx[h * 32 + i] += __float2int_rz(__uint_as_float(r[i]));
-      }
-      {
-        // zero the window for the next one (every MMA accumulates)
-        uint32_t z[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) z[i] = 0u;
-        tmem_st32(t_win, z);
-        tmem_st32(t_win + 32, z);
-        tmem_wait_st();
       }
       tc_fence_before();
       __syncwarp();
