@@ -389,10 +389,19 @@ def run_ours(args):
     # ---- CPU oracle on a bounded sample
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
+        import oracle
         rate, threads, rows, secs = cpu_oracle_rate(A_h, B_h, args.cpu_seconds)
         cpu = {"value": rate, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
                "sample": f"naive FP64 triple loop (OpenMP over rows) on {rows} of {n} rows "
                          f"of the same product, {secs:.1f} s"}
+        # the same loop on one core, as the paper's single-core panels
+        oracle.set_threads(1)
+        try:
+            rate1, _, rows1, secs1 = cpu_oracle_rate(A_h, B_h, args.cpu_seconds / 3)
+        finally:
+            oracle.set_threads(threads)
+        cpu["one_core"] = {"value": rate1, "unit": "TFLOP/s", "cores": 1,
+                           "sample": f"{rows1} of {n} rows, {secs1:.1f} s"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world,

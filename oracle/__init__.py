@@ -96,6 +96,8 @@ def _load():
     lib.oracle_round_bf16.restype = None
     lib.oracle_num_threads.argtypes = []
     lib.oracle_num_threads.restype = I
+    lib.oracle_set_threads.argtypes = [I]
+    lib.oracle_set_threads.restype = I
     _lib = lib
     return lib
 
@@ -118,6 +120,11 @@ def _dims(A, B):
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle's loops from now on; returns the count."""
+    return int(_load().oracle_set_threads(int(n)))
 
 
 def _gemm(name, A, B):

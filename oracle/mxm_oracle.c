@@ -54,6 +54,18 @@ int oracle_num_threads(void) {
 #endif
 }
 
+/* Threads the OpenMP loops use from now on (n >= 1); returns the count in
+   effect.  Lets a caller time the same loop on one core and on all. */
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------ */
 /* Plain definition: c_ij = sum_{l=0}^{k-1} a_il * b_lj  (Sec. 3.1).   */
 /* ------------------------------------------------------------------ */
