@@ -56,7 +56,8 @@ typedef enum {
   MXM_MODE_EMUL_I8 = 1,    /* Ozaki split, 7-bit digits (int8 range) in BF16 */
   MXM_MODE_EMUL_BF16 = 2,  /* Ozaki split, 8-bit digits (full BF16 significand) */
   MXM_MODE_F32 = 3,        /* comparison: inputs rounded to FP32, FP32 sums */
-  MXM_MODE_BF16_F32ACC = 4 /* comparison: inputs rounded to BF16, FP32 sums */
+  MXM_MODE_BF16_F32ACC = 4, /* comparison: inputs rounded to BF16, FP32 sums */
+  MXM_MODE_EMUL_FP8 = 5    /* Ozaki split, 4-bit digits carried in FP8 E4M3 */
 } mxm_mode;
 
 /* One problem of a grouped call (device-resident table of these). */
@@ -101,12 +102,16 @@ mxm_status mxm_f64_emul(const double* A, const double* B, double* C, int64_t m, 
                         int64_t n, int slices, void* stream);
 
 /*
- * mxm_gemm -- C = A.B in the given mxm_mode (slices is used by the two
+ * mxm_gemm -- C = A.B in the given mxm_mode (slices is used by the
  * emulated modes and ignored otherwise).  MXM_MODE_F64 is mxm_f64 and
  * MXM_MODE_EMUL_I8 is mxm_f64_emul; MXM_MODE_EMUL_BF16 takes 8-bit digits
- * (6 slices ~ 7 of the 7-bit form); the FP32 and BF16 modes round A and B to
- * the narrow type and sum in FP32: they are reported beside the FP64 modes,
- * not FP64-accurate.
+ * (6 slices ~ 7 of the 7-bit form); MXM_MODE_EMUL_FP8 takes 4-bit digits
+ * (|d| <= 15, exact in FP8 E4M3) on the FP8 tensor path, 1..16 slices, about
+ * twice as many as the 7-bit form for the same accuracy, and returns
+ * MXM_ERR_UNSUPPORTED when the per-diagonal sums would not fit int32
+ * (S 225 k >= 2^31, i.e. k beyond ~600 000) -- it has no grouped form.  The
+ * FP32 and BF16 modes round A and B to the narrow type and sum in FP32: they
+ * are reported beside the FP64 modes, not FP64-accurate.
  */
 mxm_status mxm_gemm(int mode, const double* A, const double* B, double* C, int64_t m, int64_t k,
                     int64_t n, int slices, void* stream);

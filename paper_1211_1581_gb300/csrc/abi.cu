@@ -147,6 +147,7 @@ size_t workspace_bytes(int mode, int64_t m, int64_t k, int64_t n, int slices) {
   if (mode == MXM_MODE_F64) return f64_workspace(f64_dims(m, k, n));
   if (emul_mode(mode))
     return ozaki_layout(ozaki_dims_splitk(m, k, n, slices, mode_beta(mode))).total;
+  if (mode == MXM_MODE_EMUL_FP8) return ozaki_layout(ozaki_dims_fp8(m, k, n, slices)).total;
   if (mode == MXM_MODE_BF16_F32ACC) return ozaki_layout(ozaki_dims(m, k, n, 1, 8)).total;
   return 0;
 }
@@ -167,6 +168,22 @@ mxm_status run_gemm(int mode, const double* A, const double* B, double* C, int64
     profile_mark(ce, 3, s);
   } else if (emul_mode(mode)) {
     const OzakiDims d = ozaki_dims_splitk(m, k, n, slices, mode_beta(mode));
+    const OzakiLayout L = ozaki_layout(d);
+    uint64_t* rowbits = reinterpret_cast<uint64_t*>(ws + L.rowbits);
+    uint64_t* colbits = reinterpret_cast<uint64_t*>(ws + L.colbits);
+    CallEvents* ce = profile_begin(s);
+    e = launch_ozaki_scale(A, B, d, rowbits, colbits, status, s);
+    profile_mark(ce, 1, s);
+    if (e == cudaSuccess)
+      e = launch_ozaki_split(A, B, d, rowbits, colbits, ws + L.aslices, ws + L.bslices, s);
+    profile_mark(ce, 2, s);
+    if (e == cudaSuccess)
+      e = launch_ozaki_gemm(ws + L.aslices, ws + L.bslices, rowbits, colbits, C, d,
+                            reinterpret_cast<uint64_t*>(ws + L.sums), status, s);
+    profile_mark(ce, 3, s);
+  } else if (mode == MXM_MODE_EMUL_FP8) {
+    const OzakiDims d = ozaki_dims_fp8(m, k, n, slices);
+    if (!ozaki_narrow(d.S, d.beta, d.Kt)) return MXM_ERR_UNSUPPORTED;
     const OzakiLayout L = ozaki_layout(d);
     uint64_t* rowbits = reinterpret_cast<uint64_t*>(ws + L.rowbits);
     uint64_t* colbits = reinterpret_cast<uint64_t*>(ws + L.colbits);
@@ -203,6 +220,8 @@ mxm_status run_gemm(int mode, const double* A, const double* B, double* C, int64
 mxm_status check_mode(int mode, int slices) {
   if (mode == MXM_MODE_F64 || mode == MXM_MODE_F32 || mode == MXM_MODE_BF16_F32ACC) return MXM_OK;
   if (emul_mode(mode)) return (slices >= 1 && slices <= kOzMaxSlices) ? MXM_OK : MXM_ERR_UNSUPPORTED;
+  if (mode == MXM_MODE_EMUL_FP8)
+    return (slices >= 1 && slices <= kOzMaxSlicesE4m3) ? MXM_OK : MXM_ERR_UNSUPPORTED;
   return MXM_ERR_UNSUPPORTED;
 }
 

@@ -54,11 +54,22 @@ __host__ __device__ inline int oz_chunk_offset(int r, int c) {
 }
 constexpr int kOzMaxSlices = 12;
 
+// The 4-bit-digit engine: digits |d| <= 15 carried in FP8 E4M3 (every
+// integer up to 16 is exact there) through tcgen05 kind::f8f6f4.  A tile is
+// 128 rows x 128 k of one byte: a single 128-byte-swizzle atom of 16 KiB, the
+// 16-byte chunk c (k = 16c .. 16c+15) of row r at chunk position c ^ (r % 8).
+constexpr int kOzTileBytesE4m3 = kOzTileRows * kOzTileK;
+constexpr int kOzMaxSlicesE4m3 = 16;
+__host__ __device__ inline int oz_chunk_offset_e4m3(int r, int c) {
+  return r * 128 + ((c ^ (r & 7)) << 4);
+}
+
 struct OzakiDims {
   int64_t m, k, n;
   int64_t Mt, Nt, Kt;  // tiles of 128 rows of A, 128 columns of B, 128 of k
   int S, beta;
   int64_t splits;      // k ranges per C tile (1: no split-k)
+  int fp8;             // 1: digits carried in E4M3 (beta = 4), 0: in bf16
 };
 
 inline OzakiDims ozaki_dims(int64_t m, int64_t k, int64_t n, int S, int beta) {
@@ -69,7 +80,19 @@ inline OzakiDims ozaki_dims(int64_t m, int64_t k, int64_t n, int S, int beta) {
   d.Kt = (k + kOzTileK - 1) / kOzTileK;
   d.S = S; d.beta = beta;
   d.splits = 1;
+  d.fp8 = 0;
   return d;
+}
+
+// The 4-bit-digit E4M3 engine (paired kernel only: no split-k).
+inline OzakiDims ozaki_dims_fp8(int64_t m, int64_t k, int64_t n, int S) {
+  OzakiDims d = ozaki_dims(m, k, n, S, 4);
+  d.fp8 = 1;
+  return d;
+}
+
+inline size_t ozaki_tile_bytes(const OzakiDims& d) {
+  return d.fp8 ? kOzTileBytesE4m3 : kOzTileBytes;
 }
 
 // The same with split-k where the product has fewer C tiles than SMs (each
@@ -94,8 +117,8 @@ inline OzakiLayout ozaki_layout(const OzakiDims& d) {
   size_t off = 0;
   L.rowbits = off; off = align_up(off + sizeof(uint64_t) * (size_t)(d.m > 0 ? d.m : 1), 1024);
   L.colbits = off; off = align_up(off + sizeof(uint64_t) * (size_t)(d.n > 0 ? d.n : 1), 1024);
-  L.aslices = off; off = align_up(off + (size_t)d.S * d.Mt * d.Kt * kOzTileBytes, 1024);
-  L.bslices = off; off = align_up(off + (size_t)d.S * d.Nt * d.Kt * kOzTileBytes, 1024);
+  L.aslices = off; off = align_up(off + (size_t)d.S * d.Mt * d.Kt * ozaki_tile_bytes(d), 1024);
+  L.bslices = off; off = align_up(off + (size_t)d.S * d.Nt * d.Kt * ozaki_tile_bytes(d), 1024);
   // running sums of the recombination between diagonal pairs: per C tile
   // 128 x 128 x 8 bytes, column-major inside the tile (so that a warp, which
   // owns 32 consecutive rows, touches 256 contiguous bytes per column).
@@ -108,6 +131,15 @@ inline OzakiLayout ozaki_layout(const OzakiDims& d) {
   L.sums = off; off = align_up(off + sums, 1024);
   L.total = off;
   return L;
+}
+
+// Whether the per-diagonal integer sums of a tile with Kt k-blocks fit in
+// int32, the condition of the paired slice GEMM: every digit product is at
+// most (2^beta - 1)^2 and a diagonal has at most S of them per k.
+__host__ __device__ inline bool ozaki_narrow(int S, int beta, int64_t Kt) {
+  const double dmax = static_cast<double>((1 << beta) - 1);
+  return static_cast<double>(S) * dmax * dmax * kOzTileK * static_cast<double>(Kt) <
+         2147483647.0;
 }
 
 // Largest number of K=16 MMAs whose integer products can be summed in an

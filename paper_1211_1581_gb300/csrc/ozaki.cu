@@ -172,38 +172,60 @@ __device__ __forceinline__ void split_chunk_store(const double (&x)[8], int e, i
 
 // The same for beta * S <= 64: the fraction |x| 2^-e is first put in one
 // 64-bit fixed-point word F = floor(|x| 2^{beta S - e}) (one shift), then
-// digit s is the field F >> beta (S - s) (a shift uniform over the warp) and
-// its bf16 pattern is the upper half of the FP32 pattern of the integer
-// (exact: at most 8 significant bits).
-__device__ __forceinline__ void split_chunk_store_w64(const double (&x)[8], int e, int S,
+// digit s is the field F >> beta (S - s) (a shift uniform over the warp).
+// V values per 16-byte chunk: V = 8 bf16 digits (the bf16 pattern is the
+// upper half of the FP32 pattern of the integer, exact: at most 8
+// significant bits), or V = 16 E4M3 digits (|d| <= 15, from a 16-entry
+// table of the E4M3 codes of 0..15).
+template <int V>
+__device__ __forceinline__ void split_chunk_store_w64(const double (&x)[V], int e, int S,
                                                       int beta, uint8_t* dst,
                                                       size_t slice_stride) {
-  uint64_t F[8];
-  uint32_t sg[8];
+  uint64_t F[V];
+  uint32_t sg[V];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
+  for (int j = 0; j < V; ++j) {
     const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x[j]));
     const int be = static_cast<int>((b >> 52) & 0x7FF);
     const uint64_t mant = b & 0x000FFFFFFFFFFFFFull;
     const uint64_t M = be ? (mant | 0x0010000000000000ull) : mant;
     const int sh = (be ? be - 1075 : -1074) - e + beta * S;
     F[j] = sh >= 0 ? (sh < 64 ? M << sh : 0ull) : (-sh < 64 ? M >> -sh : 0ull);
-    sg[j] = static_cast<uint32_t>(b >> 63) << 15;
+    sg[j] = static_cast<uint32_t>(b >> 63);
   }
   const uint32_t mask = (1u << beta) - 1u;
   for (int s = 1; s <= S; ++s) {
     const int p = beta * (S - s);
     uint32_t packed[4];
+    if constexpr (V == 8) {
 #pragma unroll
-    for (int j = 0; j < 8; j += 2) {
-      uint32_t bits2[2];
+      for (int j = 0; j < 8; j += 2) {
+        uint32_t bits2[2];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const uint32_t mag = static_cast<uint32_t>(F[j + h] >> p) & mask;
-        const uint32_t hi = __float_as_uint(__uint2float_rn(mag)) >> 16;
-        bits2[h] = mag ? (hi | sg[j + h]) : 0u;
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t mag = static_cast<uint32_t>(F[j + h] >> p) & mask;
+          const uint32_t hi = __float_as_uint(__uint2float_rn(mag)) >> 16;
+          bits2[h] = mag ? (hi | (sg[j + h] << 15)) : 0u;
+        }
+        packed[j >> 1] = bits2[0] | (bits2[1] << 16);
       }
-      packed[j >> 1] = bits2[0] | (bits2[1] << 16);
+    } else {
+      // E4M3 codes of 0..7 and 8..15, one byte each
+      constexpr uint64_t kLo = 0x4E4C4A4844403800ull, kHi = 0x5756555453525150ull;
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const int j = 4 * w + h;
+          const uint32_t mag = static_cast<uint32_t>(F[j] >> p) & mask;
+          const uint64_t tbl = mag < 8 ? kLo : kHi;
+          uint32_t code = static_cast<uint32_t>(tbl >> (8 * (mag & 7))) & 0xFFu;
+          if (mag) code |= sg[j] << 7;
+          word |= code << (8 * h);
+        }
+        packed[w] = word;
+      }
     }
     *reinterpret_cast<uint4*>(dst + static_cast<size_t>(s - 1) * slice_stride) =
         make_uint4(packed[0], packed[1], packed[2], packed[3]);
@@ -213,54 +235,72 @@ __device__ __forceinline__ void split_chunk_store_w64(const double (&x)[8], int 
 __device__ __forceinline__ void split_chunk(const double (&x)[8], int e, int S, int beta,
                                             uint8_t* dst, size_t slice_stride) {
   if (beta * S <= 64)
-    split_chunk_store_w64(x, e, S, beta, dst, slice_stride);
+    split_chunk_store_w64<8>(x, e, S, beta, dst, slice_stride);
   else
     split_chunk_store(x, e, S, beta, dst, slice_stride);
 }
+__device__ __forceinline__ void split_chunk(const double (&x)[16], int e, int S, int beta,
+                                            uint8_t* dst, size_t slice_stride) {
+  split_chunk_store_w64<16>(x, e, S, beta, dst, slice_stride);  // beta = 4, S <= 16
+}
+
+// Tile geometry of the two digit carriers: V digits per 16-byte chunk.
+template <int V>
+struct SplitGeo {
+  static constexpr int kChunksPerRow = kOzTileK / V;
+  static constexpr int kTileBytes = V == 8 ? kOzTileBytes : kOzTileBytesE4m3;
+  __device__ static int offset(int r, int c) {
+    return V == 8 ? oz_chunk_offset(r, c) : oz_chunk_offset_e4m3(r, c);
+  }
+};
 
 // One 128 x 128 tile (tm, tk) of A (m x k, row-major) -> its S digit tiles,
-// `slice_stride` bytes apart.  A thread takes 8 consecutive k of one row
+// `slice_stride` bytes apart.  A thread takes V consecutive k of one row
 // (consecutive threads: consecutive chunks of a row, so the loads and the
 // 16-byte stores are contiguous); rows of even k are read as 16-byte pairs.
+template <int V>
 __device__ __forceinline__ void split_a_tile(const double* __restrict__ A, int64_t m, int64_t k,
                                              const uint64_t* __restrict__ rowbits, int S,
                                              int beta, int64_t tm, int64_t tk, uint8_t* tile,
                                              size_t slice_stride) {
+  using G = SplitGeo<V>;
   const bool pairs = ((k & 1) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
 #pragma unroll 2
-  for (int p = threadIdx.x; p < kOzTileRows * kOzChunksPerRow; p += blockDim.x) {
-    const int c = p % kOzChunksPerRow, r = p / kOzChunksPerRow;
+  for (int p = threadIdx.x; p < kOzTileRows * G::kChunksPerRow; p += blockDim.x) {
+    const int c = p % G::kChunksPerRow, r = p / G::kChunksPerRow;
     const int64_t row = tm * kOzTileRows + r;
-    const int64_t k0 = tk * kOzTileK + c * 8;
-    double v[8];
+    const int64_t k0 = tk * kOzTileK + c * V;
+    double v[V];
     int e = 0;
     if (row < m) e = exponent_from_absbits(rowbits[row]);
     const double* src = A + row * k + k0;
-    if (row < m && pairs && k0 + 8 <= k) {
+    if (row < m && pairs && k0 + V <= k) {
 #pragma unroll
-      for (int j = 0; j < 8; j += 2) {
+      for (int j = 0; j < V; j += 2) {
         const double2 t = __ldg(reinterpret_cast<const double2*>(src + j));
         v[j] = t.x;
         v[j + 1] = t.y;
       }
     } else {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = (row < m && k0 + j < k) ? __ldg(src + j) : 0.0;
+      for (int j = 0; j < V; ++j) v[j] = (row < m && k0 + j < k) ? __ldg(src + j) : 0.0;
     }
-    split_chunk(v, e, S, beta, tile + oz_chunk_offset(r, c), slice_stride);
+    split_chunk(v, e, S, beta, tile + G::offset(r, c), slice_stride);
   }
 }
 
 // One tile (tn, tk) of B^T, i.e. 128 columns j x 128 k of B (k x n,
 // row-major) -> its S digit tiles: both MMA operands are K-major.  The tile
 // is read in four passes of 32 rows of B (coalesced along the rows) through
-// shared memory, then every thread takes 8 consecutive k of one column.
+// shared memory, then every thread takes V consecutive k of one column.
 constexpr int kSplitBRows = 32;
+template <int V>
 __device__ __forceinline__ void split_b_tile(const double* __restrict__ B, int64_t k, int64_t n,
                                              const uint64_t* __restrict__ colbits, int S,
                                              int beta, int64_t tn, int64_t tk, uint8_t* tile,
                                              size_t slice_stride,
                                              double (*sb)[kOzTileRows + 1]) {
+  using G = SplitGeo<V>;
   const int64_t col0 = tn * kOzTileRows;
   for (int pass = 0; pass < kOzTileK / kSplitBRows; ++pass) {
     const int64_t l0 = tk * kOzTileK + pass * kSplitBRows;
@@ -270,39 +310,43 @@ __device__ __forceinline__ void split_b_tile(const double* __restrict__ B, int64
       sb[lr][cc] = (l < k && col < n) ? __ldg(B + l * n + col) : 0.0;
     }
     __syncthreads();
-    constexpr int kChunks = kSplitBRows / 8;  // chunks of 8 k per column in a pass
+    constexpr int kChunks = kSplitBRows / V;  // chunks of V k per column in a pass
     for (int p = threadIdx.x; p < kOzTileRows * kChunks; p += blockDim.x) {
       const int r = p % kOzTileRows, cl = p / kOzTileRows;
       const int64_t col = col0 + r;
       const int f = col < n ? exponent_from_absbits(colbits[col]) : 0;
-      double v[8];
+      double v[V];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = sb[cl * 8 + j][r];
-      split_chunk(v, f, S, beta, tile + oz_chunk_offset(r, pass * kChunks + cl), slice_stride);
+      for (int j = 0; j < V; ++j) v[j] = sb[cl * V + j][r];
+      split_chunk(v, f, S, beta, tile + G::offset(r, pass * kChunks + cl), slice_stride);
     }
     __syncthreads();
   }
 }
 
 // A -> A_s tiles [S][Mt][Kt].
+template <int V>
 __global__ void __launch_bounds__(256) oz_split_a_kernel(
     const double* __restrict__ A, int64_t m, int64_t k, const uint64_t* __restrict__ rowbits,
     int S, int beta, int64_t Mt, int64_t Kt, uint8_t* __restrict__ aslices) {
+  constexpr size_t kTile = SplitGeo<V>::kTileBytes;
   const int64_t tk = blockIdx.x, tm = blockIdx.y;
-  split_a_tile(A, m, k, rowbits, S, beta, tm, tk,
-               aslices + (static_cast<size_t>(tm) * Kt + tk) * kOzTileBytes,
-               static_cast<size_t>(Mt) * Kt * kOzTileBytes);
+  split_a_tile<V>(A, m, k, rowbits, S, beta, tm, tk,
+                  aslices + (static_cast<size_t>(tm) * Kt + tk) * kTile,
+                  static_cast<size_t>(Mt) * Kt * kTile);
 }
 
 // B -> B_t tiles [S][Nt][Kt].
+template <int V>
 __global__ void __launch_bounds__(256) oz_split_b_kernel(
     const double* __restrict__ B, int64_t k, int64_t n, const uint64_t* __restrict__ colbits,
     int S, int beta, int64_t Nt, int64_t Kt, uint8_t* __restrict__ bslices) {
+  constexpr size_t kTile = SplitGeo<V>::kTileBytes;
   __shared__ double sb[kSplitBRows][kOzTileRows + 1];
   const int64_t tk = blockIdx.x, tn = blockIdx.y;
-  split_b_tile(B, k, n, colbits, S, beta, tn, tk,
-               bslices + (static_cast<size_t>(tn) * Kt + tk) * kOzTileBytes,
-               static_cast<size_t>(Nt) * Kt * kOzTileBytes, sb);
+  split_b_tile<V>(B, k, n, colbits, S, beta, tn, tk,
+                  bslices + (static_cast<size_t>(tn) * Kt + tk) * kTile,
+                  static_cast<size_t>(Nt) * Kt * kTile, sb);
 }
 
 // ---------------------------------------------------------------- grouped steps 1-2
@@ -396,14 +440,14 @@ __global__ void __launch_bounds__(256) oz_grouped_split_kernel(uint8_t* __restri
     if (t < na) {
       const GroupedProblem& p = recs[grouped_find(recs, hdr->count, t, &GroupedProblem::atile_begin)];
       const int64_t local = t - p.atile_begin;
-      split_a_tile(p.A, p.m, p.k, rowbits + p.row_begin, S, beta, local / p.Kt, local % p.Kt,
+      split_a_tile<8>(p.A, p.m, p.k, rowbits + p.row_begin, S, beta, local / p.Kt, local % p.Kt,
                    ws + hdr->off_a + static_cast<size_t>(t) * kOzTileBytes,
                    static_cast<size_t>(na) * kOzTileBytes);
     } else {
       const int64_t tb = t - na;
       const GroupedProblem& p = recs[grouped_find(recs, hdr->count, tb, &GroupedProblem::btile_begin)];
       const int64_t local = tb - p.btile_begin;
-      split_b_tile(p.B, p.k, p.n, colbits + p.col_begin, S, beta, local / p.Kt, local % p.Kt,
+      split_b_tile<8>(p.B, p.k, p.n, colbits + p.col_begin, S, beta, local / p.Kt, local % p.Kt,
                    ws + hdr->off_b + static_cast<size_t>(tb) * kOzTileBytes,
                    static_cast<size_t>(nb) * kOzTileBytes, sb);
     }
@@ -530,6 +574,7 @@ struct OzSingle {
   uint64_t* sums;     // running sums (paired kernel), or the split-k partials
   int64_t splits;     // k ranges per C tile; > 1: units write partials
   int S;
+  int64_t tile_bytes; // operand tile size of the digit carrier
   __device__ __forceinline__ int64_t count() const { return Mt * Nt * splits; }
   // Unit t: C tile t / splits, k range t % splits.
   __device__ __forceinline__ OzTile tile(int64_t t) const {
@@ -538,10 +583,10 @@ struct OzSingle {
     tile_coords(tt, Mt, Nt, tm, tn);
     const int64_t kb0 = Kt * sp / splits, kb1 = Kt * (sp + 1) / splits;
     OzTile j;
-    j.a_slice = static_cast<size_t>(Mt) * Kt * kOzTileBytes;
-    j.b_slice = static_cast<size_t>(Nt) * Kt * kOzTileBytes;
-    j.a = aslices + static_cast<size_t>(tm * Kt + kb0) * kOzTileBytes;
-    j.b = bslices + static_cast<size_t>(tn * Kt + kb0) * kOzTileBytes;
+    j.a_slice = static_cast<size_t>(Mt) * Kt * tile_bytes;
+    j.b_slice = static_cast<size_t>(Nt) * Kt * tile_bytes;
+    j.a = aslices + static_cast<size_t>(tm * Kt + kb0) * tile_bytes;
+    j.b = bslices + static_cast<size_t>(tn * Kt + kb0) * tile_bytes;
     j.Kt = kb1 - kb0;
     j.rowbits = rowbits;
     j.colbits = colbits;
@@ -925,21 +970,48 @@ __global__ void __launch_bounds__(kThreads, 1)
 // registers to warpgroups 1-2 (the epilogue: two diagonals of exact int32
 // sums).
 constexpr int kP2Threads = 384;
-constexpr int kP2RingA = 3;  // an A tile serves one step
-constexpr int kP2RingB = 4;  // a B tile serves two steps: one more slot of look-ahead
+// Operand formats of the paired kernel.  Digits carried in bf16: 32 KiB
+// tiles (two 64-k atoms), 8 MMAs of K = 16 per k-block, rings of 3 A and 4 B
+// tiles (a B tile serves two steps: one more slot of look-ahead).  Digits
+// carried in E4M3: 16 KiB tiles (one 128-k atom), 4 MMAs of K = 32, rings
+// twice as deep in the same shared memory.
+struct FmtBf16 {
+  static constexpr int kTileBytes = kOzTileBytes;
+  static constexpr int kMmas = 8;
+  static constexpr int kRingA = 3, kRingB = 4;
+  __device__ static uint32_t idesc() { return idesc_bf16_f32(128, kOzTileRows); }
+  __device__ static uint64_t koff(int kk) {  // k step kk: atom kk / 4, 32 bytes per step inside it
+    return static_cast<uint64_t>((kk >> 2) * (kOzAtomBytes >> 4) + (kk & 3) * 2);
+  }
+  __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    mma_bf16_ss(d, a, b, idesc, acc);
+  }
+};
+struct FmtE4m3 {
+  static constexpr int kTileBytes = kOzTileBytesE4m3;
+  static constexpr int kMmas = 4;
+  static constexpr int kRingA = 6, kRingB = 8;
+  __device__ static uint32_t idesc() { return idesc_e4m3_f32(128, kOzTileRows); }
+  __device__ static uint64_t koff(int kk) { return static_cast<uint64_t>(kk * 2); }
+  __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    mma_e4m3_ss(d, a, b, idesc, acc);
+  }
+};
 constexpr int kP2EpiWarps = 8;
 
+template <typename Fmt>
 struct __align__(1024) Gemm2Smem {
-  uint8_t a[kP2RingA][kOzTileBytes];
-  uint8_t b[kP2RingB][kOzTileBytes];
-  uint64_t a_full[kP2RingA], a_empty[kP2RingA];
-  uint64_t b_full[kP2RingB], b_empty[kP2RingB];
+  uint8_t a[Fmt::kRingA][Fmt::kTileBytes];
+  uint8_t b[Fmt::kRingB][Fmt::kTileBytes];
+  uint64_t a_full[Fmt::kRingA], a_empty[Fmt::kRingA];
+  uint64_t b_full[Fmt::kRingB], b_empty[Fmt::kRingB];
   uint64_t accfull[4], accempty[4];  // accumulator 2x + buffer; x = 0: diagonal g, 1: g-1
   uint32_t tmem_base;
   int abort_flag;
 };
 
-constexpr size_t kGemm2SmemBytes = sizeof(Gemm2Smem) + 1024;
+template <typename Fmt>
+constexpr size_t gemm2_smem_bytes() { return sizeof(Gemm2Smem<Fmt>) + 1024; }
 
 // One ring of N shared-memory slots with full/empty barriers.
 template <int N>
@@ -956,21 +1028,22 @@ struct Ring {
 
 // The fold of one diagonal g into a running sum held as 64 bits: an exact
 // int64 partial (units of 2^{-beta (S+1)}) while g >= gx, an FP64 value after.
-template <typename Tiles>
+template <typename Tiles, typename Fmt>
 __global__ void __launch_bounds__(kP2Threads, 1)
     oz_gemm2_kernel(const Tiles tiles, int S, int beta, int window, int* __restrict__ status) {
+  constexpr int kRingA = Fmt::kRingA, kRingB = Fmt::kRingB, kTile = Fmt::kTileBytes;
   extern __shared__ uint8_t smem_raw[];
-  Gemm2Smem& sm = *reinterpret_cast<Gemm2Smem*>(
+  Gemm2Smem<Fmt>& sm = *reinterpret_cast<Gemm2Smem<Fmt>*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kP2RingA; ++i) {
+    for (int i = 0; i < kRingA; ++i) {
       mbar_init(&sm.a_full[i], 1);
       mbar_init(&sm.a_empty[i], 2);  // one arrival per MMA issuer
     }
-    for (int i = 0; i < kP2RingB; ++i) {
+    for (int i = 0; i < kRingB; ++i) {
       mbar_init(&sm.b_full[i], 1);
       mbar_init(&sm.b_empty[i], 2);
     }
@@ -997,14 +1070,14 @@ __global__ void __launch_bounds__(kP2Threads, 1)
     regs_dec_80();
     if (warp == 0 && lane == 0) {
       // ------------------------------------------------ producer (bulk copies)
-      Ring<kP2RingA> ra;
-      Ring<kP2RingB> rb;
+      Ring<kRingA> ra;
+      Ring<kRingB> rb;
       bool ok = true;
-      auto load = [&](auto& r, uint8_t (*buf)[kOzTileBytes], uint64_t* full, uint64_t* empty,
+      auto load = [&](auto& r, uint8_t (*buf)[Fmt::kTileBytes], uint64_t* full, uint64_t* empty,
                       const uint8_t* src) {
         if (!mbar_wait_bounded(&empty[r.slot], r.phase ^ 1u, abort_flag, status)) return false;
-        mbar_arrive_expect_tx(&full[r.slot], kOzTileBytes);
-        bulk_g2s(buf[r.slot], src, kOzTileBytes, &full[r.slot]);
+        mbar_arrive_expect_tx(&full[r.slot], kTile);
+        bulk_g2s(buf[r.slot], src, kTile, &full[r.slot]);
         r.advance();
         return true;
       };
@@ -1013,7 +1086,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
         for (int q = 0; q < ngroups && ok; ++q) {
           const int g = S + 1 - 2 * q;
           for (int64_t kb = 0; kb < j.Kt && ok; ++kb) {
-            const size_t koff = static_cast<size_t>(kb) * kOzTileBytes;
+            const size_t koff = static_cast<size_t>(kb) * kTile;
             ok = load(rb, sm.b, sm.b_full, sm.b_empty, j.b + (g - 2) * j.b_slice + koff);
             for (int s = 1; s <= g - 1 && ok; ++s) {
               ok = load(ra, sm.a, sm.a_full, sm.a_empty, j.a + (s - 1) * j.a_slice + koff);
@@ -1025,11 +1098,11 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       }
       // tail: wait until every slot is released so no copy or commit lands
       // after the block has exited
-      for (int i = 0; i < kP2RingA; ++i) {
+      for (int i = 0; i < kRingA; ++i) {
         if (!mbar_wait_bounded(&sm.a_empty[ra.slot], ra.phase ^ 1u, abort_flag, status)) break;
         ra.advance();
       }
-      for (int i = 0; i < kP2RingB; ++i) {
+      for (int i = 0; i < kRingB; ++i) {
         if (!mbar_wait_bounded(&sm.b_empty[rb.slot], rb.phase ^ 1u, abort_flag, status)) break;
         rb.advance();
       }
@@ -1043,11 +1116,11 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       // one per issuer (a commit after its MMAs, or a plain arrival for a
       // tile it does not read).
       const int x = warp - 1;
-      const uint32_t idesc = idesc_bf16_f32(128, kBN);
+      const uint32_t idesc = Fmt::idesc();
       const uint64_t adesc0 = sw128_kmajor_desc(smem_u32(sm.a[0]));
       const uint64_t bdesc0 = sw128_kmajor_desc(smem_u32(sm.b[0]));
-      Ring<kP2RingA> ra;
-      Ring<kP2RingB> rb;
+      Ring<kRingA> ra;
+      Ring<kRingB> rb;
       int buf = 0, cnt = 0;
       bool acq = false;
       uint32_t uses0 = 0u, uses1 = 0u;  // windows started in this issuer's two buffers
@@ -1065,15 +1138,14 @@ __global__ void __launch_bounds__(kP2Threads, 1)
         return true;
       };
       auto mma8 = [&](int aslot, int bslot) {
-        const uint64_t da = adesc0 + static_cast<uint64_t>(aslot) * (kOzTileBytes >> 4);
-        const uint64_t db = bdesc0 + static_cast<uint64_t>(bslot) * (kOzTileBytes >> 4);
+        const uint64_t da = adesc0 + static_cast<uint64_t>(aslot) * (kTile >> 4);
+        const uint64_t db = bdesc0 + static_cast<uint64_t>(bslot) * (kTile >> 4);
         const uint32_t d = tmem + static_cast<uint32_t>((2 * x + buf) * kBN);
         const uint32_t acc0 = cnt > 0 ? 1u : 0u;
 #pragma unroll
-        for (int kk = 0; kk < kMmaPerStage; ++kk) {
-          const uint64_t off =
-              static_cast<uint64_t>((kk >> 2) * (kOzAtomBytes >> 4) + (kk & 3) * 2);
-          mma_bf16_ss(d, da + off, db + off, idesc, kk > 0 ? 1u : acc0);
+        for (int kk = 0; kk < Fmt::kMmas; ++kk) {
+          const uint64_t off = Fmt::koff(kk);
+          Fmt::mma(d, da + off, db + off, idesc, kk > 0 ? 1u : acc0);
         }
       };
       auto finish = [&](bool last) {
@@ -1315,13 +1387,21 @@ cudaError_t launch_ozaki_split(const double* A, const double* B, const OzakiDims
   if (d.Kt == 0) return cudaSuccess;
   if (d.Mt > 0) {
     dim3 grid(static_cast<unsigned>(d.Kt), static_cast<unsigned>(d.Mt));
-    oz_split_a_kernel<<<grid, 256, 0, s>>>(A, d.m, d.k, rowbits, d.S, d.beta, d.Mt, d.Kt,
-                                           aslices);
+    if (d.fp8)
+      oz_split_a_kernel<16><<<grid, 256, 0, s>>>(A, d.m, d.k, rowbits, d.S, d.beta, d.Mt, d.Kt,
+                                                 aslices);
+    else
+      oz_split_a_kernel<8><<<grid, 256, 0, s>>>(A, d.m, d.k, rowbits, d.S, d.beta, d.Mt, d.Kt,
+                                                aslices);
   }
   if (d.Nt > 0) {
     dim3 grid(static_cast<unsigned>(d.Kt), static_cast<unsigned>(d.Nt));
-    oz_split_b_kernel<<<grid, 256, 0, s>>>(B, d.k, d.n, colbits, d.S, d.beta, d.Nt, d.Kt,
-                                           bslices);
+    if (d.fp8)
+      oz_split_b_kernel<16><<<grid, 256, 0, s>>>(B, d.k, d.n, colbits, d.S, d.beta, d.Nt, d.Kt,
+                                                 bslices);
+    else
+      oz_split_b_kernel<8><<<grid, 256, 0, s>>>(B, d.k, d.n, colbits, d.S, d.beta, d.Nt, d.Kt,
+                                                bslices);
   }
   return cudaGetLastError();
 }
@@ -1381,11 +1461,6 @@ __global__ void __launch_bounds__(256) oz_splitk_fold_kernel(
       final_scale(st, exponent_from_absbits(rowbits[row]) + exponent_from_absbits(colbits[col]));
 }
 
-static bool narrow_sums(int S, int beta, int64_t Kt) {
-  // int32 running sums suffice while S (2^beta - 1)^2 * 128 Kt < 2^31
-  const long long dmax = (1ll << beta) - 1;
-  return static_cast<double>(S) * dmax * dmax * kOzTileK * Kt < 2147483647.0;
-}
 
 cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
                               const uint64_t* rowbits, const uint64_t* colbits, double* C,
@@ -1394,9 +1469,22 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
   const int window = ozaki_window_stages(d.beta);
   const int64_t splits = d.splits > 1 ? d.splits : 1;
   OzSingle tiles{aslices, bslices, rowbits, colbits, C,      d.m, d.n,
-                 d.Mt,    d.Nt,    d.Kt,    sums,    splits, d.S};
+                 d.Mt,    d.Nt,    d.Kt,    sums,    splits, d.S,
+                 static_cast<int64_t>(ozaki_tile_bytes(d))};
   const int64_t count = d.Mt * d.Nt * splits;
   const int64_t grid = count < sm_count() ? count : sm_count();
+  if (d.fp8) {
+    // the E4M3 engine: paired kernel only (the caller checks ozaki_narrow)
+    if (splits > 1 || !ozaki_narrow(d.S, d.beta, d.Kt)) return cudaErrorNotSupported;
+    auto kern = oz_gemm2_kernel<OzSingle, FmtE4m3>;
+    const size_t kSmem = gemm2_smem_bytes<FmtE4m3>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kSmem));
+    if (e != cudaSuccess) return e;
+    kern<<<static_cast<unsigned>(grid), kP2Threads, kSmem, s>>>(tiles, d.S, d.beta, window,
+                                                                status);
+    return cudaGetLastError();
+  }
   if (splits > 1) {
     // one diagonal at a time, each k range's D_g to the partials, then the fold
     cudaError_t e =
@@ -1407,13 +1495,14 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
         sums, rowbits, colbits, C, d.m, d.n, d.Mt, d.Nt, d.Kt, splits, d.S, d.beta);
     return cudaGetLastError();
   }
-  if (narrow_sums(d.S, d.beta, d.Kt)) {
-    auto kern = oz_gemm2_kernel<OzSingle>;
+  if (ozaki_narrow(d.S, d.beta, d.Kt)) {
+    auto kern = oz_gemm2_kernel<OzSingle, FmtBf16>;
+    const size_t kSmem = gemm2_smem_bytes<FmtBf16>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(kGemm2SmemBytes));
+                                         static_cast<int>(kSmem));
     if (e != cudaSuccess) return e;
-    kern<<<static_cast<unsigned>(grid), kP2Threads, kGemm2SmemBytes, s>>>(tiles, d.S, d.beta,
-                                                                          window, status);
+    kern<<<static_cast<unsigned>(grid), kP2Threads, kSmem, s>>>(tiles, d.S, d.beta, window,
+                                                                status);
     return cudaGetLastError();
   }
   return launch_oz_gemm_t<long long, false>(tiles, grid, d.S, d.beta, window, status, s);
@@ -1444,7 +1533,8 @@ cudaError_t launch_bf16_gemm(const double* A, const double* B, double* C, const 
       B, d.k, d.n, 1, d.Kt, bplane);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  OzSingle tiles{aplane, bplane, nullptr, nullptr, C, d.m, d.n, d.Mt, d.Nt, d.Kt, nullptr, 1, 1};
+  OzSingle tiles{aplane, bplane, nullptr, nullptr, C,       d.m, d.n, d.Mt, d.Nt,
+                 d.Kt,   nullptr, 1,     1,       kOzTileBytes};
   const int64_t count = d.Mt * d.Nt;
   const int64_t grid = count < sm_count() ? count : sm_count();
   // one window covers all of k (FP32 accumulation is the mode's semantics)

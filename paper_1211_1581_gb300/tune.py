@@ -1,10 +1,10 @@
 """Choice of engine and slice count for the FP64-accurate product, measured.
 
-Two engines compute C = A.B (Sec. 3.1) to FP64 accuracy: the native FP64
-tensor path (DMMA) and the Ozaki split (Ozaki, Ogita, Oishi, Rump 2012;
-integer-slice form of Ootomo, Ozaki, Yokota 2024) on the bf16 tensor pipe,
-with S slices of 7-bit digits (MODE_EMUL_I8) or of 8-bit digits
-(MODE_EMUL_BF16).  The cost of the split grows as S(S+1)/2 digit products;
+Several engines compute C = A.B (Sec. 3.1) to FP64 accuracy: the native
+FP64 tensor path (DMMA) and the Ozaki split (Ozaki, Ogita, Oishi, Rump 2012;
+integer-slice form of Ootomo, Ozaki, Yokota 2024) with S slices of 7-bit
+digits (MODE_EMUL_I8) or 8-bit digits (MODE_EMUL_BF16) on the bf16 tensor
+pipe, or of 4-bit digits on the FP8 tensor pipe (MODE_EMUL_FP8).  The cost of the split grows as S(S+1)/2 digit products;
 the slice count needed for FP64 accuracy depends on the data: a term
 a_il b_lj far below the row / column maxima 2^{e_i}, 2^{f_j} loses its low
 digits first, so wide exponent spreads need more slices.  Which engine is
@@ -37,8 +37,10 @@ from . import mxm
 
 U = 2.0 ** -53
 REFERENCE = (mxm.MODE_EMUL_BF16, 12)
-MODE_NAMES = {mxm.MODE_F64: "f64", mxm.MODE_EMUL_I8: "emul_i8", mxm.MODE_EMUL_BF16: "emul_bf16"}
-MAX_SLICES = 12
+MODE_NAMES = {mxm.MODE_F64: "f64", mxm.MODE_EMUL_I8: "emul_i8", mxm.MODE_EMUL_BF16: "emul_bf16",
+              mxm.MODE_EMUL_FP8: "emul_fp8"}
+MAX_SLICES = {mxm.MODE_EMUL_I8: 12, mxm.MODE_EMUL_BF16: 12, mxm.MODE_EMUL_FP8: 16}
+ENGINES = (mxm.MODE_F64, mxm.MODE_EMUL_I8, mxm.MODE_EMUL_BF16, mxm.MODE_EMUL_FP8)
 
 
 @dataclass
@@ -89,8 +91,7 @@ class TuneCache:
         os.replace(tmp, self.path)
 
 
-def select(measure, tol: float, modes=(mxm.MODE_F64, mxm.MODE_EMUL_I8, mxm.MODE_EMUL_BF16),
-           max_slices: int = MAX_SLICES) -> Choice:
+def select(measure, tol: float, modes=ENGINES, max_slices=None) -> Choice:
     """Pick the fastest accurate candidate.
 
     ``measure(mode, slices) -> (err_ratio, ms)``.  Native FP64 is one
@@ -100,7 +101,8 @@ def select(measure, tol: float, modes=(mxm.MODE_F64, mxm.MODE_EMUL_I8, mxm.MODE_
     measured = []
     best = None
     for mode in modes:
-        counts = [0] if mode == mxm.MODE_F64 else range(1, max_slices + 1)
+        top = max_slices if isinstance(max_slices, int) else MAX_SLICES.get(mode, 12)
+        counts = [0] if mode == mxm.MODE_F64 else range(1, top + 1)
         for s in counts:
             err, ms = measure(mode, s)
             measured.append([mode, s, float(err), float(ms)])

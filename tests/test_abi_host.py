@@ -81,6 +81,16 @@ def test_workspace_size_is_host_arithmetic():
     assert mxm.mxm_workspace_size(1, 256, 128, 128, 0) == 0
 
 
+def test_fp8_workspace_size_and_slices():
+    # E4M3 digit tiles are 16 KiB: S slices x (2 A tiles + 1 B tile) + sums
+    ws = mxm.mxm_workspace_size(5, 256, 128, 128, 16)
+    planes = 16 * (2 + 1) * 128 * 128
+    sums = 2 * 128 * 128 * 8
+    assert planes + sums <= ws < planes + sums + 8 * 1024
+    assert mxm.mxm_workspace_size(5, 256, 128, 128, 17) == 0
+    assert mxm.mxm_workspace_size(5, 256, 128, 128, 0) == 0
+
+
 def test_splitk_workspace_size():
     """Products with fewer C tiles than half the 304 split-k units cut k
     into ranges (FP64: at least 8 k-blocks of 16 each; emulated: at least 4

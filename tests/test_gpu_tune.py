@@ -23,7 +23,7 @@ def test_tuned_choice_is_fp64_accurate(kind, tmp_path):
     choice = tune.tune(A, B, tag=kind, cache=cache)
     assert choice.err_ratio <= 1.0
     # every emulated scan ended at its first accurate count
-    for mode in (mxm.MODE_EMUL_I8, mxm.MODE_EMUL_BF16):
+    for mode in (mxm.MODE_EMUL_I8, mxm.MODE_EMUL_BF16, mxm.MODE_EMUL_FP8):
         rows = [r for r in choice.measured if r[0] == mode]
         assert rows and rows[-1][2] <= 1.0 and all(r[2] > 1.0 for r in rows[:-1])
         assert [r[1] for r in rows] == list(range(1, len(rows) + 1))
