@@ -98,6 +98,10 @@ def _load():
     lib.oracle_num_threads.restype = I
     lib.oracle_set_threads.argtypes = [I]
     lib.oracle_set_threads.restype = I
+    for name in ("oracle_spmv", "oracle_spmv_dot2", "oracle_spmv_abs"):
+        f = getattr(lib, name)
+        f.argtypes = [P, P, P, P, P, I64, I64, I64]
+        f.restype = I
     _lib = lib
     return lib
 
@@ -237,3 +241,35 @@ def bf16_to_f64(bits):
 
 if __name__ == "__main__":  # pragma: no cover
     print(build(force="--force" in sys.argv))
+
+
+def _spmv(name, rowp, indx, vals, x, ncols=None):
+    rowp = np.ascontiguousarray(rowp, dtype=np.int32)
+    indx = np.ascontiguousarray(indx, dtype=np.int32)
+    vals = _f64(vals)
+    x = _f64(x)
+    nrows = rowp.shape[0] - 1
+    ncols = x.shape[0] if ncols is None else ncols
+    if vals.shape[0] != indx.shape[0] or x.shape[0] != ncols:
+        raise ValueError("CSR array lengths do not match")
+    y = np.empty(nrows, dtype=np.float64)
+    st = getattr(_load(), name)(_ptr(vals), _ptr(indx), _ptr(rowp), _ptr(x), _ptr(y), nrows,
+                                ncols, vals.shape[0])
+    if st != 0:
+        raise ValueError(f"{name}: invalid CSR structure")
+    return y
+
+
+def spmv(rowp, indx, vals, x):
+    """y = A x, A in CSR (rowp, indx, matvals), rows in storage order (Sec. 3.2)."""
+    return _spmv("oracle_spmv", rowp, indx, vals, x)
+
+
+def spmv_dot2(rowp, indx, vals, x):
+    """y = A x with every row by Dot2 (the accuracy reference)."""
+    return _spmv("oracle_spmv_dot2", rowp, indx, vals, x)
+
+
+def spmv_abs(rowp, indx, vals, x):
+    """|A| |x| (the scale of the elementwise error bound)."""
+    return _spmv("oracle_spmv_abs", rowp, indx, vals, x)

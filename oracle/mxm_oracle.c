@@ -32,6 +32,11 @@
  *                       scale, split, exact slice products, recombination.
  *   oracle_gemm_f32     FP32 naive loop (comparison mode).
  *   oracle_round_bf16   double -> bfloat16, round to nearest even.
+ *   oracle_spmv         mod2as (Sec. 3.2): y = A x, A in the 3-array CSR
+ *                       form, every row summed in storage order (the
+ *                       OMP2 loop of Sec. 3.2), rows shared out by OpenMP.
+ *   oracle_spmv_dot2    the same rows by Dot2 (accuracy reference).
+ *   oracle_spmv_abs     |A|.|x|, the scale of the error bound.
  */
 #include <math.h>
 #include <stdint.h>
@@ -398,4 +403,68 @@ static uint16_t round_bf16_one(double x) {
 
 void oracle_round_bf16(const double* x, uint16_t* out, int64_t count) {
   for (int64_t t = 0; t < count; ++t) out[t] = round_bf16_one(x[t]);
+}
+
+/* ------------------------------------------------------------------ */
+/* mod2as (Sec. 3.2): y = A x for an nrows x ncols matrix in the 3-array */
+/* CSR form of the paper: matvals[j] is the j-th non-zero, indx[j] its   */
+/* column, rowp[i] the position of the first non-zero of row i, and      */
+/* rowp[nrows] = nnz.  Every row is summed (the ArBB kernel maps over    */
+/* all nrows rows; the OpenMP listings' "i < nrows - 1" would skip the   */
+/* last one), and y is overwritten (the ArBB reduce starts from 0).      */
+/* A structure that is not monotone or indexes outside the arrays is     */
+/* rejected with ORACLE_INVALID before anything is read through it.      */
+static int csr_valid(const int32_t* indx, const int32_t* rowp, int64_t nrows, int64_t ncols,
+                     int64_t nnz) {
+  if (nrows < 0 || ncols < 0 || nnz < 0) return 0;
+  if (rowp[0] != 0 || rowp[nrows] != nnz) return 0;
+  for (int64_t i = 0; i < nrows; ++i)
+    if (rowp[i] > rowp[i + 1]) return 0;
+  for (int64_t j = 0; j < nnz; ++j)
+    if (indx[j] < 0 || indx[j] >= ncols) return 0;
+  return 1;
+}
+
+int oracle_spmv(const double* vals, const int32_t* indx, const int32_t* rowp, const double* x,
+                double* y, int64_t nrows, int64_t ncols, int64_t nnz) {
+  if (!csr_valid(indx, rowp, nrows, ncols, nnz)) return ORACLE_INVALID;
+  int64_t i;
+#pragma omp parallel for schedule(static)
+  for (i = 0; i < nrows; ++i) {
+    double t = 0.0;
+    for (int64_t j = rowp[i]; j < rowp[i + 1]; ++j) t = t + vals[j] * x[indx[j]];
+    y[i] = t;
+  }
+  return ORACLE_OK;
+}
+
+int oracle_spmv_dot2(const double* vals, const int32_t* indx, const int32_t* rowp,
+                     const double* x, double* y, int64_t nrows, int64_t ncols, int64_t nnz) {
+  if (!csr_valid(indx, rowp, nrows, ncols, nnz)) return ORACLE_INVALID;
+  int64_t i;
+#pragma omp parallel for schedule(static)
+  for (i = 0; i < nrows; ++i) {
+    double p = 0.0, s = 0.0;
+    for (int64_t j = rowp[i]; j < rowp[i + 1]; ++j) {
+      double h, r, q;
+      two_product(vals[j], x[indx[j]], &h, &r);
+      two_sum(p, h, &p, &q);
+      s = s + (q + r);
+    }
+    y[i] = p + s;
+  }
+  return ORACLE_OK;
+}
+
+int oracle_spmv_abs(const double* vals, const int32_t* indx, const int32_t* rowp,
+                    const double* x, double* y, int64_t nrows, int64_t ncols, int64_t nnz) {
+  if (!csr_valid(indx, rowp, nrows, ncols, nnz)) return ORACLE_INVALID;
+  int64_t i;
+#pragma omp parallel for schedule(static)
+  for (i = 0; i < nrows; ++i) {
+    double t = 0.0;
+    for (int64_t j = rowp[i]; j < rowp[i + 1]; ++j) t = t + fabs(vals[j]) * fabs(x[indx[j]]);
+    y[i] = t;
+  }
+  return ORACLE_OK;
 }

@@ -33,8 +33,9 @@ def _mix(z: np.ndarray) -> np.ndarray:
     return z
 
 
-def words(seed: int, stream: int, count: int, *, chunk: int = 1 << 24) -> np.ndarray:
-    """``count`` 64-bit words of stream (seed, stream)."""
+def words(seed: int, stream: int, count: int, *, start: int = 0,
+          chunk: int = 1 << 24) -> np.ndarray:
+    """``count`` 64-bit words of stream (seed, stream), from word ``start``."""
     with np.errstate(over="ignore"):
         s = np.array([seed & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64)
         st = np.array([(stream + 1) & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64)
@@ -42,7 +43,7 @@ def words(seed: int, stream: int, count: int, *, chunk: int = 1 << 24) -> np.nda
         out = np.empty(count, dtype=np.uint64)
         for lo in range(0, count, chunk):
             hi = min(count, lo + chunk)
-            ctr = np.arange(lo + 1, hi + 1, dtype=np.uint64)
+            ctr = np.arange(start + lo + 1, start + hi + 1, dtype=np.uint64)
             out[lo:hi] = _mix(key + ctr * GAMMA)
     return out
 
@@ -125,3 +126,27 @@ def gemm_operands(kind: str, m: int, k: int, n: int, seed: int = 0, cfg: int = 0
     if kind == "spread":
         return exp_spread(seed, 2 * cfg, (m, k)), exp_spread(seed, 2 * cfg + 1, (k, n))
     raise ValueError(f"unknown input kind {kind!r}")
+
+
+def csr_random(seed: int, stream: int, n: int, fill: float, *, rows_per_block: int = 256):
+    """A random n x n sparse matrix in the 3-array CSR form of mod2as
+    (Sec. 3.2): entry (i, j) is present when word i*n + j of stream
+    (seed, stream) is below ``fill`` as a uniform in [0, 1) (so the fill
+    fraction of Table 1 holds in expectation, rows of binomial length);
+    values uniform in [-1, 1) from stream + 1, one per present entry in
+    row-major order.  Returns (rowp int32[n + 1], indx int32[nnz],
+    matvals float64[nnz]), columns increasing within a row."""
+    rowp = np.zeros(n + 1, dtype=np.int64)
+    cols = []
+    for r0 in range(0, n, rows_per_block):
+        r1 = min(n, r0 + rows_per_block)
+        w = words(seed, stream, (r1 - r0) * n, start=r0 * n)
+        u = (w >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+        present = (u < fill).reshape(r1 - r0, n)
+        rowp[r0 + 1:r1 + 1] = present.sum(axis=1)
+        cols.append(np.nonzero(present)[1])
+    rowp = np.cumsum(rowp)
+    indx = np.concatenate(cols) if cols else np.zeros(0, dtype=np.int64)
+    nnz = int(rowp[-1])
+    vals = uniform_pm1(seed, stream + 1, (nnz,))
+    return rowp.astype(np.int32), indx.astype(np.int32), vals

@@ -3,9 +3,11 @@
 Each case below plants one mistake in a private copy of the oracle's C
 source (a dropped term, a flipped sign, a wrong slice weight, a missing
 diagonal, rounding instead of truncation, an off-by-one exponent, a wrong
-slice index, a missing absolute value, a dropped Dot2 correction), compiles
-it, and runs tests/test_oracle_pins.py against it in a subprocess: every
-mutant must make that suite fail.  Nothing here touches a GPU.
+slice index, a missing absolute value, a dropped Dot2 correction; for the
+mod2as oracle a skipped last row, a wrong column, a dropped first term),
+compiles it, and runs the matching pins (tests/test_oracle_pins.py or
+tests/test_oracle_spmv_pins.py) against it in a subprocess: every mutant
+must make its suite fail.  Nothing here touches a GPU.
 """
 import os
 import shutil
@@ -24,7 +26,8 @@ MUTANTS = {
     "naive_sign_flip": (
         "s += A[i * k + l] * B[l * n + j];\n      C[i * n + j] = s;\n    }\n  }\n}\n\n/* arbb_mxm2a",
         "s -= A[i * k + l] * B[l * n + j];\n      C[i * n + j] = s;\n    }\n  }\n}\n\n/* arbb_mxm2a"),
-    "dot2_drops_correction": ("s = s + (q + r);", "s = s + q;"),
+    "dot2_drops_correction": ("s = s + (q + r);\n  }\n  return p + s;",
+                              "s = s + q;\n  }\n  return p + s;"),
     "ozaki_wrong_weight": (
         "acc = acc + ldexp((double)Dg, -beta * g);\n  }\n  return ldexp(acc, e_i + f_j);",
         "acc = acc + ldexp((double)Dg, -beta * (g - 1));\n  }\n  return ldexp(acc, e_i + f_j);"),
@@ -39,7 +42,20 @@ MUTANTS = {
     "abs_missing_fabs": (
         "s += fabs(A[i * k + l]) * fabs(B[l * n + j]);\n      C[i * n + j] = s;",
         "s += A[i * k + l] * fabs(B[l * n + j]);\n      C[i * n + j] = s;"),
+    # mod2as (Sec. 3.2); checked by tests/test_oracle_spmv_pins.py
+    "spmv_skips_last_row": (
+        "for (i = 0; i < nrows; ++i) {\n    double t = 0.0;\n    for (int64_t j = rowp[i]; j < rowp[i + 1]; ++j) t = t + vals[j] * x[indx[j]];",
+        "for (i = 0; i < nrows - 1; ++i) {\n    double t = 0.0;\n    for (int64_t j = rowp[i]; j < rowp[i + 1]; ++j) t = t + vals[j] * x[indx[j]];"),
+    "spmv_wrong_column": ("t = t + vals[j] * x[indx[j]];", "t = t + vals[j] * x[j % ncols];"),
+    "spmv_drops_first_term": (
+        "for (int64_t j = rowp[i]; j < rowp[i + 1]; ++j) t = t + vals[j] * x[indx[j]];",
+        "for (int64_t j = rowp[i] + 1; j < rowp[i + 1]; ++j) t = t + vals[j] * x[indx[j]];"),
+    "spmv_dot2_drops_correction": ("s = s + (q + r);\n    }\n    y[i] = p + s;",
+                                   "s = s + q;\n    }\n    y[i] = p + s;"),
+    "spmv_abs_missing_fabs": ("t = t + fabs(vals[j]) * fabs(x[indx[j]]);",
+                              "t = t + vals[j] * fabs(x[indx[j]]);"),
 }
+PINS = {name: "test_oracle_spmv_pins.py" for name in MUTANTS if name.startswith("spmv_")}
 
 
 def _compile(src_text, out_dir):
@@ -61,7 +77,8 @@ def test_pins_catch_mutant(name, tmp_path):
     assert text.count(old) == 1, f"mutation site for {name} not unique/found"
     so = _compile(text.replace(old, new), str(tmp_path))
     env = dict(os.environ, MXM_ORACLE_LIB=so, OMP_NUM_THREADS="2")
+    pins = PINS.get(name, "test_oracle_pins.py")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the oracle pins"
