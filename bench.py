@@ -49,10 +49,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-check", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
-    p.add_argument("--suite", action="store_true",
+    p.add_argument("--suite", nargs="?", const="all", choices=("all", "gemm", "spmv"),
                    help="instead of the benchmark line: one JSON line per case of the "
                         "workload suite (FP64 sweep, slice counts and modes, rectangular "
-                        "shapes, grouped batch under a CUDA graph)")
+                        "shapes, grouped batch under a CUDA graph; mod2as sparse products)")
     return p.parse_args()
 
 
@@ -452,13 +452,18 @@ def run_suite(args):
     torch.cuda.set_device(0)
     mxm.load()
     stream = torch.cuda.current_stream()
-    dmma = mxm.mxm_peak_probe(1)
     peaks, _ = load_peaks()
     names = {mxm.MODE_F64: "f64", mxm.MODE_EMUL_I8: "emul_i8", mxm.MODE_EMUL_BF16: "emul_bf16",
              mxm.MODE_F32: "f32", mxm.MODE_BF16_F32ACC: "bf16_f32acc", mxm.MODE_EMUL_FP8: "emul_fp8"}
 
     def emit(**d):
         print(json.dumps(dict(suite=True, **d)), flush=True)
+
+    if args.suite in ("all", "spmv"):
+        run_spmv_suite(emit, stream, peaks)
+    if args.suite == "spmv":
+        return
+    dmma = mxm.mxm_peak_probe(1)
 
     def one(case, kind, m, k, n, runs, reps=3, seed=0, cfg=2, tuned=False):
         A_h, B_h = inputs.gemm_operands(kind, m, k, n, seed=seed, cfg=cfg)
@@ -534,6 +539,70 @@ def run_suite(args):
              ms=round(ms, 4), tflops=round(flops / (ms * 1e-3) / 1e12, 3),
              err_over_ku_AB_24_checked=err, status=st, graph=True)
         del ws, g
+
+
+# Table 1 of the paper: mod2as orders and fill in percent
+SPMV_TABLE1 = [(100, 3.50), (200, 3.75), (256, 5.0), (400, 4.38), (500, 5.00), (512, 4.00),
+               (960, 4.50), (1000, 5.00), (1024, 5.50), (2000, 7.50), (4096, 3.50),
+               (4992, 4.00), (5000, 4.00), (9984, 4.50), (10000, 5.00), (10240, 5.72)]
+
+
+def spmv_bytes(nrows, ncols, nnz):
+    """Algorithmic bytes of one y = A x in CSR: 8 + 4 per value (matvals,
+    indx), 4 per row pointer, 8 per y entry written, x read once."""
+    return 12 * nnz + 4 * (nrows + 1) + 8 * nrows + 8 * ncols
+
+
+def run_spmv_suite(emit, stream, peaks):
+    """mod2as (Sec. 3.2) rows: the Table 1 orders and fills (operands well
+    inside L2: repeated calls, L2-warm, as the paper's repeated kernel
+    loop), then two matrices of 400-600 MB (larger than L2, cold between
+    calls) against the measured HBM copy rate.  The CPU line beside each
+    Table 1 case is the storage-order oracle loop, timed on the host."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1211_1581_gb300 import inputs, mxm
+
+    def dev(a, dt):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dtype=dt).cuda()
+
+    hbm = peaks.get("hbm_gbs") if peaks else None
+    for n, fill in SPMV_TABLE1 + [(2_000_000, None), (200_000, None)]:
+        if fill is not None:
+            rowp, indx, vals = inputs.csr_random(0, 70, n, fill / 100.0)
+            case, reps = "spmv_table1", 50
+        else:
+            mean = 16 if n > 1_000_000 else 250
+            rowp, indx, vals = inputs.csr_sampled(2, 95, n, n, mean)
+            case, reps = "spmv_large", 10
+        x = inputs.uniform_pm1(0, 72, (n,))
+        nnz = len(vals)
+        dv, di, dr, dx = dev(vals, torch.float64), dev(indx, torch.int32), dev(rowp, torch.int32), \
+            dev(x, torch.float64)
+        y = torch.empty(n, dtype=torch.float64, device="cuda")
+        ms = _timed_ms(lambda: mxm.mxm_spmv(dv, di, dr, dx, y, stream=stream), reps, stream)
+        st = mxm.mxm_get_device_status()
+        gbs = spmv_bytes(n, n, nnz) / (ms * 1e-3) / 1e9
+        d = {"case": case, "n": n, "nnz": nnz, "fill_pct": fill, "mode": "spmv_f64",
+             "ms": round(ms, 5), "gflops": round(2.0 * nnz / (ms * 1e-3) / 1e9, 2),
+             "algorithmic_gbs": round(gbs, 1), "status": st,
+             "l2": "warm (operands inside L2)" if fill is not None else "operands larger than L2"}
+        if fill is None and hbm:
+            d["frac_of_measured_hbm"] = round(gbs / hbm, 3)
+        if fill is not None:
+            t0 = time.perf_counter()
+            k = 0
+            while time.perf_counter() - t0 < 0.2 or k < 3:
+                oracle.spmv(rowp, indx, vals, x)
+                k += 1
+            cms = (time.perf_counter() - t0) / k * 1e3
+            d["cpu_oracle"] = {"ms": round(cms, 4), "gflops": round(2.0 * nnz / (cms * 1e-3) / 1e9, 3),
+                               "cores": oracle.num_threads()}
+        emit(**d)
+        del dv, di, dr, dx, y
+        torch.cuda.empty_cache()
 
 
 def run_reference(args):

@@ -203,6 +203,26 @@ mxm_status mxm_profile_enable(int on);
 mxm_status mxm_profile_read(double* ms, int max_phases, int64_t* calls);
 
 /*
+ * mxm_spmv -- y = A x, the mod2as sparse product (Sec. 3.2).  A is
+ * nrows x ncols in the paper's 3-array CSR form, all arrays in device
+ * memory and owned by the caller: matvals[nnz] (FP64 values, row by row),
+ * indx[nnz] (int32: the column of each value), rowp[nrows + 1] (int32: the
+ * position in matvals of each row's first value, rowp[nrows] = nnz); x[ncols]
+ * and y[nrows] FP64.  y is overwritten; x and y must not overlap.  Each row
+ * is summed in FP64 with fused multiply-adds (a row's values are shared out
+ * over 2..32 lanes by stride and their partial sums added by a tree), so
+ * |y_i - sum_j a_ij x_j| <= 2 len_i u (|A||x|)_i with len_i the row's length.
+ * Asynchronous on `stream`; argument errors are returned (sizes above
+ * INT32_MAX: MXM_ERR_UNSUPPORTED; misaligned pointers: MXM_ERR_ALIGNMENT).
+ * A row whose rowp entries, or a value whose column, lie outside the arrays
+ * is skipped (its y_i is not written) and makes mxm_get_device_status
+ * report MXM_ERR_INVALID_ARG.
+ */
+mxm_status mxm_spmv(const double* matvals, const int32_t* indx, const int32_t* rowp,
+                    const double* x, double* y, int64_t nrows, int64_t ncols, int64_t nnz,
+                    void* stream);
+
+/*
  * mxm_f64_emul_noalloc -- mxm_f64_emul (7-bit digits, `slices` slices) for
  * callers that cannot allocate device memory, e.g. code inside a process
  * whose allocator owns the device, loops that must never reach the driver's

@@ -1,0 +1,137 @@
+// spmv.cu -- the mod2as sparse product y = A x (Sec. 3.2) with A in the
+// paper's 3-array CSR form (matvals, indx, rowp).
+//
+// One group of G lanes (G a power of two from 2 to 32, chosen from the
+// average row length so that short rows do not leave most of a warp idle)
+// takes one row: the lanes stride over the row's values (consecutive lanes,
+// consecutive values: the loads of matvals and indx are contiguous), each
+// keeps an FP64 partial sum built with fused multiply-adds, and a shuffle
+// tree adds the G partials; the group's first lane writes y_i.  The gather
+// x[indx[j]] goes through the read-only path.  The kernel is bound by the
+// bytes of matvals and indx (12 per value) and, for a vector that does not
+// stay in cache, the gathered x.
+//
+// Rows are taken warp by warp (a warp holds 32 / G rows), so every lane of
+// a warp runs the same number of loop rounds and the shuffles are always
+// full-warp.  A row whose rowp entries, or a value whose column, fall
+// outside the arrays is skipped (its y is left unwritten) and sets the
+// bounds bit of the device status word: bad structure is reported, never
+// read through.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mxm.h"
+#include "mxm_internal.h"
+
+namespace mxm {
+
+int* device_status_word();  // abi.cu
+
+namespace {
+
+constexpr int kSpmvThreads = 256;
+
+template <int G>
+__global__ void __launch_bounds__(kSpmvThreads) csr_spmv_kernel(
+    const double* __restrict__ vals, const int32_t* __restrict__ indx,
+    const int32_t* __restrict__ rowp, const double* __restrict__ x, double* __restrict__ y,
+    int64_t nrows, int64_t ncols, int64_t nnz, int* __restrict__ status) {
+  constexpr int kRowsPerWarp = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane & (G - 1);    // lane within the row's group
+  const int grp = lane / G;          // the warp's row slot
+  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * kSpmvThreads + threadIdx.x) >> 5;
+  const int64_t warps = (static_cast<int64_t>(gridDim.x) * kSpmvThreads) >> 5;
+  bool bad = false;
+  for (int64_t base = warp * kRowsPerWarp; base < nrows; base += warps * kRowsPerWarp) {
+    const int64_t row = base + grp;
+    double t = 0.0;
+    if (row < nrows) {
+      const int64_t b = __ldg(rowp + row), e = __ldg(rowp + row + 1);
+      if (b < 0 || e < b || e > nnz) {
+        bad = true;
+      } else {
+        // unrolled so that several value, column and gather loads are in
+        // flight per lane; an out-of-range column is flagged, not read
+#pragma unroll 4
+        for (int64_t j = b + sub; j < e; j += G) {
+          const int32_t c = __ldg(indx + j);
+          const bool ok = c >= 0 && c < ncols;
+          bad |= !ok;
+          if (ok) t = fma(__ldg(vals + j), __ldg(x + c), t);
+        }
+      }
+    }
+    // tree over the G lanes of each group (full-warp shuffles)
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+    const bool row_bad = __any_sync(0xFFFFFFFFu, bad) &&
+                         (__ballot_sync(0xFFFFFFFFu, bad) >> (grp * G) & ((1ull << G) - 1)) != 0;
+    if (row < nrows && sub == 0 && !row_bad) y[row] = t;
+    if (row_bad && sub == 0 && row < nrows) atomicOr(status, kStatusBounds);
+    bad = false;
+  }
+}
+
+template <int G>
+cudaError_t launch_spmv_g(const double* vals, const int32_t* indx, const int32_t* rowp,
+                          const double* x, double* y, int64_t nrows, int64_t ncols, int64_t nnz,
+                          int* status, cudaStream_t s) {
+  const int64_t warps_needed = (nrows + (32 / G) - 1) / (32 / G);
+  int64_t blocks = (warps_needed * 32 + kSpmvThreads - 1) / kSpmvThreads;
+  const int64_t cap = static_cast<int64_t>(sm_count()) * (2048 / kSpmvThreads);
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  csr_spmv_kernel<G><<<static_cast<unsigned>(blocks), kSpmvThreads, 0, s>>>(
+      vals, indx, rowp, x, y, nrows, ncols, nnz, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Lanes per row from the average row length (CSR-vector heuristic).
+int spmv_group(int64_t nrows, int64_t nnz) {
+  const double avg = nrows > 0 ? static_cast<double>(nnz) / static_cast<double>(nrows) : 0.0;
+  if (avg <= 4) return 2;
+  if (avg <= 8) return 4;
+  if (avg <= 16) return 8;
+  if (avg <= 32) return 16;
+  return 32;
+}
+
+cudaError_t launch_spmv(const double* vals, const int32_t* indx, const int32_t* rowp,
+                        const double* x, double* y, int64_t nrows, int64_t ncols, int64_t nnz,
+                        int* status, cudaStream_t s) {
+  switch (spmv_group(nrows, nnz)) {
+    case 2: return launch_spmv_g<2>(vals, indx, rowp, x, y, nrows, ncols, nnz, status, s);
+    case 4: return launch_spmv_g<4>(vals, indx, rowp, x, y, nrows, ncols, nnz, status, s);
+    case 8: return launch_spmv_g<8>(vals, indx, rowp, x, y, nrows, ncols, nnz, status, s);
+    case 16: return launch_spmv_g<16>(vals, indx, rowp, x, y, nrows, ncols, nnz, status, s);
+    default: return launch_spmv_g<32>(vals, indx, rowp, x, y, nrows, ncols, nnz, status, s);
+  }
+}
+
+}  // namespace mxm
+
+using namespace mxm;
+
+extern "C" mxm_status mxm_spmv(const double* matvals, const int32_t* indx, const int32_t* rowp,
+                               const double* x, double* y, int64_t nrows, int64_t ncols,
+                               int64_t nnz, void* stream) {
+  if (nrows < 0 || ncols < 0 || nnz < 0) return MXM_ERR_INVALID_ARG;
+  if (nrows > INT32_MAX || ncols > INT32_MAX || nnz > INT32_MAX) return MXM_ERR_UNSUPPORTED;
+  if (nrows == 0) return MXM_OK;
+  if (y == nullptr || rowp == nullptr || (nnz > 0 && (matvals == nullptr || indx == nullptr)) ||
+      (ncols > 0 && x == nullptr))
+    return MXM_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(matvals) | reinterpret_cast<uintptr_t>(x) |
+       reinterpret_cast<uintptr_t>(y)) & 7 ||
+      (reinterpret_cast<uintptr_t>(indx) | reinterpret_cast<uintptr_t>(rowp)) & 3)
+    return MXM_ERR_ALIGNMENT;
+  int* status = device_status_word();
+  if (status == nullptr) return MXM_ERR_CUDA;
+  const cudaError_t e = launch_spmv(matvals, indx, rowp, x, y, nrows, ncols, nnz, status,
+                                    static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? MXM_OK : MXM_ERR_CUDA;
+}

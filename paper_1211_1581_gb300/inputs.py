@@ -150,3 +150,31 @@ def csr_random(seed: int, stream: int, n: int, fill: float, *, rows_per_block: i
     nnz = int(rowp[-1])
     vals = uniform_pm1(seed, stream + 1, (nnz,))
     return rowp.astype(np.int32), indx.astype(np.int32), vals
+
+
+def csr_sampled(seed: int, stream: int, nrows: int, ncols: int, mean_len: float):
+    """A large random sparse matrix in the same CSR form, drawn per value
+    rather than per (i, j) cell: row i asks for round(mean_len + sd * z_i)
+    columns (z_i standard normal by Box-Muller from stream + 2, sd the
+    binomial spread sqrt(mean_len (1 - mean_len / ncols)), clipped to
+    [0, ncols]), each column word mod ncols from stream; repeated columns
+    in a row are merged, so rows hold distinct increasing columns and
+    lengths close to binomial, as in ``csr_random``.  Values uniform in
+    [-1, 1) from stream + 1.  Returns (rowp, indx, matvals) like
+    ``csr_random``."""
+    p = min(1.0, mean_len / max(ncols, 1))
+    sd = float(np.sqrt(mean_len * (1.0 - p)))
+    u = unit(seed, stream + 2, 2 * nrows).reshape(2, nrows)
+    z = np.sqrt(-2.0 * np.log1p(-u[0])) * np.cos(2.0 * np.pi * u[1])
+    want = np.clip(np.rint(mean_len + sd * z), 0, ncols).astype(np.int64)
+    total = int(want.sum())
+    rows = np.repeat(np.arange(nrows, dtype=np.int64), want)
+    cols = (words(seed, stream, total) % np.uint64(max(ncols, 1))).astype(np.int64)
+    key = np.sort(rows * ncols + cols)
+    if len(key):
+        key = key[np.concatenate(([True], key[1:] != key[:-1]))]
+    r = key // max(ncols, 1)
+    rowp = np.zeros(nrows + 1, dtype=np.int64)
+    rowp[1:] = np.cumsum(np.bincount(r, minlength=nrows))
+    vals = uniform_pm1(seed, stream + 1, (len(key),))
+    return rowp.astype(np.int32), (key % max(ncols, 1)).astype(np.int32), vals

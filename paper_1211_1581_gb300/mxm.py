@@ -52,6 +52,7 @@ SIGNATURES = {
     "mxm_profile_enable": (_I, [_I]),
     "mxm_profile_read": (_I, [ctypes.POINTER(ctypes.c_double), _I, ctypes.POINTER(_I64)]),
     "mxm_f64_emul_noalloc": (_I, [_P, _P, _P, _I64, _I64, _I64, _I, _P]),
+    "mxm_spmv": (_I, [_P, _P, _P, _P, _P, _I64, _I64, _I64, _P]),
 }
 
 _lib = None
@@ -242,3 +243,23 @@ def mxm_profile_read():
 
 def mxm_version() -> int:
     return int(load().mxm_version())
+
+
+def mxm_spmv(matvals, indx, rowp, x, y, stream=None):
+    """y = A x for A in CSR (matvals float64, indx and rowp int32; CUDA
+    tensors), asynchronously on ``stream`` (mod2as, Sec. 3.2)."""
+    import torch
+    for name, t, dt in (("matvals", matvals, torch.float64), ("indx", indx, torch.int32),
+                        ("rowp", rowp, torch.int32), ("x", x, torch.float64),
+                        ("y", y, torch.float64)):
+        if not isinstance(t, torch.Tensor) or t.dtype != dt or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA {dt} tensor")
+        if t.dim() != 1 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous 1-D tensor")
+    nrows = rowp.shape[0] - 1
+    if nrows < 0 or y.shape[0] != nrows or indx.shape[0] != matvals.shape[0]:
+        raise ValueError("CSR array lengths do not match")
+    _check(load().mxm_spmv(matvals.data_ptr(), indx.data_ptr(), rowp.data_ptr(), x.data_ptr(),
+                           y.data_ptr(), nrows, x.shape[0], matvals.shape[0],
+                           _stream_ptr(stream)), "mxm_spmv")
+    return y

@@ -130,3 +130,16 @@ def test_grouped_workspace_size_on_host():
     assert lib.mxm_grouped(0, None, 1, 7, None, 0, None) == mxm.MXM_OK
     assert lib.mxm_grouped(4, ctypes.c_void_p(0x1000), 1, 7, ctypes.c_void_p(0x10000), 16, None) == \
         mxm.MXM_ERR_WORKSPACE_TOO_SMALL
+
+
+def test_spmv_argument_errors_on_host():
+    lib = mxm.load()
+    P = ctypes.c_void_p
+    fake = P(0x10000)
+    assert lib.mxm_spmv(fake, fake, fake, fake, fake, -1, 4, 4, None) == mxm.MXM_ERR_INVALID_ARG
+    assert lib.mxm_spmv(fake, fake, fake, fake, fake, 0, 4, 4, None) == mxm.MXM_OK
+    assert lib.mxm_spmv(fake, fake, None, fake, fake, 4, 4, 4, None) == mxm.MXM_ERR_INVALID_ARG
+    assert lib.mxm_spmv(P(0x10004), fake, fake, fake, fake, 4, 4, 4, None) == mxm.MXM_ERR_ALIGNMENT
+    assert lib.mxm_spmv(fake, P(0x10002), fake, fake, fake, 4, 4, 4, None) == mxm.MXM_ERR_ALIGNMENT
+    assert lib.mxm_spmv(fake, fake, fake, fake, fake, 1 << 32, 4, 4, None) == \
+        mxm.MXM_ERR_UNSUPPORTED

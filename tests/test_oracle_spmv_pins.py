@@ -127,3 +127,18 @@ def test_generator():
     D = dense_of(rowp, indx, vals, 500)
     r2, i2, v2 = csr_of(D)
     assert np.array_equal(r2, rowp) and np.array_equal(i2, indx) and np.array_equal(v2, vals)
+
+
+def test_sampled_generator():
+    """The per-value generator for large matrices: valid CSR, repeatable,
+    mean length and spread those of the binomial fill it stands in for."""
+    a = inputs.csr_sampled(7, 61, 20000, 30000, 40.0)
+    b = inputs.csr_sampled(7, 61, 20000, 30000, 40.0)
+    assert all(np.array_equal(p, q) for p, q in zip(a, b))
+    rowp, indx, vals = a
+    assert rowp.dtype == np.int32 and indx.dtype == np.int32 and len(vals) == rowp[-1]
+    lens = np.diff(rowp)
+    assert abs(lens.mean() - 40.0) < 0.3 and abs(lens.std() - np.sqrt(40 * (1 - 40 / 30000))) < 0.5
+    r = np.repeat(np.arange(20000, dtype=np.int64), lens)
+    key = r * 30000 + indx
+    assert np.all(np.diff(key) > 0) and indx.min() >= 0 and indx.max() < 30000
