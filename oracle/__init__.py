@@ -18,6 +18,10 @@ Functions (all take and return numpy arrays, row-major float64):
 * ``ozaki_split``  - steps 1-2 of the Ozaki split (exponents + digits).
 * ``ozaki_gemm`` / ``ozaki_entries`` - the full emulated product.
 * ``gemm_f32``, ``round_bf16`` - comparison-mode references.
+* ``spmv`` / ``spmv_dot2`` / ``spmv_abs`` - mod2as (Sec. 3.2), CSR y = A x
+  in storage order, by Dot2, and |A||x|.
+* ``cg``           - conjugate gradients (Sec. 3.4, Fig. 6) on a CSR SPD
+  matrix, the paper's step order.
 """
 from __future__ import annotations
 
@@ -102,6 +106,8 @@ def _load():
         f = getattr(lib, name)
         f.argtypes = [P, P, P, P, P, I64, I64, I64]
         f.restype = I
+    lib.oracle_cg.argtypes = [P, P, P, P, P, I64, I64, ctypes.c_double, I64, P, P, P]
+    lib.oracle_cg.restype = I
     _lib = lib
     return lib
 
@@ -239,9 +245,6 @@ def bf16_to_f64(bits):
     return b.view(np.float32).astype(np.float64)
 
 
-if __name__ == "__main__":  # pragma: no cover
-    print(build(force="--force" in sys.argv))
-
 
 def _spmv(name, rowp, indx, vals, x, ncols=None):
     rowp = np.ascontiguousarray(rowp, dtype=np.int32)
@@ -273,3 +276,34 @@ def spmv_dot2(rowp, indx, vals, x):
 def spmv_abs(rowp, indx, vals, x):
     """|A| |x| (the scale of the elementwise error bound)."""
     return _spmv("oracle_spmv_abs", rowp, indx, vals, x)
+
+
+CG_BREAKDOWN = 9
+
+
+def cg(rowp, indx, vals, b, stop, max_iters):
+    """Conjugate gradients for A x = b (Sec. 3.4, Fig. 6), A SPD in CSR,
+    x0 = 0.  Returns a dict: x, iters, r2 (the last (r, r)), hist (r2
+    after every step), breakdown (True when (p, A p) <= 0 ended the loop)."""
+    rowp = np.ascontiguousarray(rowp, dtype=np.int32)
+    indx = np.ascontiguousarray(indx, dtype=np.int32)
+    vals = _f64(vals)
+    b = _f64(b)
+    n = rowp.shape[0] - 1
+    if b.shape[0] != n or vals.shape[0] != indx.shape[0]:
+        raise ValueError("CSR array lengths do not match")
+    x = np.empty(n, dtype=np.float64)
+    hist = np.full(int(max_iters) + 1, np.nan)
+    it = ctypes.c_int64(0)
+    r2 = ctypes.c_double(0.0)
+    st = _load().oracle_cg(_ptr(vals), _ptr(indx), _ptr(rowp), _ptr(b), _ptr(x), n,
+                           vals.shape[0], float(stop), int(max_iters), ctypes.byref(it),
+                           ctypes.byref(r2), _ptr(hist))
+    if st not in (0, CG_BREAKDOWN):
+        raise ValueError("oracle_cg: invalid CSR structure")
+    return {"x": x, "iters": it.value, "r2": r2.value, "hist": hist[:it.value].copy(),
+            "breakdown": st == CG_BREAKDOWN}
+
+
+if __name__ == "__main__":  # pragma: no cover
+    print(build(force="--force" in sys.argv))

@@ -37,6 +37,9 @@
  *                       OMP2 loop of Sec. 3.2), rows shared out by OpenMP.
  *   oracle_spmv_dot2    the same rows by Dot2 (accuracy reference).
  *   oracle_spmv_abs     |A|.|x|, the scale of the error bound.
+ *   oracle_cg           conjugate gradients (Sec. 3.4, Fig. 6) for an SPD
+ *                       matrix in the same CSR form, steps in the paper's
+ *                       order, dot products summed in index order.
  */
 #include <math.h>
 #include <stdint.h>
@@ -467,4 +470,74 @@ int oracle_spmv_abs(const double* vals, const int32_t* indx, const int32_t* rowp
     y[i] = t;
   }
   return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Conjugate gradients (Sec. 3.4, Fig. 6 and the ArBB loop beside it)    */
+/* for A x = b, A symmetric positive definite in the CSR form above      */
+/* (n x n).  x0 = 0, so r0 = b and p0 = b; r2 = (b, b).  While           */
+/* r2 > stop and fewer than max_iters steps were taken:                  */
+/*   q = A p (every row in storage order, as oracle_spmv);               */
+/*   alpha = r2 / (p, q);  r2_old = r2;  r = r - alpha q;                */
+/*   r2 = (r, r);  beta = r2 / r2_old;  x = x + alpha p;  p = r + beta p. */
+/* Dot products are summed in index order.  The paper does not say what  */
+/* happens when (p, A p) <= 0 (A not positive definite along p): here    */
+/* the step is not taken, the loop ends and ORACLE_BREAKDOWN is returned. */
+/* iters receives the number of steps taken, r2_final the last r2, and   */
+/* r2_hist (if not NULL, max_iters entries) the r2 after every step.     */
+#define ORACLE_BREAKDOWN 9
+
+int oracle_cg(const double* vals, const int32_t* indx, const int32_t* rowp, const double* b,
+              double* x, int64_t n, int64_t nnz, double stop, int64_t max_iters, int64_t* iters,
+              double* r2_final, double* r2_hist) {
+  if (!csr_valid(indx, rowp, n, n, nnz)) return ORACLE_INVALID;
+  double* r = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* p = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* q = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (!r || !p || !q) {
+    free(r);
+    free(p);
+    free(q);
+    return ORACLE_INVALID;
+  }
+  double r2 = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    x[i] = 0.0;
+    r[i] = b[i];
+    p[i] = b[i];
+    r2 = r2 + b[i] * b[i];
+  }
+  int status = ORACLE_OK;
+  int64_t k = 0;
+  while (r2 > stop && k < max_iters) {
+    int64_t i;
+#pragma omp parallel for schedule(static)
+    for (i = 0; i < n; ++i) {
+      double t = 0.0;
+      for (int64_t j = rowp[i]; j < rowp[i + 1]; ++j) t = t + vals[j] * p[indx[j]];
+      q[i] = t;
+    }
+    double pq = 0.0;
+    for (i = 0; i < n; ++i) pq = pq + p[i] * q[i];
+    if (!(pq > 0.0)) {
+      status = ORACLE_BREAKDOWN;
+      break;
+    }
+    const double alpha = r2 / pq;
+    const double r2_old = r2;
+    for (i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];
+    r2 = 0.0;
+    for (i = 0; i < n; ++i) r2 = r2 + r[i] * r[i];
+    const double beta = r2 / r2_old;
+    for (i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
+    for (i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+    if (r2_hist) r2_hist[k] = r2;
+    ++k;
+  }
+  *iters = k;
+  *r2_final = r2;
+  free(r);
+  free(p);
+  free(q);
+  return status;
 }

@@ -1,4 +1,6 @@
-"""Seeded synthetic inputs for the mod2am product (Sec. 3.1) and its variants.
+"""Seeded synthetic inputs for the mod2am product (Sec. 3.1) and its variants,
+the mod2as sparse product (Sec. 3.2) and the conjugate-gradient solver
+(Sec. 3.4).
 
 This module only draws numbers; it holds none of the product's arithmetic.
 Both the CUDA path and the CPU oracle are fed from it.  The paper measured
@@ -178,3 +180,37 @@ def csr_sampled(seed: int, stream: int, nrows: int, ncols: int, mean_len: float)
     rowp[1:] = np.cumsum(np.bincount(r, minlength=nrows))
     vals = uniform_pm1(seed, stream + 1, (len(key),))
     return rowp.astype(np.int32), (key % max(ncols, 1)).astype(np.int32), vals
+
+
+def banded_spd(seed: int, stream: int, n: int, bw: int):
+    """A random symmetric positive definite band matrix in CSR, as the
+    conjugate-gradient inputs of Sec. 3.4 (Table 2): ``bw`` diagonals
+    (bw odd; h = (bw - 1) / 2 on each side of the main one).  Entry
+    (i, i + d), 1 <= d <= h, equals entry (i + d, i) and is word
+    i * h + d - 1 of stream (seed, stream) as a uniform in [-1, 1); the
+    diagonal entry is 1 + the sum of the row's off-diagonal magnitudes, so
+    the matrix is strictly diagonally dominant with a positive diagonal
+    (hence SPD, eigenvalues in [1, 1 + 2 * max row sum] by Gershgorin).
+    Returns (rowp int32[n + 1], indx int32[nnz], matvals float64[nnz])."""
+    if bw < 1 or bw % 2 == 0:
+        raise ValueError("bw must be odd and positive")
+    h = min((bw - 1) // 2, max(n - 1, 0))
+    up = uniform_pm1(seed, stream, (max(n * h, 1),))[:n * h].reshape(n, h) if h else \
+        np.zeros((n, 0))
+    # band[i, h + d] = a(i, i + d) for -h <= d <= h
+    band = np.zeros((n, 2 * h + 1))
+    for d in range(1, h + 1):
+        band[:n - d, h + d] = up[:n - d, d - 1]
+        band[d:, h - d] = up[:n - d, d - 1]
+    band[:, h] = 1.0 + np.abs(band).sum(axis=1)
+    cols = np.arange(n)[:, None] + np.arange(-h, h + 1)[None, :]
+    keep = (cols >= 0) & (cols < n)
+    rowp = np.zeros(n + 1, dtype=np.int64)
+    rowp[1:] = np.cumsum(keep.sum(axis=1))
+    return rowp.astype(np.int32), cols[keep].astype(np.int32), band[keep]
+
+
+# Table 2 of the paper: (n, bw) of the conjugate-gradient runs
+CG_TABLE2 = [(128, 3), (128, 31), (128, 63), (256, 3), (256, 31), (256, 63), (256, 127),
+             (512, 3), (512, 31), (512, 63), (512, 127), (512, 255), (1024, 3), (1024, 31),
+             (1024, 63), (1024, 127), (1024, 255), (1024, 511)]

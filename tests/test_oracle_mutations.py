@@ -54,8 +54,19 @@ MUTANTS = {
                                    "s = s + q;\n    }\n    y[i] = p + s;"),
     "spmv_abs_missing_fabs": ("t = t + fabs(vals[j]) * fabs(x[indx[j]]);",
                               "t = t + vals[j] * fabs(x[indx[j]]);"),
+    # conjugate gradients (Sec. 3.4); checked by tests/test_oracle_cg_pins.py
+    "cg_beta_inverted": ("const double beta = r2 / r2_old;", "const double beta = r2_old / r2;"),
+    "cg_residual_sign": ("r[i] = r[i] - alpha * q[i];", "r[i] = r[i] + alpha * q[i];"),
+    "cg_direction_from_residual": ("p[i] = r[i] + beta * p[i];", "p[i] = r[i] + beta * r[i];"),
+    "cg_x_along_residual": ("x[i] = x[i] + alpha * p[i];", "x[i] = x[i] + alpha * r[i];"),
+    "cg_no_beta": ("p[i] = r[i] + beta * p[i];", "p[i] = r[i] + 0.0 * beta * p[i];"),
+    "cg_product_drops_diagonal": ("t = t + vals[j] * p[indx[j]];",
+                                  "if (indx[j] != i) t = t + vals[j] * p[indx[j]];"),
+    "cg_stop_off_by_one": ("while (r2 > stop && k < max_iters) {",
+                           "while (r2 > stop && k <= max_iters) {"),
 }
 PINS = {name: "test_oracle_spmv_pins.py" for name in MUTANTS if name.startswith("spmv_")}
+PINS.update({name: "test_oracle_cg_pins.py" for name in MUTANTS if name.startswith("cg_")})
 
 
 def _compile(src_text, out_dir):
