@@ -49,10 +49,11 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-check", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
-    p.add_argument("--suite", nargs="?", const="all", choices=("all", "gemm", "spmv"),
+    p.add_argument("--suite", nargs="?", const="all", choices=("all", "gemm", "spmv", "cg"),
                    help="instead of the benchmark line: one JSON line per case of the "
                         "workload suite (FP64 sweep, slice counts and modes, rectangular "
-                        "shapes, grouped batch under a CUDA graph; mod2as sparse products)")
+                        "shapes, grouped batch under a CUDA graph; mod2as sparse products; "
+                        "conjugate-gradient solves)")
     return p.parse_args()
 
 
@@ -461,7 +462,9 @@ def run_suite(args):
 
     if args.suite in ("all", "spmv"):
         run_spmv_suite(emit, stream, peaks)
-    if args.suite == "spmv":
+    if args.suite in ("all", "cg"):
+        run_cg_suite(emit, stream)
+    if args.suite in ("spmv", "cg"):
         return
     dmma = mxm.mxm_peak_probe(1)
 
@@ -603,6 +606,52 @@ def run_spmv_suite(emit, stream, peaks):
         emit(**d)
         del dv, di, dr, dx, y
         torch.cuda.empty_cache()
+
+
+def run_cg_suite(emit, stream):
+    """Conjugate gradients (Sec. 3.4): the Table 2 orders and bandwidths,
+    plus the largest order the one-launch solver takes, each solved to
+    r2 <= 1e-24 (b, b).  Rate in the paper's terms: FP64 operations of the
+    steps taken (2 nnz + 10 n per step) over the solve time (one launch,
+    CUDA events).  The CPU line is the oracle's solve, timed on the host."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1211_1581_gb300 import inputs, mxm
+
+    def dev(a, dt):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dtype=dt).cuda()
+
+    for n, bw in inputs.CG_TABLE2 + [(12288, 63), (12288, 511)]:
+        rowp, indx, vals = inputs.banded_spd(6, 91, n, bw)
+        b = inputs.uniform_pm1(6, 92, (n,))
+        stop = 1e-24 * float(b @ b)
+        dv, di, dr, db = dev(vals, torch.float64), dev(indx, torch.int32), dev(rowp, torch.int32), \
+            dev(b, torch.float64)
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        work = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+        it = torch.zeros(1, dtype=torch.int32, device="cuda")
+        r2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ms = _timed_ms(lambda: mxm.mxm_cg(dv, di, dr, db, x, stop, 10 * n, work, it, r2,
+                                          stream=stream), 20, stream)
+        st = mxm.mxm_get_device_status()
+        k = int(it.item())
+        nnz = len(vals)
+        flops = k * (2.0 * nnz + 10.0 * n)
+        d = {"case": "cg", "n": n, "bw": bw, "nnz": nnz, "iters": k, "ms": round(ms, 4),
+             "us_per_step": round(ms * 1e3 / max(k, 1), 2),
+             "gflops": round(flops / (ms * 1e-3) / 1e9, 3), "status": st}
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < 0.2 or reps < 2:
+            o = oracle.cg(rowp, indx, vals, b, stop, 10 * n)
+            reps += 1
+        cms = (time.perf_counter() - t0) / reps * 1e3
+        d["cpu_oracle"] = {"ms": round(cms, 4), "iters": o["iters"],
+                           "gflops": round(o["iters"] * (2.0 * nnz + 10.0 * n) / (cms * 1e-3) / 1e9, 3),
+                           "cores": oracle.num_threads()}
+        emit(**d)
 
 
 def run_reference(args):

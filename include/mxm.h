@@ -48,7 +48,8 @@ typedef enum {
   MXM_ERR_TIMEOUT = 5,            /* a bounded device wait gave up (device status) */
   MXM_ERR_CUDA = 6,               /* a CUDA runtime call failed */
   MXM_ERR_NO_WORKSPACE = 7,       /* workspace needed while a stream is capturing */
-  MXM_ERR_WORKSPACE_TOO_SMALL = 8 /* caller workspace smaller than required */
+  MXM_ERR_WORKSPACE_TOO_SMALL = 8, /* caller workspace smaller than required */
+  MXM_ERR_BREAKDOWN = 9            /* conjugate gradients met (p, A p) <= 0 (device status) */
 } mxm_status;
 
 typedef enum {
@@ -166,8 +167,9 @@ mxm_status mxm_grouped(int64_t count, const mxm_problem* d_problems, int mode, i
 /*
  * mxm_get_device_status -- synchronise `stream`, then read and clear the
  * sticky device status word of the current device: MXM_OK, or the first of
- * MXM_ERR_NONFINITE / MXM_ERR_TIMEOUT / MXM_ERR_WORKSPACE_TOO_SMALL recorded
- * by a kernel since the last read.
+ * MXM_ERR_NONFINITE / MXM_ERR_TIMEOUT / MXM_ERR_WORKSPACE_TOO_SMALL /
+ * MXM_ERR_INVALID_ARG (a sparse structure indexing outside its arrays) /
+ * MXM_ERR_BREAKDOWN recorded by a kernel since the last read.
  */
 mxm_status mxm_get_device_status(void* stream);
 
@@ -221,6 +223,50 @@ mxm_status mxm_profile_read(double* ms, int max_phases, int64_t* calls);
 mxm_status mxm_spmv(const double* matvals, const int32_t* indx, const int32_t* rowp,
                     const double* x, double* y, int64_t nrows, int64_t ncols, int64_t nnz,
                     void* stream);
+
+/*
+ * mxm_cg -- conjugate gradients for A x = b (Sec. 3.4, the textbook
+ * iteration of Fig. 6 and the ArBB loop beside it), A an n x n symmetric
+ * positive definite matrix in the CSR form of mxm_spmv (nrows = ncols = n).
+ * x0 = 0, so r0 = p0 = b and r2 = (b, b); while r2 > stop and fewer than
+ * max_iters steps were taken: q = A p; alpha = r2 / (p, q); r -= alpha q;
+ * r2_new = (r, r); beta = r2_new / r2; x += alpha p; p = r + beta p.
+ *
+ * The whole solve is one launch on `stream` (a thread-block cluster of up
+ * to 16 CTAs, the loop test on the device: no host round trip per step).
+ * Arguments, all device memory, FP64 / int32, unaliased:
+ *   matvals, indx, rowp   A in CSR (nnz values, nnz columns, n + 1 row
+ *                         pointers; columns in [0, n));
+ *   b                     the right-hand side, n doubles (read only);
+ *   x                     the solution, n doubles (written);
+ *   work                  2 n doubles of scratch (r and q), caller-owned;
+ *                         mxm_cg_workspace_size(n) bytes;
+ *   iters                 one int32: the number of steps taken;
+ *   r2                    one double: the last (r, r) (the recursive
+ *                         residual, as the paper's loop test uses it);
+ *   r2_hist               NULL, or max_iters doubles: r2 after each step.
+ * Results: x after the last step.  The dot products are deterministic (the
+ * same result on every run for the same n and nnz).  A step with
+ * (p, A p) <= 0 is not taken: the loop ends and MXM_ERR_BREAKDOWN is
+ * recorded in the device status word.  Bad structure (a row pointer or
+ * column outside the arrays) is skipped and recorded as
+ * MXM_ERR_INVALID_ARG in the device status word; x is then unspecified.
+ * Host-side errors: n <= 0, max_iters < 0, NULL or overlapping arrays:
+ * MXM_ERR_INVALID_ARG; n > mxm_cg_max_n() or nnz > INT32_MAX:
+ * MXM_ERR_UNSUPPORTED; misaligned pointers: MXM_ERR_ALIGNMENT; a failed
+ * launch: MXM_ERR_CUDA.
+ */
+mxm_status mxm_cg(const double* matvals, const int32_t* indx, const int32_t* rowp,
+                  const double* b, double* x, int64_t n, int64_t nnz, double stop,
+                  int32_t max_iters, double* work, int32_t* iters, double* r2, double* r2_hist,
+                  void* stream);
+
+/* mxm_cg_max_n -- the largest n mxm_cg accepts (p is held twice in the
+ * shared memory of every CTA). */
+int64_t mxm_cg_max_n(void);
+
+/* mxm_cg_workspace_size -- bytes of `work` mxm_cg needs for order n. */
+size_t mxm_cg_workspace_size(int64_t n);
 
 /*
  * mxm_f64_emul_noalloc -- mxm_f64_emul (7-bit digits, `slices` slices) for

@@ -254,6 +254,7 @@ const char* mxm_status_string(mxm_status s) {
     case MXM_ERR_CUDA: return "MXM_ERR_CUDA";
     case MXM_ERR_NO_WORKSPACE: return "MXM_ERR_NO_WORKSPACE";
     case MXM_ERR_WORKSPACE_TOO_SMALL: return "MXM_ERR_WORKSPACE_TOO_SMALL";
+    case MXM_ERR_BREAKDOWN: return "MXM_ERR_BREAKDOWN";
   }
   return "MXM_ERR_UNKNOWN";
 }
@@ -487,6 +488,7 @@ mxm_status mxm_get_device_status(void* stream) {
   if (v & kStatusTimeout) return MXM_ERR_TIMEOUT;
   if (v & kStatusWorkspace) return MXM_ERR_WORKSPACE_TOO_SMALL;
   if (v & kStatusBounds) return MXM_ERR_INVALID_ARG;
+  if (v & kStatusBreakdown) return MXM_ERR_BREAKDOWN;
   return MXM_OK;
 }
 

@@ -13,6 +13,7 @@ constexpr int kStatusNonFinite = 1;
 constexpr int kStatusTimeout = 2;
 constexpr int kStatusWorkspace = 4;
 constexpr int kStatusBounds = 8;
+constexpr int kStatusBreakdown = 16;
 
 // Every bounded wait inside a kernel gives up after this long.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s

@@ -182,15 +182,17 @@ def csr_sampled(seed: int, stream: int, nrows: int, ncols: int, mean_len: float)
     return rowp.astype(np.int32), (key % max(ncols, 1)).astype(np.int32), vals
 
 
-def banded_spd(seed: int, stream: int, n: int, bw: int):
+def banded_spd(seed: int, stream: int, n: int, bw: int, shift: float = 1.0):
     """A random symmetric positive definite band matrix in CSR, as the
     conjugate-gradient inputs of Sec. 3.4 (Table 2): ``bw`` diagonals
     (bw odd; h = (bw - 1) / 2 on each side of the main one).  Entry
     (i, i + d), 1 <= d <= h, equals entry (i + d, i) and is word
     i * h + d - 1 of stream (seed, stream) as a uniform in [-1, 1); the
-    diagonal entry is 1 + the sum of the row's off-diagonal magnitudes, so
-    the matrix is strictly diagonally dominant with a positive diagonal
-    (hence SPD, eigenvalues in [1, 1 + 2 * max row sum] by Gershgorin).
+    diagonal entry is ``shift`` + the sum of the row's off-diagonal
+    magnitudes, so the matrix is strictly diagonally dominant with a
+    positive diagonal (hence SPD, eigenvalues in [shift, shift + 2 * max
+    off-diagonal row sum] by Gershgorin; a small shift gives a worse
+    conditioned system and more steps).
     Returns (rowp int32[n + 1], indx int32[nnz], matvals float64[nnz])."""
     if bw < 1 or bw % 2 == 0:
         raise ValueError("bw must be odd and positive")
@@ -202,7 +204,7 @@ def banded_spd(seed: int, stream: int, n: int, bw: int):
     for d in range(1, h + 1):
         band[:n - d, h + d] = up[:n - d, d - 1]
         band[d:, h - d] = up[:n - d, d - 1]
-    band[:, h] = 1.0 + np.abs(band).sum(axis=1)
+    band[:, h] = shift + np.abs(band).sum(axis=1)
     cols = np.arange(n)[:, None] + np.arange(-h, h + 1)[None, :]
     keep = (cols >= 0) & (cols < n)
     rowp = np.zeros(n + 1, dtype=np.int64)

@@ -22,6 +22,7 @@ MXM_ERR_TIMEOUT = 5
 MXM_ERR_CUDA = 6
 MXM_ERR_NO_WORKSPACE = 7
 MXM_ERR_WORKSPACE_TOO_SMALL = 8
+MXM_ERR_BREAKDOWN = 9
 
 MODE_F64 = 0
 MODE_EMUL_I8 = 1
@@ -53,6 +54,10 @@ SIGNATURES = {
     "mxm_profile_read": (_I, [ctypes.POINTER(ctypes.c_double), _I, ctypes.POINTER(_I64)]),
     "mxm_f64_emul_noalloc": (_I, [_P, _P, _P, _I64, _I64, _I64, _I, _P]),
     "mxm_spmv": (_I, [_P, _P, _P, _P, _P, _I64, _I64, _I64, _P]),
+    "mxm_cg": (_I, [_P, _P, _P, _P, _P, _I64, _I64, ctypes.c_double, ctypes.c_int32, _P, _P, _P,
+                    _P, _P]),
+    "mxm_cg_max_n": (_I64, []),
+    "mxm_cg_workspace_size": (_SZ, [_I64]),
 }
 
 _lib = None
@@ -263,3 +268,39 @@ def mxm_spmv(matvals, indx, rowp, x, y, stream=None):
                            y.data_ptr(), nrows, x.shape[0], matvals.shape[0],
                            _stream_ptr(stream)), "mxm_spmv")
     return y
+
+
+def mxm_cg(matvals, indx, rowp, b, x, stop, max_iters, work=None, iters=None, r2=None,
+           r2_hist=None, stream=None):
+    """Conjugate gradients for A x = b (Sec. 3.4), A SPD in CSR (CUDA
+    tensors: matvals float64, indx and rowp int32, b and x float64), the
+    whole solve in one launch on ``stream``.  ``iters`` (int32[1]), ``r2``
+    (float64[1]) and ``work`` (float64[2n]) are allocated when not given;
+    ``r2_hist`` (float64[max_iters]) is optional.  Returns (iters, r2) as
+    device tensors; read them after the stream (and check
+    mxm_get_device_status for MXM_ERR_BREAKDOWN)."""
+    import torch
+    for name, t, dt in (("matvals", matvals, torch.float64), ("indx", indx, torch.int32),
+                        ("rowp", rowp, torch.int32), ("b", b, torch.float64),
+                        ("x", x, torch.float64)):
+        if not isinstance(t, torch.Tensor) or t.dtype != dt or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA {dt} tensor")
+        if t.dim() != 1 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous 1-D tensor")
+    n = rowp.shape[0] - 1
+    if n < 1 or b.shape[0] != n or x.shape[0] != n or indx.shape[0] != matvals.shape[0]:
+        raise ValueError("CSR array lengths do not match")
+    dev = b.device
+    work = torch.empty(2 * n, dtype=torch.float64, device=dev) if work is None else work
+    iters = torch.zeros(1, dtype=torch.int32, device=dev) if iters is None else iters
+    r2 = torch.zeros(1, dtype=torch.float64, device=dev) if r2 is None else r2
+    if work.dtype != torch.float64 or work.numel() < 2 * n or not work.is_contiguous():
+        raise ValueError("work must be a contiguous float64 tensor of 2n entries")
+    if r2_hist is not None and (r2_hist.dtype != torch.float64 or r2_hist.numel() < max_iters):
+        raise ValueError("r2_hist must be a float64 tensor of max_iters entries")
+    _check(load().mxm_cg(matvals.data_ptr(), indx.data_ptr(), rowp.data_ptr(), b.data_ptr(),
+                         x.data_ptr(), n, matvals.shape[0], float(stop), int(max_iters),
+                         work.data_ptr(), iters.data_ptr(), r2.data_ptr(),
+                         r2_hist.data_ptr() if r2_hist is not None else None,
+                         _stream_ptr(stream)), "mxm_cg")
+    return iters, r2

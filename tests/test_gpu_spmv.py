@@ -73,11 +73,13 @@ def test_identity_permutation_and_empty():
     check_bound(run_spmv(rowp, indx, vals, x), rowp, indx, vals, x, "mixed lengths")
 
 
-@pytest.mark.parametrize("avg", [2, 6, 12, 24, 200])
-def test_every_lane_group_width(avg):
-    """Average row lengths that select 2, 4, 8, 16 and 32 lanes per row."""
-    n = 5000
-    rowp, indx, vals = inputs.csr_random(1, 92, n, avg / n)
+@pytest.mark.parametrize("avg,n", [(3, 160_000), (12, 160_000), (48, 160_000), (200, 40_000),
+                                   (600, 20_000), (48, 2_000)])
+def test_every_lane_group_width(avg, n):
+    """Average row lengths and row counts that select 2, 4, 8, 16 and 32
+    lanes per row (and a short matrix widened for occupancy), with rounds
+    of 2 or 4 values per lane and ragged last rounds."""
+    rowp, indx, vals = inputs.csr_sampled(1, 92, n, n, avg)
     x = inputs.exp_spread(1, 94, (n,), -10, 10)
     check_bound(run_spmv(rowp, indx, vals, x), rowp, indx, vals, x, f"avg={avg}")
 
