@@ -54,6 +54,10 @@ def parse():
                         "workload suite (FP64 sweep, slice counts and modes, rectangular "
                         "shapes, grouped batch under a CUDA graph; mod2as sparse products; "
                         "conjugate-gradient solves)")
+    p.add_argument("--only", default="",
+                   help="with --suite spmv / cg: run only the rows whose key (case:n, or "
+                        "cg:n:bw) is this string or extends it by ':...', e.g. "
+                        "spmv_large:200000, cg:1024 or cg:1024:511")
     return p.parse_args()
 
 
@@ -461,9 +465,9 @@ def run_suite(args):
         print(json.dumps(dict(suite=True, **d)), flush=True)
 
     if args.suite in ("all", "spmv"):
-        run_spmv_suite(emit, stream, peaks)
+        run_spmv_suite(emit, stream, peaks, args.only)
     if args.suite in ("all", "cg"):
-        run_cg_suite(emit, stream)
+        run_cg_suite(emit, stream, args.only)
     if args.suite in ("spmv", "cg"):
         return
     dmma = mxm.mxm_peak_probe(1)
@@ -544,6 +548,11 @@ def run_suite(args):
         del ws, g
 
 
+def _selected(key, only):
+    """--only: the key itself, or a key that extends it by ':...'."""
+    return not only or key == only or key.startswith(only + ":")
+
+
 # Table 1 of the paper: mod2as orders and fill in percent
 SPMV_TABLE1 = [(100, 3.50), (200, 3.75), (256, 5.0), (400, 4.38), (500, 5.00), (512, 4.00),
                (960, 4.50), (1000, 5.00), (1024, 5.50), (2000, 7.50), (4096, 3.50),
@@ -556,7 +565,7 @@ def spmv_bytes(nrows, ncols, nnz):
     return 12 * nnz + 4 * (nrows + 1) + 8 * nrows + 8 * ncols
 
 
-def run_spmv_suite(emit, stream, peaks):
+def run_spmv_suite(emit, stream, peaks, only=""):
     """mod2as (Sec. 3.2) rows: the Table 1 orders and fills (operands well
     inside L2: repeated calls, L2-warm, as the paper's repeated kernel
     loop), then two matrices of 400-600 MB (larger than L2, cold between
@@ -573,6 +582,8 @@ def run_spmv_suite(emit, stream, peaks):
 
     hbm = peaks.get("hbm_gbs") if peaks else None
     for n, fill in SPMV_TABLE1 + [(2_000_000, None), (200_000, None)]:
+        if not _selected(f"{'spmv_table1' if fill is not None else 'spmv_large'}:{n}", only):
+            continue
         if fill is not None:
             rowp, indx, vals = inputs.csr_random(0, 70, n, fill / 100.0)
             case, reps = "spmv_table1", 50
@@ -608,7 +619,7 @@ def run_spmv_suite(emit, stream, peaks):
         torch.cuda.empty_cache()
 
 
-def run_cg_suite(emit, stream):
+def run_cg_suite(emit, stream, only=""):
     """Conjugate gradients (Sec. 3.4): the Table 2 orders and bandwidths,
     plus the largest order the one-launch solver takes, each solved to
     r2 <= 1e-24 (b, b).  Rate in the paper's terms: FP64 operations of the
@@ -624,16 +635,17 @@ def run_cg_suite(emit, stream):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dtype=dt).cuda()
 
     for n, bw in inputs.CG_TABLE2 + [(12288, 63), (12288, 511)]:
+        if not _selected(f"cg:{n}:{bw}", only):
+            continue
         rowp, indx, vals = inputs.banded_spd(6, 91, n, bw)
         b = inputs.uniform_pm1(6, 92, (n,))
         stop = 1e-24 * float(b @ b)
         dv, di, dr, db = dev(vals, torch.float64), dev(indx, torch.int32), dev(rowp, torch.int32), \
             dev(b, torch.float64)
         x = torch.empty(n, dtype=torch.float64, device="cuda")
-        work = torch.empty(2 * n, dtype=torch.float64, device="cuda")
         it = torch.zeros(1, dtype=torch.int32, device="cuda")
         r2 = torch.zeros(1, dtype=torch.float64, device="cuda")
-        ms = _timed_ms(lambda: mxm.mxm_cg(dv, di, dr, db, x, stop, 10 * n, work, it, r2,
+        ms = _timed_ms(lambda: mxm.mxm_cg(dv, di, dr, db, x, stop, 10 * n, it, r2,
                                           stream=stream), 20, stream)
         st = mxm.mxm_get_device_status()
         k = int(it.item())

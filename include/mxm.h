@@ -238,9 +238,8 @@ mxm_status mxm_spmv(const double* matvals, const int32_t* indx, const int32_t* r
  *   matvals, indx, rowp   A in CSR (nnz values, nnz columns, n + 1 row
  *                         pointers; columns in [0, n));
  *   b                     the right-hand side, n doubles (read only);
- *   x                     the solution, n doubles (written);
- *   work                  2 n doubles of scratch (r and q), caller-owned;
- *                         mxm_cg_workspace_size(n) bytes;
+ *   x                     the solution, n doubles (written once, after the
+ *                         last step; r, q and x live in shared memory);
  *   iters                 one int32: the number of steps taken;
  *   r2                    one double: the last (r, r) (the recursive
  *                         residual, as the paper's loop test uses it);
@@ -251,22 +250,18 @@ mxm_status mxm_spmv(const double* matvals, const int32_t* indx, const int32_t* r
  * recorded in the device status word.  Bad structure (a row pointer or
  * column outside the arrays) is skipped and recorded as
  * MXM_ERR_INVALID_ARG in the device status word; x is then unspecified.
- * Host-side errors: n <= 0, max_iters < 0, NULL or overlapping arrays:
+ * Host-side errors: n <= 0, max_iters < 0, NULL arrays, x overlapping an input:
  * MXM_ERR_INVALID_ARG; n > mxm_cg_max_n() or nnz > INT32_MAX:
  * MXM_ERR_UNSUPPORTED; misaligned pointers: MXM_ERR_ALIGNMENT; a failed
  * launch: MXM_ERR_CUDA.
  */
 mxm_status mxm_cg(const double* matvals, const int32_t* indx, const int32_t* rowp,
                   const double* b, double* x, int64_t n, int64_t nnz, double stop,
-                  int32_t max_iters, double* work, int32_t* iters, double* r2, double* r2_hist,
-                  void* stream);
+                  int32_t max_iters, int32_t* iters, double* r2, double* r2_hist, void* stream);
 
 /* mxm_cg_max_n -- the largest n mxm_cg accepts (p is held twice in the
  * shared memory of every CTA). */
 int64_t mxm_cg_max_n(void);
-
-/* mxm_cg_workspace_size -- bytes of `work` mxm_cg needs for order n. */
-size_t mxm_cg_workspace_size(int64_t n);
 
 /*
  * mxm_f64_emul_noalloc -- mxm_f64_emul (7-bit digits, `slices` slices) for

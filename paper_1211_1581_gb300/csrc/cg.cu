@@ -7,7 +7,8 @@
 // rounding of a solve does not depend on the device) owns the system.  CTA c
 // owns the rows [c n / C, (c + 1) n / C); every CTA keeps the whole search
 // direction p in its shared memory (two buffers), so the sparse product
-// gathers p from shared memory.  One step:
+// gathers p from shared memory, and its own rows of q, r and x there too
+// (x goes to global memory once, after the loop).  One step:
 //
 //   1. q = A p on the CTA's rows (lane groups of G as in the mod2as kernel);
 //      the CTA's share of (p, q) goes to slot c of every CTA's table
@@ -25,8 +26,13 @@
 // barriers; nothing here spins.  A step with (p, A p) <= 0 is not taken (the
 // loop ends and the breakdown bit of the device status word is set); a row
 // pointer or column outside the arrays is skipped and sets the bounds bit.
-// r and q live in a caller workspace of 2n doubles, x is written in place
-// (x0 = 0, so r0 = p0 = b as in the paper's listing).
+// x0 = 0, so r0 = p0 = b as in the paper's listing.
+//
+// FP64 arithmetic is scarce on this GPU (a warp-wide FP64 instruction holds
+// an SM sub-partition's FP64 pipe for tens of clocks), so the scalars alpha
+// and beta are computed once per CTA by one thread and read from shared
+// memory, and the CTA sums are trees over shared memory in which only the
+// warps with work issue FP64 adds.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -43,7 +49,8 @@ namespace {
 constexpr int kCgThreads = 512;
 constexpr int kCgWarps = kCgThreads / 32;
 constexpr int kCgMaxCluster = 16;
-constexpr int64_t kCgMaxN = 12288;  // two p buffers of 96 KiB in shared memory
+constexpr int kCgBatch = 4;  // values per lane per round of the product
+constexpr int64_t kCgMaxN = 12288;  // p twice (192 KiB) and 3 x 768 own rows, cluster of 16
 
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
@@ -79,25 +86,45 @@ __device__ __forceinline__ void st_peer(uint32_t addr, double v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
 }
 
-// Sum of one double per thread, the same order on every call: each warp's
-// xor tree, then warp 0 adds the kCgWarps warp sums by another xor tree.
-// Every thread receives the total.
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    double t = lane < kCgWarps ? red[lane] : 0.0;
-#pragma unroll
-    for (int o = kCgWarps / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
-    if (lane == 0) red[kCgWarps] = t;
+// Sum of one double per thread in a fixed tree (the same order on every
+// call with the same `active`): the values of threads at or beyond `active`
+// must be 0 and are not added.  Pairs across halves of the smallest power
+// of two >= active in shared memory down to one warp, then that warp's xor
+// tree.  Every thread of warp 0 receives the total.  Only warps holding
+// values issue FP64 adds: each warp-wide FP64 instruction holds its SM
+// sub-partition's FP64 pipe for about 64 clocks on this GPU.
+__device__ __forceinline__ double block_sum(double v, double* red, int active) {
+  const int tid = threadIdx.x;
+  int width = 32;
+  while (width < active) width <<= 1;
+  if (width > 32) {
+    red[tid] = v;
+    __syncthreads();
+    for (int s = width / 2; s >= 32; s >>= 1) {
+      if (tid < s) red[tid] += red[tid + s];
+      __syncthreads();
+    }
+    if (tid < 32) v = red[tid];
   }
-  __syncthreads();
-  const double total = red[kCgWarps];
-  __syncthreads();  // red is reused by the next call
-  return total;
+  if (tid < 32) {
+    // xor butterfly over the smallest power-of-two block of lanes holding
+    // values (every lane of the block gets the same sum: each level adds
+    // the same two numbers in both lanes), then lane 0's to all
+    int P = 1;
+    while (P < active && P < 32) P <<= 1;
+    for (int o = P / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    v = __shfl_sync(0xFFFFFFFFu, v, 0);
+  }
+  return v;
+}
+
+// Sum of the C shares of a cluster in rank order pairs (an xor tree over
+// lanes 0..C-1 of warp 0); every thread of warp 0 receives it.
+__device__ __forceinline__ double shares_sum(const double* sh, uint32_t C) {
+  const int lane = threadIdx.x & 31;
+  double v = lane < static_cast<int>(C) ? sh[lane] : 0.0;
+  for (uint32_t o = 1; o < C; o <<= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
 }
 
 struct CgArgs {
@@ -106,9 +133,8 @@ struct CgArgs {
   const int32_t* rowp;
   const double* b;
   double* x;
-  double* r;  // workspace: n
-  double* q;  // workspace: n
   int64_t n, nnz;
+  int64_t rows_cap;  // ceil(n / C): own rows of q, r, x in shared memory
   double stop;
   int32_t max_iters;
   int32_t* iters_out;  // device, 1
@@ -119,14 +145,22 @@ struct CgArgs {
 
 template <int G>
 __global__ void __launch_bounds__(kCgThreads, 1) cg_cluster_kernel(const CgArgs a) {
-  extern __shared__ double pbuf[];  // two buffers of n doubles
-  __shared__ double red[kCgWarps + 1];
+  // dynamic shared memory: p twice (n each), then q, r, x of the own rows
+  extern __shared__ double dsm[];
+  __shared__ double red[kCgThreads];
   __shared__ double shares[2][kCgMaxCluster];
+  __shared__ double scal[2];  // alpha or beta, and r2, written by thread 0
+  __shared__ int stop_flag;   // (p, A p) <= 0, written by thread 0
   constexpr int kRowsPerWarp = 32 / G;
   const int64_t n = a.n;
+  double* const qs = dsm + 2 * n;
+  double* const rs = qs + a.rows_cap;
+  double* const xs = rs + a.rows_cap;
   const uint32_t rank = cluster_rank(), C = cluster_size();
   const int64_t lo = static_cast<int64_t>(rank) * n / C;
   const int64_t hi = static_cast<int64_t>(rank + 1) * n / C;
+  const int64_t own = hi - lo;
+  const int active = own < kCgThreads ? static_cast<int>(own) : kCgThreads;  // threads with rows
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int sub = lane & (G - 1), grp = lane / G;
 
@@ -135,15 +169,17 @@ __global__ void __launch_bounds__(kCgThreads, 1) cg_cluster_kernel(const CgArgs 
   double bb = 0.0;
   for (int64_t i = tid; i < n; i += kCgThreads) {
     const double bi = a.b[i];
-    pbuf[i] = bi;
+    dsm[i] = bi;
     bb = fma(bi, bi, bb);
   }
-  for (int64_t i = lo + tid; i < hi; i += kCgThreads) {
-    a.x[i] = 0.0;
-    a.r[i] = a.b[i];
+  for (int64_t i = tid; i < own; i += kCgThreads) {
+    xs[i] = 0.0;
+    rs[i] = a.b[lo + i];
   }
-  double r2 = block_sum(bb, red);
+  bb = block_sum(bb, red, kCgThreads);
+  if (tid == 0) scal[1] = bb;
   cluster_barrier();  // every CTA's p buffer is filled before any peer writes into it
+  double r2 = scal[1];
 
   const uint32_t shares_pq = smem_addr(&shares[0][rank]);
   const uint32_t shares_rr = smem_addr(&shares[1][rank]);
@@ -151,10 +187,9 @@ __global__ void __launch_bounds__(kCgThreads, 1) cg_cluster_kernel(const CgArgs 
   int cur = 0;
   int32_t k = 0;
   while (r2 > a.stop && k < a.max_iters) {
-    const double* p = pbuf + cur * n;
-    double* pn = pbuf + (cur ^ 1) * n;
-    // 1. q = A p on the own rows, and the CTA's share of (p, q)
-    double pq = 0.0;
+    const double* p = dsm + cur * n;
+    double* pn = dsm + (cur ^ 1) * n;
+    // 1. q = A p on the own rows, then the CTA's share of (p, q)
     for (int64_t base = lo + static_cast<int64_t>(warp) * kRowsPerWarp; base < hi;
          base += static_cast<int64_t>(kCgWarps) * kRowsPerWarp) {
       const int64_t row = base + grp;
@@ -167,49 +202,74 @@ __global__ void __launch_bounds__(kCgThreads, 1) cg_cluster_kernel(const CgArgs 
           re = rb;
         }
       }
+      // kCgBatch values per lane per round (positions j0, j0 + G, ...):
+      // the loads first, so that the matrix streams from L2 with many
+      // loads in flight, then the fused multiply-adds in storage order
       double t = 0.0;
-      for (int64_t j = rb + sub; j < re; j += G) {
-        const int32_t c = __ldg(a.indx + j);
-        const bool ok = c >= 0 && c < n;
-        bad |= !ok;
-        if (ok) t = fma(__ldg(a.vals + j), p[c], t);
+      for (int64_t j0 = rb + sub; j0 < re; j0 += G * kCgBatch) {
+        int32_t c[kCgBatch];
+        double v[kCgBatch];
+#pragma unroll
+        for (int u = 0; u < kCgBatch; ++u) {
+          const int64_t j = j0 + static_cast<int64_t>(u) * G;
+          c[u] = j < re ? __ldg(a.indx + j) : -1;
+          v[u] = j < re ? __ldg(a.vals + j) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kCgBatch; ++u) {
+          const bool ok = c[u] >= 0 && c[u] < n;
+          bad |= !ok && j0 + static_cast<int64_t>(u) * G < re;
+          if (ok) t = fma(v[u], p[c[u]], t);
+        }
       }
 #pragma unroll
       for (int o = G / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
-      if (row < hi && sub == 0) {
-        a.q[row] = t;
-        pq = fma(p[row], t, pq);
-      }
+      if (row < hi && sub == 0) qs[row - lo] = t;
     }
-    pq = block_sum(pq, red);
+    __syncthreads();
+    double pq = 0.0;
+    for (int64_t i = tid; i < own; i += kCgThreads) pq = fma(p[lo + i], qs[i], pq);
+    pq = block_sum(pq, red, active);
     if (tid < static_cast<int>(C)) st_peer(peer_addr(shares_pq, tid), pq);
     cluster_barrier();
-    double pAp = 0.0;
-    for (uint32_t c = 0; c < C; ++c) pAp += shares[0][c];
-    if (!(pAp > 0.0)) {  // the same test in every CTA
+    if (tid < 32) {
+      const double pAp = shares_sum(shares[0], C);
+      if (tid == 0) {
+        stop_flag = !(pAp > 0.0);
+        scal[0] = r2 / pAp;  // alpha
+      }
+    }
+    __syncthreads();
+    if (stop_flag) {  // the same in every CTA: the same shares, the same order
       breakdown = true;
       break;
     }
-    // 2. alpha, r and x on the own rows, and the CTA's share of (r, r)
-    const double alpha = r2 / pAp;
+    const double alpha = scal[0];
+    // 2. r and x on the own rows, and the CTA's share of (r, r)
     double rr = 0.0;
-    for (int64_t i = lo + tid; i < hi; i += kCgThreads) {
-      const double ri = fma(-alpha, a.q[i], a.r[i]);
-      a.r[i] = ri;
-      a.x[i] = fma(alpha, p[i], a.x[i]);
+    for (int64_t i = tid; i < own; i += kCgThreads) {
+      const double ri = fma(-alpha, qs[i], rs[i]);
+      rs[i] = ri;
+      xs[i] = fma(alpha, p[lo + i], xs[i]);
       rr = fma(ri, ri, rr);
     }
-    rr = block_sum(rr, red);
+    rr = block_sum(rr, red, active);
     if (tid < static_cast<int>(C)) st_peer(peer_addr(shares_rr, tid), rr);
     cluster_barrier();
-    double r2_new = 0.0;
-    for (uint32_t c = 0; c < C; ++c) r2_new += shares[1][c];
-    // 3. beta and the next direction, broadcast to every CTA's other buffer
-    const double beta = r2_new / r2;
-    r2 = r2_new;
-    for (int64_t i = lo + tid; i < hi; i += kCgThreads) {
-      const double pi = fma(beta, p[i], a.r[i]);
-      const uint32_t local = smem_addr(pn + i);
+    if (tid < 32) {
+      const double r2n = shares_sum(shares[1], C);
+      if (tid == 0) {
+        scal[1] = r2n;
+        scal[0] = r2n / r2;  // beta
+      }
+    }
+    __syncthreads();
+    // 3. the next direction, broadcast to every CTA's other buffer
+    const double beta = scal[0];
+    r2 = scal[1];
+    for (int64_t i = tid; i < own; i += kCgThreads) {
+      const double pi = fma(beta, p[lo + i], rs[i]);
+      const uint32_t local = smem_addr(pn + lo + i);
       for (uint32_t c = 0; c < C; ++c) st_peer(peer_addr(local, c), pi);
     }
     if (rank == 0 && tid == 0 && a.r2_hist != nullptr) a.r2_hist[k] = r2;
@@ -217,6 +277,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) cg_cluster_kernel(const CgArgs 
     cur ^= 1;
     cluster_barrier();
   }
+  for (int64_t i = tid; i < own; i += kCgThreads) a.x[lo + i] = xs[i];
   if (rank == 0 && tid == 0) {
     *a.iters_out = k;
     *a.r2_out = r2;
@@ -226,9 +287,16 @@ __global__ void __launch_bounds__(kCgThreads, 1) cg_cluster_kernel(const CgArgs 
   cluster_barrier();  // no CTA leaves while a peer may still address its shared memory
 }
 
+// Dynamic shared memory of a cluster of C for order n.
+size_t cg_smem_bytes(int64_t n, int C) {
+  const int64_t rows_cap = (n + C - 1) / C;
+  return static_cast<size_t>(2 * n + 3 * rows_cap) * sizeof(double);
+}
+
 template <int G>
-cudaError_t launch_cg_g(const CgArgs& a, int C, cudaStream_t s) {
-  const size_t smem = static_cast<size_t>(2 * a.n) * sizeof(double);
+cudaError_t launch_cg_g(CgArgs a, int C, cudaStream_t s) {
+  const size_t smem = cg_smem_bytes(a.n, C);
+  a.rows_cap = (a.n + C - 1) / C;
   cudaError_t e = cudaFuncSetAttribute(cg_cluster_kernel<G>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
@@ -259,23 +327,43 @@ cudaError_t launch_cg_g(const CgArgs& a, int C, cudaStream_t s) {
 
 }  // namespace
 
-// Cluster size from the matrix alone: enough CTAs that each has a few
-// thousand values per step (FP64 fused multiply-adds are the bound of the
-// product), at least 32 rows per CTA, at most 16.
-int cg_cluster_size(int64_t n, int64_t nnz) {
-  int C = 1;
-  while (C < kCgMaxCluster && nnz / (2 * C) >= 4096 && n / (2 * C) >= 32) C *= 2;
+// Cluster size from the order alone (so the rounding of a solve depends on
+// n and nnz only): 16 CTAs, the most FP64 pipes a cluster reaches, as long
+// as each keeps 8 rows; the cluster barrier costs the same for any size.
+int cg_cluster_size(int64_t n, int64_t /*nnz*/) {
+  int C = kCgMaxCluster;
+  while (C > 1 && n / C < 8) C /= 2;
   return C;
 }
 
-// Lanes per row: about 8 values per lane, and enough row groups for the
-// CTA's warps.
+// Lanes per row: the G in {1, ..., 32} whose product step issues the
+// fewest warp-wide FP64 instructions on the busiest SM sub-partition:
+// a warp takes 32 / G rows per round, each round costs ceil(L / G) fused
+// multiply-adds and log2(G) shuffle-adds (L the average row length), the
+// CTA's 16 warps sit four to a sub-partition.  Ties go to the wider group.
+// G is at least what keeps all 512 threads on rows when the CTA has fewer
+// than 512 rows (the matrix streams from L2 and needs the loads of every
+// lane in flight), and at least 8 for rows of 64 values or more (loads of
+// consecutive values by 8 lanes fill whole 32-byte sectors).
 int cg_group(int64_t n, int64_t nnz, int C) {
-  const double avg = n > 0 ? static_cast<double>(nnz) / static_cast<double>(n) : 0.0;
-  int g = avg <= 12 ? 2 : avg <= 24 ? 4 : avg <= 96 ? 8 : avg <= 384 ? 16 : 32;
-  const int64_t rows = n / C;
-  while (g < 32 && rows * g < 32 * kCgWarps) g *= 2;
-  return g;
+  const int64_t rows = (n + C - 1) / C;
+  const int64_t L = n > 0 ? (nnz + n - 1) / n : 0;
+  int best = 32;
+  int64_t best_cost = -1;
+  for (int g = 32, lg = 5; g >= 1; g /= 2, --lg) {
+    const int64_t groups = (rows + (32 / g) - 1) / (32 / g);  // warp-rounds in all
+    const int64_t warps = groups < kCgWarps ? groups : kCgWarps;
+    const int64_t rounds = (groups + kCgWarps - 1) / kCgWarps;
+    const int64_t per_warp = rounds * ((L + g - 1) / g + lg);
+    const int64_t cost = (warps + 3) / 4 * per_warp;
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = g;
+    }
+  }
+  while (best < 32 && rows * best < kCgThreads && best * 2 <= L) best *= 2;
+  while (best < 8 && best * 8 <= L) best *= 2;  // long rows: 8 lanes coalesce the loads
+  return best;
 }
 
 }  // namespace mxm
@@ -284,35 +372,32 @@ using namespace mxm;
 
 extern "C" int64_t mxm_cg_max_n(void) { return kCgMaxN; }
 
-extern "C" size_t mxm_cg_workspace_size(int64_t n) {
-  return n > 0 ? static_cast<size_t>(2 * n) * sizeof(double) : 0;
-}
-
 extern "C" mxm_status mxm_cg(const double* matvals, const int32_t* indx, const int32_t* rowp,
                              const double* b, double* x, int64_t n, int64_t nnz, double stop,
-                             int32_t max_iters, double* work, int32_t* iters, double* r2,
+                             int32_t max_iters, int32_t* iters, double* r2,
                              double* r2_hist, void* stream) {
   if (n < 0 || nnz < 0 || max_iters < 0) return MXM_ERR_INVALID_ARG;
   if (n == 0) return MXM_ERR_INVALID_ARG;
   if (n > kCgMaxN || nnz > INT32_MAX) return MXM_ERR_UNSUPPORTED;
-  if (rowp == nullptr || b == nullptr || x == nullptr || work == nullptr || iters == nullptr ||
+  if (rowp == nullptr || b == nullptr || x == nullptr || iters == nullptr ||
       r2 == nullptr || (nnz > 0 && (matvals == nullptr || indx == nullptr)))
     return MXM_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(matvals) | reinterpret_cast<uintptr_t>(b) |
-       reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(work) |
+       reinterpret_cast<uintptr_t>(x) |
        reinterpret_cast<uintptr_t>(r2) | reinterpret_cast<uintptr_t>(r2_hist)) & 7 ||
       (reinterpret_cast<uintptr_t>(indx) | reinterpret_cast<uintptr_t>(rowp) |
        reinterpret_cast<uintptr_t>(iters)) & 3)
     return MXM_ERR_ALIGNMENT;
-  // x and the workspace must not overlap each other or the inputs read while they change
+  // x is written only after the loop, but it must not alias what the loop reads
   const auto overlap = [](const void* p, size_t pb, const void* q, size_t qb) {
     const auto a0 = reinterpret_cast<uintptr_t>(p), b0 = reinterpret_cast<uintptr_t>(q);
     return a0 < b0 + qb && b0 < a0 + pb;
   };
   const size_t vb = static_cast<size_t>(n) * sizeof(double);
-  if (overlap(x, vb, work, 2 * vb) || overlap(x, vb, b, vb) || overlap(work, 2 * vb, b, vb) ||
+  if (overlap(x, vb, b, vb) ||
       (nnz > 0 && (overlap(x, vb, matvals, nnz * sizeof(double)) ||
-                   overlap(work, 2 * vb, matvals, nnz * sizeof(double)))))
+                   overlap(x, vb, indx, nnz * sizeof(int32_t)))) ||
+      overlap(x, vb, rowp, static_cast<size_t>(n + 1) * sizeof(int32_t)))
     return MXM_ERR_INVALID_ARG;
   int* status = device_status_word();
   if (status == nullptr) return MXM_ERR_CUDA;
@@ -322,9 +407,8 @@ extern "C" mxm_status mxm_cg(const double* matvals, const int32_t* indx, const i
   a.rowp = rowp;
   a.b = b;
   a.x = x;
-  a.r = work;
-  a.q = work + n;
   a.n = n;
+  a.rows_cap = n;
   a.nnz = nnz;
   a.stop = stop;
   a.max_iters = max_iters;
@@ -337,6 +421,7 @@ extern "C" mxm_status mxm_cg(const double* matvals, const int32_t* indx, const i
   // the size's cluster, or a smaller one where the device cannot place it
   for (int C = cg_cluster_size(n, nnz); C >= 1 && e == cudaErrorLaunchOutOfResources; C /= 2) {
     switch (cg_group(n, nnz, C)) {
+      case 1: e = launch_cg_g<1>(a, C, s); break;
       case 2: e = launch_cg_g<2>(a, C, s); break;
       case 4: e = launch_cg_g<4>(a, C, s); break;
       case 8: e = launch_cg_g<8>(a, C, s); break;

@@ -55,9 +55,8 @@ SIGNATURES = {
     "mxm_f64_emul_noalloc": (_I, [_P, _P, _P, _I64, _I64, _I64, _I, _P]),
     "mxm_spmv": (_I, [_P, _P, _P, _P, _P, _I64, _I64, _I64, _P]),
     "mxm_cg": (_I, [_P, _P, _P, _P, _P, _I64, _I64, ctypes.c_double, ctypes.c_int32, _P, _P, _P,
-                    _P, _P]),
+                    _P]),
     "mxm_cg_max_n": (_I64, []),
-    "mxm_cg_workspace_size": (_SZ, [_I64]),
 }
 
 _lib = None
@@ -270,12 +269,12 @@ def mxm_spmv(matvals, indx, rowp, x, y, stream=None):
     return y
 
 
-def mxm_cg(matvals, indx, rowp, b, x, stop, max_iters, work=None, iters=None, r2=None,
-           r2_hist=None, stream=None):
+def mxm_cg(matvals, indx, rowp, b, x, stop, max_iters, iters=None, r2=None, r2_hist=None,
+           stream=None):
     """Conjugate gradients for A x = b (Sec. 3.4), A SPD in CSR (CUDA
     tensors: matvals float64, indx and rowp int32, b and x float64), the
-    whole solve in one launch on ``stream``.  ``iters`` (int32[1]), ``r2``
-    (float64[1]) and ``work`` (float64[2n]) are allocated when not given;
+    whole solve in one launch on ``stream``.  ``iters`` (int32[1]) and
+    ``r2`` (float64[1]) are allocated when not given;
     ``r2_hist`` (float64[max_iters]) is optional.  Returns (iters, r2) as
     device tensors; read them after the stream (and check
     mxm_get_device_status for MXM_ERR_BREAKDOWN)."""
@@ -291,16 +290,13 @@ def mxm_cg(matvals, indx, rowp, b, x, stop, max_iters, work=None, iters=None, r2
     if n < 1 or b.shape[0] != n or x.shape[0] != n or indx.shape[0] != matvals.shape[0]:
         raise ValueError("CSR array lengths do not match")
     dev = b.device
-    work = torch.empty(2 * n, dtype=torch.float64, device=dev) if work is None else work
     iters = torch.zeros(1, dtype=torch.int32, device=dev) if iters is None else iters
     r2 = torch.zeros(1, dtype=torch.float64, device=dev) if r2 is None else r2
-    if work.dtype != torch.float64 or work.numel() < 2 * n or not work.is_contiguous():
-        raise ValueError("work must be a contiguous float64 tensor of 2n entries")
     if r2_hist is not None and (r2_hist.dtype != torch.float64 or r2_hist.numel() < max_iters):
         raise ValueError("r2_hist must be a float64 tensor of max_iters entries")
     _check(load().mxm_cg(matvals.data_ptr(), indx.data_ptr(), rowp.data_ptr(), b.data_ptr(),
                          x.data_ptr(), n, matvals.shape[0], float(stop), int(max_iters),
-                         work.data_ptr(), iters.data_ptr(), r2.data_ptr(),
+                         iters.data_ptr(), r2.data_ptr(),
                          r2_hist.data_ptr() if r2_hist is not None else None,
                          _stream_ptr(stream)), "mxm_cg")
     return iters, r2
