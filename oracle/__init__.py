@@ -22,6 +22,8 @@ Functions (all take and return numpy arrays, row-major float64):
   in storage order, by Dot2, and |A||x|.
 * ``cg``           - conjugate gradients (Sec. 3.4, Fig. 6) on a CSR SPD
   matrix, the paper's step order.
+* ``dft`` / ``fft`` - mod2f (Sec. 3.3): the DFT of Eq. 1 term by term, and
+  the radix-2 decimation-in-frequency recursion of Eqs. 2-3.
 """
 from __future__ import annotations
 
@@ -108,6 +110,10 @@ def _load():
         f.restype = I
     lib.oracle_cg.argtypes = [P, P, P, P, P, I64, I64, ctypes.c_double, I64, P, P, P]
     lib.oracle_cg.restype = I
+    lib.oracle_dft.argtypes = [P, P, I64]
+    lib.oracle_dft.restype = None
+    lib.oracle_fft_dif.argtypes = [P, P, I64]
+    lib.oracle_fft_dif.restype = I
     _lib = lib
     return lib
 
@@ -303,6 +309,29 @@ def cg(rowp, indx, vals, b, stop, max_iters):
         raise ValueError("oracle_cg: invalid CSR structure")
     return {"x": x, "iters": it.value, "r2": r2.value, "hist": hist[:it.value].copy(),
             "breakdown": st == CG_BREAKDOWN}
+
+
+def _complex_io(f):
+    f = np.ascontiguousarray(f, dtype=np.complex128)
+    if f.ndim != 1:
+        raise ValueError("1-D data expected")
+    return f, np.empty_like(f)
+
+
+def dft(f):
+    """F(k) = sum_n f(n) exp(-2 pi i k n / N), term by term (Eq. 1)."""
+    f, F = _complex_io(f)
+    _load().oracle_dft(_ptr(f), _ptr(F), f.shape[0])
+    return F
+
+
+def fft(f):
+    """The same transform by the radix-2 DIF recursion (Eqs. 2-3); N a
+    power of two."""
+    f, F = _complex_io(f)
+    if _load().oracle_fft_dif(_ptr(f), _ptr(F), f.shape[0]) != 0:
+        raise ValueError("fft: N must be a power of two")
+    return F
 
 
 if __name__ == "__main__":  # pragma: no cover

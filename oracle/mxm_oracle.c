@@ -40,8 +40,15 @@
  *   oracle_cg           conjugate gradients (Sec. 3.4, Fig. 6) for an SPD
  *                       matrix in the same CSR form, steps in the paper's
  *                       order, dot products summed in index order.
+ *   oracle_dft          mod2f (Sec. 3.3): the DFT of Eq. 1 term by term.
+ *   oracle_fft_dif      the radix-2 decimation-in-frequency recursion of
+ *                       Eqs. 2-3, level by level, bit-reversed read-out.
  */
+#define _USE_MATH_DEFINES
 #include <math.h>
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -540,4 +547,79 @@ int oracle_cg(const double* vals, const int32_t* indx, const int32_t* rowp, cons
   free(p);
   free(q);
   return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* mod2f (Sec. 3.3): the 1-D complex DFT of Eq. 1,                       */
+/*   F(k) = sum_{n=0}^{N-1} f(n) exp(-2 pi i k n / N),                   */
+/* for complex FP64 data stored interleaved (re, im) per point.          */
+/* Twiddle W_N^m = exp(-2 pi i m / N) = cos(2 pi m / N) - i sin(2 pi m / */
+/* N), with m reduced mod N first (so the angle is in [0, 2 pi)).        */
+/* Complex products (a + bi)(c + di) = (ac - bd) + (ad + bc) i, each     */
+/* product and sum rounded separately.                                   */
+static void twiddle(int64_t m, int64_t N, double* c, double* s) {
+  const double ang = 2.0 * M_PI * (double)(m % N) / (double)N;
+  *c = cos(ang);
+  *s = -sin(ang);
+}
+
+/* The definition (Eq. 1) term by term, n in order: O(N^2). */
+void oracle_dft(const double* f, double* F, int64_t N) {
+  int64_t k;
+#pragma omp parallel for schedule(static)
+  for (k = 0; k < N; ++k) {
+    double re = 0.0, im = 0.0;
+    for (int64_t n = 0; n < N; ++n) {
+      double c, s;
+      twiddle((k * n) % N, N, &c, &s);
+      const double a = f[2 * n], b = f[2 * n + 1];
+      re = re + (a * c - b * s);
+      im = im + (a * s + b * c);
+    }
+    F[2 * k] = re;
+    F[2 * k + 1] = im;
+  }
+}
+
+/* Radix-2 decimation in frequency (Eqs. 2-3), applied level by level:  */
+/* a block of length L (a sub-transform) becomes its f_e (first half)   */
+/* and f_o (second half),                                               */
+/*   f_e(n) = f(n) + f(n + L/2),                                        */
+/*   f_o(n) = (f(n) - f(n + L/2)) W_L^n,       0 <= n < L/2,            */
+/* and both halves are transformed further.  After the last level the   */
+/* value at position p is F(bitrev(p)) (Eq. 2: the even frequencies come */
+/* from the first half, the odd from the second), so the result is read */
+/* out through the bit reversal.  N must be a power of two.             */
+int oracle_fft_dif(const double* f, double* F, int64_t N) {
+  if (N < 1 || (N & (N - 1)) != 0) return ORACLE_INVALID;
+  double* w = (double*)malloc(sizeof(double) * 2 * (size_t)N);
+  if (!w) return ORACLE_INVALID;
+  memcpy(w, f, sizeof(double) * 2 * (size_t)N);
+  for (int64_t L = N; L >= 2; L /= 2) {
+    const int64_t h = L / 2;
+    for (int64_t blk = 0; blk < N; blk += L) {
+      for (int64_t n = 0; n < h; ++n) {
+        double* x0 = w + 2 * (blk + n);
+        double* x1 = w + 2 * (blk + n + h);
+        const double ar = x0[0], ai = x0[1], br = x1[0], bi = x1[1];
+        double c, s;
+        twiddle(n, L, &c, &s);
+        const double dr = ar - br, di = ai - bi;
+        x0[0] = ar + br;
+        x0[1] = ai + bi;
+        x1[0] = dr * c - di * s;
+        x1[1] = dr * s + di * c;
+      }
+    }
+  }
+  int bits = 0;
+  while (((int64_t)1 << bits) < N) ++bits;
+  for (int64_t p = 0; p < N; ++p) {
+    int64_t r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((p >> b) & 1) << (bits - 1 - b);
+    F[2 * r] = w[2 * p];
+    F[2 * r + 1] = w[2 * p + 1];
+  }
+  free(w);
+  return ORACLE_OK;
 }

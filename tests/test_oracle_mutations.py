@@ -64,9 +64,20 @@ MUTANTS = {
                                   "if (indx[j] != i) t = t + vals[j] * p[indx[j]];"),
     "cg_stop_off_by_one": ("while (r2 > stop && k < max_iters) {",
                            "while (r2 > stop && k <= max_iters) {"),
+    # mod2f (Sec. 3.3); checked by tests/test_oracle_fft_pins.py
+    "fft_twiddle_sign": ("  *s = -sin(ang);", "  *s = sin(ang);"),
+    "fft_twiddle_index": ("        twiddle(n, L, &c, &s);", "        twiddle(n + 1, L, &c, &s);"),
+    "fft_difference_sign": ("const double dr = ar - br, di = ai - bi;",
+                            "const double dr = br - ar, di = bi - ai;"),
+    "fft_no_bit_reversal": ("    F[2 * r] = w[2 * p];\n    F[2 * r + 1] = w[2 * p + 1];",
+                            "    F[2 * p] = w[2 * p]; (void)r;\n    F[2 * p + 1] = w[2 * p + 1];"),
+    "fft_complex_product": ("x1[1] = dr * s + di * c;", "x1[1] = dr * s - di * c;"),
+    "dft_conjugated_term": ("im = im + (a * s + b * c);", "im = im + (a * s - b * c);"),
 }
 PINS = {name: "test_oracle_spmv_pins.py" for name in MUTANTS if name.startswith("spmv_")}
 PINS.update({name: "test_oracle_cg_pins.py" for name in MUTANTS if name.startswith("cg_")})
+PINS.update({name: "test_oracle_fft_pins.py" for name in MUTANTS
+             if name.startswith(("fft_", "dft_"))})
 
 
 def _compile(src_text, out_dir):
