@@ -49,15 +49,16 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-check", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
-    p.add_argument("--suite", nargs="?", const="all", choices=("all", "gemm", "spmv", "cg"),
+    p.add_argument("--suite", nargs="?", const="all",
+                   choices=("all", "gemm", "spmv", "cg", "fft"),
                    help="instead of the benchmark line: one JSON line per case of the "
                         "workload suite (FP64 sweep, slice counts and modes, rectangular "
                         "shapes, grouped batch under a CUDA graph; mod2as sparse products; "
-                        "conjugate-gradient solves)")
+                        "conjugate-gradient solves; mod2f transforms)")
     p.add_argument("--only", default="",
-                   help="with --suite spmv / cg: run only the rows whose key (case:n, or "
-                        "cg:n:bw) is this string or extends it by ':...', e.g. "
-                        "spmv_large:200000, cg:1024 or cg:1024:511")
+                   help="with --suite spmv / cg / fft: run only the rows whose key (case:n, "
+                        "cg:n:bw, fft:n) is this string or extends it by ':...', e.g. "
+                        "spmv_large:200000, cg:1024, cg:1024:511 or fft:1048576")
     return p.parse_args()
 
 
@@ -468,7 +469,9 @@ def run_suite(args):
         run_spmv_suite(emit, stream, peaks, args.only)
     if args.suite in ("all", "cg"):
         run_cg_suite(emit, stream, args.only)
-    if args.suite in ("spmv", "cg"):
+    if args.suite in ("all", "fft"):
+        run_fft_suite(emit, stream, args.only)
+    if args.suite in ("spmv", "cg", "fft"):
         return
     dmma = mxm.mxm_peak_probe(1)
 
@@ -664,6 +667,46 @@ def run_cg_suite(emit, stream, only=""):
                            "gflops": round(o["iters"] * (2.0 * nnz + 10.0 * n) / (cms * 1e-3) / 1e9, 3),
                            "cores": oracle.num_threads()}
         emit(**d)
+
+
+def run_fft_suite(emit, stream, only=""):
+    """mod2f (Sec. 3.3): the paper's orders 2^8 ... 2^20 and 2^22, complex
+    FP64.  Rate in the usual FFT convention, 5 N log2 N flops per transform;
+    FP64 instructions issued are about 4 N log2 N (8 per butterfly).  Data
+    of 2^20 points and more exceeds the 16 MB that stays in L2 only at
+    2^22 (64 MB); smaller orders run from L2 between repeated calls.  The
+    CPU line is the oracle's radix-2 recursion, timed on the host."""
+    import torch
+
+    import oracle
+    from paper_1211_1581_gb300 import inputs, mxm
+
+    for p in list(range(8, 21)) + [22]:
+        N = 1 << p
+        if not _selected(f"fft:{N}", only):
+            continue
+        u = inputs.uniform_pm1(0, 150 + p, (2 * N,))
+        f = u[0::2] + 1j * u[1::2]
+        plan = mxm.FFT(N, stream=stream)
+        x = torch.from_numpy(f).cuda()
+        out = torch.empty_like(x)
+        reps = 50 if N <= (1 << 16) else 10
+        ms = _timed_ms(lambda: plan(x, out=out, stream=stream), reps, stream)
+        st = mxm.mxm_get_device_status()
+        flops = 5.0 * N * p
+        d = {"case": "fft", "n": N, "ms": round(ms, 5), "gflops": round(flops / (ms * 1e-3) / 1e9, 2),
+             "passes": 1 if N <= 1024 else 2, "status": st}
+        t0 = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t0 < 0.2 or k < 2:
+            oracle.fft(f)
+            k += 1
+        cms = (time.perf_counter() - t0) / k * 1e3
+        d["cpu_oracle"] = {"ms": round(cms, 4), "gflops": round(flops / (cms * 1e-3) / 1e9, 3),
+                           "cores": 1}
+        emit(**d)
+        del plan, x, out
+        torch.cuda.empty_cache()
 
 
 def run_reference(args):

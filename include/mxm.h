@@ -264,6 +264,40 @@ mxm_status mxm_cg(const double* matvals, const int32_t* indx, const int32_t* row
 int64_t mxm_cg_max_n(void);
 
 /*
+ * mxm_fft -- the forward 1-D complex DFT of mod2f (Sec. 3.3, Eq. 1):
+ * out(k) = sum_{j<n} in(j) exp(-2 pi i k j / n), 0 <= k < n, computed by
+ * radix-2 decimation in frequency (Eqs. 2-3) in shared memory, in one pass
+ * (n <= 1024) or two passes through `work` (the four-step factorisation).
+ * Arguments (device memory; complex FP64 interleaved re, im; 16-byte
+ * aligned):
+ *   in      n complex values (read);
+ *   out     n complex values (written); may be `in` itself;
+ *   work    n complex values of scratch, apart from in and out (unused and
+ *           may be NULL when n <= 1024);
+ *   table   the twiddles W_T^j = exp(-2 pi i j / T), j < T / 2, written by
+ *           mxm_fft_twiddles(table, T) (T / 2 complex values); T a power
+ *           of two with n <= T (one table serves every smaller order);
+ *           unused when n == 1;
+ *   n       a power of two, 1 <= n <= mxm_fft_max_n().
+ * Asynchronous on `stream`; no allocation; graph-capturable.  Errors: n not
+ * a power of two or too large, T < n or not a power of two, NULL or
+ * overlapping arrays: MXM_ERR_INVALID_ARG; misalignment: MXM_ERR_ALIGNMENT;
+ * a failed launch: MXM_ERR_CUDA.  Accuracy: within the radix-2 bound
+ * ||F' - F|| / ||F|| <= (log2 n + 1) eta / (1 - (log2 n + 1) eta),
+ * eta = mu + gamma_4 (sqrt 2 + mu), mu the table's error (about u).
+ */
+mxm_status mxm_fft(const double* in, double* out, double* work, const double* table,
+                   int64_t table_n, int64_t n, void* stream);
+
+/* mxm_fft_twiddles -- write the table of mxm_fft for order T (a power of
+ * two, T <= mxm_fft_max_n()): T / 2 complex values W_T^j, j < T / 2, from
+ * sincospi.  Asynchronous on `stream`; nothing is written for T = 1. */
+mxm_status mxm_fft_twiddles(double* table, int64_t n, void* stream);
+
+/* mxm_fft_max_n -- the largest order mxm_fft accepts (2^22). */
+int64_t mxm_fft_max_n(void);
+
+/*
  * mxm_f64_emul_noalloc -- mxm_f64_emul (7-bit digits, `slices` slices) for
  * callers that cannot allocate device memory, e.g. code inside a process
  * whose allocator owns the device, loops that must never reach the driver's

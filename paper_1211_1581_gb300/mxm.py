@@ -57,6 +57,9 @@ SIGNATURES = {
     "mxm_cg": (_I, [_P, _P, _P, _P, _P, _I64, _I64, ctypes.c_double, ctypes.c_int32, _P, _P, _P,
                     _P]),
     "mxm_cg_max_n": (_I64, []),
+    "mxm_fft": (_I, [_P, _P, _P, _P, _I64, _I64, _P]),
+    "mxm_fft_twiddles": (_I, [_P, _I64, _P]),
+    "mxm_fft_max_n": (_I64, []),
 }
 
 _lib = None
@@ -300,3 +303,34 @@ def mxm_cg(matvals, indx, rowp, b, x, stop, max_iters, iters=None, r2=None, r2_h
                          r2_hist.data_ptr() if r2_hist is not None else None,
                          _stream_ptr(stream)), "mxm_cg")
     return iters, r2
+
+
+class FFT:
+    """The mod2f transform (Sec. 3.3) of order n on the current CUDA device:
+    owns the twiddle table (mxm_fft_twiddles, written once) and the work
+    array; ``fft(x, out=None)`` runs mxm_fft on a complex128 CUDA tensor of
+    n values (``out`` may be ``x``)."""
+
+    def __init__(self, n, stream=None):
+        import torch
+        if n < 1 or n & (n - 1):
+            raise ValueError("n must be a power of two")
+        self.n = n
+        self.table = torch.empty(max(n // 2, 1) * 2, dtype=torch.float64, device="cuda")
+        self.work = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+        _check(load().mxm_fft_twiddles(self.table.data_ptr(), n, _stream_ptr(stream)),
+               "mxm_fft_twiddles")
+
+    def __call__(self, x, out=None, stream=None):
+        import torch
+        if not isinstance(x, torch.Tensor) or x.dtype != torch.complex128 or not x.is_cuda:
+            raise TypeError("x must be a CUDA complex128 tensor")
+        if x.dim() != 1 or x.shape[0] != self.n or not x.is_contiguous():
+            raise ValueError(f"x must be a contiguous tensor of {self.n} values")
+        out = torch.empty_like(x) if out is None else out
+        if out.dtype != torch.complex128 or out.shape != x.shape or not out.is_contiguous():
+            raise ValueError("out must match x")
+        _check(load().mxm_fft(x.data_ptr(), out.data_ptr(), self.work.data_ptr(),
+                              self.table.data_ptr(), self.n, self.n, _stream_ptr(stream)),
+               "mxm_fft")
+        return out

@@ -170,3 +170,24 @@ def test_cg_argument_errors_on_host():
     assert call(xx=P(0x40000 + 8)) == mxm.MXM_ERR_INVALID_ARG    # x overlaps b
     assert call(xx=f) == mxm.MXM_ERR_INVALID_ARG                 # x aliases the values
     assert mxm.load().mxm_status_string(mxm.MXM_ERR_BREAKDOWN) == b"MXM_ERR_BREAKDOWN"
+
+
+def test_fft_argument_errors_on_host():
+    lib = mxm.load()
+    P = ctypes.c_void_p
+    a, w, t = P(0x100000), P(0x200000), P(0x300000)
+    assert lib.mxm_fft_max_n() == 1 << 22
+    assert lib.mxm_fft(a, a, w, t, 64, 48, None) == mxm.MXM_ERR_INVALID_ARG      # not 2^p
+    assert lib.mxm_fft(a, a, w, t, 64, 0, None) == mxm.MXM_ERR_INVALID_ARG
+    assert lib.mxm_fft(a, a, w, t, 32, 64, None) == mxm.MXM_ERR_INVALID_ARG      # table too small
+    assert lib.mxm_fft(a, a, w, t, 96, 64, None) == mxm.MXM_ERR_INVALID_ARG      # table not 2^p
+    assert lib.mxm_fft(a, a, w, None, 64, 64, None) == mxm.MXM_ERR_INVALID_ARG
+    assert lib.mxm_fft(None, a, w, t, 64, 64, None) == mxm.MXM_ERR_INVALID_ARG
+    assert lib.mxm_fft(a, a, None, t, 4096, 4096, None) == mxm.MXM_ERR_INVALID_ARG  # two passes
+    assert lib.mxm_fft(a, a, P(0x100000 + 4096 * 8), t, 4096, 4096, None) == \
+        mxm.MXM_ERR_INVALID_ARG                                                     # work overlaps
+    assert lib.mxm_fft(P(0x100008), P(0x100008), w, t, 64, 64, None) == mxm.MXM_ERR_ALIGNMENT
+    assert lib.mxm_fft(a, P(0x100000 + 16), w, t, 64, 64, None) == mxm.MXM_ERR_INVALID_ARG
+    assert lib.mxm_fft_twiddles(t, 48, None) == mxm.MXM_ERR_INVALID_ARG
+    assert lib.mxm_fft_twiddles(t, 1, None) == mxm.MXM_OK
+    assert lib.mxm_fft_twiddles(P(0x300008), 64, None) == mxm.MXM_ERR_ALIGNMENT
