@@ -19,11 +19,12 @@
 //
 // A CTA takes C neighbouring columns, so every global access moves C
 // consecutive complex values.  Small transforms (N <= 1024) are one pass of
-// one CTA.  FP64 is scarce on this GPU (~0.6 G fused multiply-adds per
-// second per SM): a butterfly costs 8 FP64 operations, 4 in the two last
-// stages, whose twiddles are 1 and -i.  Twiddles come from a caller-owned
-// table of W_T^j, j < T/2, for a power of two T that N divides (one table
-// serves every smaller order), copied per CTA into shared memory.
+// one CTA.  FP64 is scarce on this GPU (~4 G fused multiply-adds per second
+// per SM): the stages go two at a time (radix 4, 28 FP64 operations per 4
+// points and 2 stages against 32 for radix 2; none in the last, whose
+// twiddles are 1 and -i).  Twiddles come from a caller-owned table of
+// W_T^j, j < T/2, for a power of two T that N divides (one table serves
+// every smaller order), expanded per CTA into shared memory.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -90,13 +91,13 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPass a) 
   int lbits = 0;
   while ((int64_t{1} << lbits) < L) ++lbits;
   double2* data = sm;             // [C][L]
-  double2* tw = sm + C * L;       // W_L^m, m < L/2
+  double2* tw = sm + C * L;       // W_L^m, m < L
   const int64_t c0 = static_cast<int64_t>(blockIdx.x) * C;
   const int tid = threadIdx.x;
 
   // twiddles of the L-point transform: W_L^m = W_T^{m T / L}
   const int64_t tstride = a.T / (L > 0 ? L : 1);
-  for (int64_t m = tid; m < L / 2; m += kFftThreads) tw[m] = __ldg(a.table + m * tstride);
+  for (int64_t m = tid; m < L; m += kFftThreads) tw[m] = table_w(a.table, a.T, m * tstride);
   // load: C consecutive columns per row, c fastest
   for (int64_t t = tid; t < L * C; t += kFftThreads) {
     const int64_t r = t / C, c = t - r * C;
@@ -107,24 +108,48 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPass a) 
   }
   __syncthreads();
 
-  // decimation-in-frequency stages, half = L/2 ... 1
-  for (int64_t half = L >> 1; half >= 1; half >>= 1) {
-    const int64_t tw_step = L / (2 * half);  // W_{2 half}^j = W_L^{j L / (2 half)}
-    for (int64_t t = tid; t < C * (L >> 1); t += kFftThreads) {
-      const int64_t c = t / (L >> 1), u = t - c * (L >> 1);
-      const int64_t grp = u / half, j = u - grp * half;
-      double2* p0 = data + c * L + grp * 2 * half + j;
-      double2* p1 = p0 + half;
-      const double2 x0 = *p0, x1 = *p1;
-      *p0 = cadd(x0, x1);
-      const double2 d = csub(x0, x1);
-      if (half == 1) {
-        *p1 = d;  // W_2^0 = 1
-      } else if (half == 2) {
-        *p1 = j == 0 ? d : make_double2(d.y, -d.x);  // W_4^1 = -i
+  // decimation-in-frequency stages two at a time (radix 4): a block of
+  // length B = 4q with a_m = x(j + m q), W = W_B, j < q, becomes
+  //   x(j)      = (a0 + a2) + (a1 + a3)
+  //   x(j + q)  = ((a0 + a2) - (a1 + a3)) W^{2j}
+  //   x(j + 2q) = ((a0 - a2) - i (a1 - a3)) W^j
+  //   x(j + 3q) = ((a0 - a2) + i (a1 - a3)) W^{3j}
+  // which is the two radix-2 stages of lengths B and B/2 (Eqs. 2-3) with
+  // W_B^{j + q} = -i W_B^j folded in: 3 complex products per 4 points
+  // instead of 4, and one barrier per two stages.  An odd stage count ends
+  // with the twiddle-free radix-2 stage of length 2.
+  int64_t B = L;
+  for (; B >= 4; B >>= 2) {
+    const int64_t q = B >> 2;
+    const int64_t ts = L / B;  // W_B^m = W_L^{m L / B}
+    for (int64_t t = tid; t < C * (L >> 2); t += kFftThreads) {
+      const int64_t c = t / (L >> 2), u = t - c * (L >> 2);
+      const int64_t grp = u / q, j = u - grp * q;
+      double2* p = data + c * L + grp * B + j;
+      const double2 a0 = p[0], a1 = p[q], a2 = p[2 * q], a3 = p[3 * q];
+      const double2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+      const double2 s13 = cadd(a1, a3), d13 = csub(a1, a3);
+      const double2 nd13 = make_double2(d13.y, -d13.x);  // -i (a1 - a3)
+      p[0] = cadd(s02, s13);
+      const double2 y1 = csub(s02, s13), y2 = cadd(d02, nd13), y3 = csub(d02, nd13);
+      if (q == 1) {  // j = 0: every twiddle is 1
+        p[q] = y1;
+        p[2 * q] = y2;
+        p[3 * q] = y3;
       } else {
-        *p1 = cmul(d, tw[j * tw_step]);
+        p[q] = cmul(y1, tw[2 * j * ts]);
+        p[2 * q] = cmul(y2, tw[j * ts]);
+        p[3 * q] = cmul(y3, tw[3 * j * ts]);
       }
+    }
+    __syncthreads();
+  }
+  if (B == 2) {  // the last stage, length 2: W_2^0 = 1
+    for (int64_t t = tid; t < C * (L >> 1); t += kFftThreads) {
+      double2* p = data + 2 * t;
+      const double2 x0 = p[0], x1 = p[1];
+      p[0] = cadd(x0, x1);
+      p[1] = csub(x0, x1);
     }
     __syncthreads();
   }
@@ -161,11 +186,10 @@ __global__ void fft_twiddle_kernel(double2* table, int64_t T) {
 bool pow2(int64_t v) { return v >= 1 && (v & (v - 1)) == 0; }
 
 // Columns per CTA: as many as keep at least two CTAs per SM, at most 8,
-// within 96 KiB of shared memory.
+// within 96 KiB of shared memory (C columns and the L twiddles).
 int fft_columns(int64_t L, int64_t cols) {
   int C = 8;
-  while (C > 1 && (cols / C < 2 * static_cast<int64_t>(sm_count()) ||
-                   (C * L + L / 2) * 16 > 96 * 1024))
+  while (C > 1 && (cols / C < 2 * static_cast<int64_t>(sm_count()) || (C * L + L) * 16 > 96 * 1024))
     C /= 2;
   return C;
 }
@@ -174,7 +198,7 @@ cudaError_t launch_pass(FftPass a, cudaStream_t s) {
   const int64_t L = a.stage == 1 ? a.N1 : a.N2;
   const int64_t cols = a.stage == 1 ? a.N2 : a.N1;
   a.C = fft_columns(L, cols);
-  const size_t smem = static_cast<size_t>(a.C * L + L / 2) * sizeof(double2);
+  const size_t smem = static_cast<size_t>(a.C * L + L) * sizeof(double2);
   cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
