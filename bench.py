@@ -624,10 +624,12 @@ def run_spmv_suite(emit, stream, peaks, only=""):
 
 def run_cg_suite(emit, stream, only=""):
     """Conjugate gradients (Sec. 3.4): the Table 2 orders and bandwidths,
-    plus the largest order the one-launch solver takes, each solved to
-    r2 <= 1e-24 (b, b).  Rate in the paper's terms: FP64 operations of the
-    steps taken (2 nnz + 10 n per step) over the solve time (one launch,
-    CUDA events).  The CPU line is the oracle's solve, timed on the host."""
+    the largest order of the cluster engine and a 10^6 order, each solved
+    to r2 <= 1e-24 (b, b) by each engine that takes it (the cluster engine:
+    one launch; the graph engine: one graph launch).  Rate in the paper's
+    terms: FP64 operations of the steps taken (2 nnz + 10 n per step) over
+    the solve time (CUDA events).  The CPU line is the oracle's solve,
+    timed on the host."""
     import numpy as np
     import torch
 
@@ -637,7 +639,7 @@ def run_cg_suite(emit, stream, only=""):
     def dev(a, dt):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dtype=dt).cuda()
 
-    for n, bw in inputs.CG_TABLE2 + [(12288, 63), (12288, 511)]:
+    for n, bw in inputs.CG_TABLE2 + [(12288, 63), (12288, 511), (1_000_000, 7)]:
         if not _selected(f"cg:{n}:{bw}", only):
             continue
         rowp, indx, vals = inputs.banded_spd(6, 91, n, bw)
@@ -648,15 +650,20 @@ def run_cg_suite(emit, stream, only=""):
         x = torch.empty(n, dtype=torch.float64, device="cuda")
         it = torch.zeros(1, dtype=torch.int32, device="cuda")
         r2 = torch.zeros(1, dtype=torch.float64, device="cuda")
-        ms = _timed_ms(lambda: mxm.mxm_cg(dv, di, dr, db, x, stop, 10 * n, it, r2,
-                                          stream=stream), 20, stream)
-        st = mxm.mxm_get_device_status()
-        k = int(it.item())
+        work = torch.empty((mxm.load().mxm_cg_workspace_size(n) + 7) // 8, dtype=torch.float64,
+                           device="cuda")
         nnz = len(vals)
-        flops = k * (2.0 * nnz + 10.0 * n)
-        d = {"case": "cg", "n": n, "bw": bw, "nnz": nnz, "iters": k, "ms": round(ms, 4),
-             "us_per_step": round(ms * 1e3 / max(k, 1), 2),
-             "gflops": round(flops / (ms * 1e-3) / 1e9, 3), "status": st}
+        d = {"case": "cg", "n": n, "bw": bw, "nnz": nnz}
+        engines = [("cluster", mxm.CG_CLUSTER)] if n <= mxm.load().mxm_cg_max_n() else []
+        engines.append(("graph", mxm.CG_GRAPH))
+        for name, eng in engines:
+            ms = _timed_ms(lambda: mxm.mxm_cg(dv, di, dr, db, x, stop, 10 * n, it, r2,
+                                              stream=stream, engine=eng, work=work), 20, stream)
+            k = int(it.item())
+            flops = k * (2.0 * nnz + 10.0 * n)
+            d[name] = {"iters": k, "ms": round(ms, 4), "us_per_step": round(ms * 1e3 / max(k, 1), 2),
+                       "gflops": round(flops / (ms * 1e-3) / 1e9, 3),
+                       "status": mxm.mxm_get_device_status()}
         t0 = time.perf_counter()
         reps = 0
         while time.perf_counter() - t0 < 0.2 or reps < 2:
@@ -667,6 +674,8 @@ def run_cg_suite(emit, stream, only=""):
                            "gflops": round(o["iters"] * (2.0 * nnz + 10.0 * n) / (cms * 1e-3) / 1e9, 3),
                            "cores": oracle.num_threads()}
         emit(**d)
+        del dv, di, dr, db, x, work
+        torch.cuda.empty_cache()
 
 
 def run_fft_suite(emit, stream, only=""):

@@ -224,6 +224,15 @@ mxm_status mxm_spmv(const double* matvals, const int32_t* indx, const int32_t* r
                     const double* x, double* y, int64_t nrows, int64_t ncols, int64_t nnz,
                     void* stream);
 
+/* Engines of mxm_cg. */
+enum {
+  MXM_CG_AUTO = 0,     /* the cluster engine for n <= mxm_cg_max_n() and small nnz
+                          (or when work is NULL), else the graph engine */
+  MXM_CG_CLUSTER = 1,  /* one launch on a thread-block cluster of up to 16 CTAs */
+  MXM_CG_GRAPH = 2     /* a CUDA graph: the loop is a conditional WHILE node over three
+                          kernels on all SMs; needs `work`; not inside a stream capture */
+};
+
 /*
  * mxm_cg -- conjugate gradients for A x = b (Sec. 3.4, the textbook
  * iteration of Fig. 6 and the ArBB loop beside it), A an n x n symmetric
@@ -232,35 +241,42 @@ mxm_status mxm_spmv(const double* matvals, const int32_t* indx, const int32_t* r
  * max_iters steps were taken: q = A p; alpha = r2 / (p, q); r -= alpha q;
  * r2_new = (r, r); beta = r2_new / r2; x += alpha p; p = r + beta p.
  *
- * The whole solve is one launch on `stream` (a thread-block cluster of up
- * to 16 CTAs, the loop test on the device: no host round trip per step).
- * Arguments, all device memory, FP64 / int32, unaliased:
+ * The loop test runs on the device in both engines: no host round trip per
+ * step.  Arguments, all device memory, FP64 / int32, unaliased:
  *   matvals, indx, rowp   A in CSR (nnz values, nnz columns, n + 1 row
  *                         pointers; columns in [0, n));
  *   b                     the right-hand side, n doubles (read only);
- *   x                     the solution, n doubles (written once, after the
- *                         last step; r, q and x live in shared memory);
+ *   x                     the solution, n doubles (written);
+ *   engine                MXM_CG_AUTO, MXM_CG_CLUSTER or MXM_CG_GRAPH;
+ *   work                  mxm_cg_workspace_size(n) bytes of scratch for the
+ *                         graph engine (may be NULL for the cluster engine);
  *   iters                 one int32: the number of steps taken;
  *   r2                    one double: the last (r, r) (the recursive
  *                         residual, as the paper's loop test uses it);
  *   r2_hist               NULL, or max_iters doubles: r2 after each step.
  * Results: x after the last step.  The dot products are deterministic (the
- * same result on every run for the same n and nnz).  A step with
- * (p, A p) <= 0 is not taken: the loop ends and MXM_ERR_BREAKDOWN is
- * recorded in the device status word.  Bad structure (a row pointer or
- * column outside the arrays) is skipped and recorded as
+ * same result on every run for the same n, nnz and engine, on any device).
+ * A step with (p, A p) <= 0 is not taken: the loop ends and
+ * MXM_ERR_BREAKDOWN is recorded in the device status word.  Bad structure (a
+ * row pointer or column outside the arrays) is skipped and recorded as
  * MXM_ERR_INVALID_ARG in the device status word; x is then unspecified.
- * Host-side errors: n <= 0, max_iters < 0, NULL arrays, x overlapping an input:
- * MXM_ERR_INVALID_ARG; n > mxm_cg_max_n() or nnz > INT32_MAX:
- * MXM_ERR_UNSUPPORTED; misaligned pointers: MXM_ERR_ALIGNMENT; a failed
- * launch: MXM_ERR_CUDA.
+ * Host-side errors: n <= 0, max_iters < 0, an unknown engine, NULL or
+ * overlapping arrays, the graph engine without work: MXM_ERR_INVALID_ARG;
+ * the cluster engine with n > mxm_cg_max_n(), n or nnz > INT32_MAX, the graph
+ * engine inside a stream capture: MXM_ERR_UNSUPPORTED; misaligned
+ * pointers: MXM_ERR_ALIGNMENT; a failed launch: MXM_ERR_CUDA.
  */
 mxm_status mxm_cg(const double* matvals, const int32_t* indx, const int32_t* rowp,
                   const double* b, double* x, int64_t n, int64_t nnz, double stop,
-                  int32_t max_iters, int32_t* iters, double* r2, double* r2_hist, void* stream);
+                  int32_t max_iters, int32_t engine, double* work, int32_t* iters, double* r2,
+                  double* r2_hist, void* stream);
 
-/* mxm_cg_max_n -- the largest n mxm_cg accepts (p is held twice in the
- * shared memory of every CTA). */
+/* mxm_cg_workspace_size -- bytes of `work` the graph engine needs for order n
+ * (r, p, q and the blocks' shares of the dot products). */
+size_t mxm_cg_workspace_size(int64_t n);
+
+/* mxm_cg_max_n -- the largest n the cluster engine accepts (p is held twice
+ * in the shared memory of every CTA). */
 int64_t mxm_cg_max_n(void);
 
 /*

@@ -43,6 +43,11 @@
 namespace mxm {
 
 int* device_status_word();  // abi.cu
+size_t cg_graph_workspace_bytes(int64_t n);  // cg_graph.cu
+mxm_status cg_graph_solve(const double* vals, const int32_t* indx, const int32_t* rowp,
+                          const double* b, double* x, double* work, int32_t* iters, double* r2,
+                          double* r2_hist, int64_t n, int64_t nnz, double stop,
+                          int32_t max_iters, int* status, cudaStream_t s);
 
 namespace {
 
@@ -372,35 +377,61 @@ using namespace mxm;
 
 extern "C" int64_t mxm_cg_max_n(void) { return kCgMaxN; }
 
+extern "C" size_t mxm_cg_workspace_size(int64_t n) {
+  return n > 0 ? cg_graph_workspace_bytes(n) : 0;
+}
+
+// Matrices whose product has more values than this go to the graph engine
+// by default: one cluster's 16 SMs then spend longer on the FP64 work of a
+// step than the graph engine's three launches over all SMs cost.
+constexpr int64_t kCgClusterMaxNnz = 524288;
+
 extern "C" mxm_status mxm_cg(const double* matvals, const int32_t* indx, const int32_t* rowp,
                              const double* b, double* x, int64_t n, int64_t nnz, double stop,
-                             int32_t max_iters, int32_t* iters, double* r2,
-                             double* r2_hist, void* stream) {
+                             int32_t max_iters, int32_t engine, double* work, int32_t* iters,
+                             double* r2, double* r2_hist, void* stream) {
   if (n < 0 || nnz < 0 || max_iters < 0) return MXM_ERR_INVALID_ARG;
   if (n == 0) return MXM_ERR_INVALID_ARG;
-  if (n > kCgMaxN || nnz > INT32_MAX) return MXM_ERR_UNSUPPORTED;
+  if (engine != MXM_CG_AUTO && engine != MXM_CG_CLUSTER && engine != MXM_CG_GRAPH)
+    return MXM_ERR_INVALID_ARG;
+  if (nnz > INT32_MAX || n > INT32_MAX) return MXM_ERR_UNSUPPORTED;
+  if (engine == MXM_CG_AUTO)
+    engine = (n <= kCgMaxN && (nnz <= kCgClusterMaxNnz || work == nullptr)) ? MXM_CG_CLUSTER
+                                                                           : MXM_CG_GRAPH;
+  if (engine == MXM_CG_CLUSTER && n > kCgMaxN) return MXM_ERR_UNSUPPORTED;
   if (rowp == nullptr || b == nullptr || x == nullptr || iters == nullptr ||
-      r2 == nullptr || (nnz > 0 && (matvals == nullptr || indx == nullptr)))
+      r2 == nullptr || (nnz > 0 && (matvals == nullptr || indx == nullptr)) ||
+      (engine == MXM_CG_GRAPH && work == nullptr))
     return MXM_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(matvals) | reinterpret_cast<uintptr_t>(b) |
-       reinterpret_cast<uintptr_t>(x) |
+       reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(work) |
        reinterpret_cast<uintptr_t>(r2) | reinterpret_cast<uintptr_t>(r2_hist)) & 7 ||
       (reinterpret_cast<uintptr_t>(indx) | reinterpret_cast<uintptr_t>(rowp) |
        reinterpret_cast<uintptr_t>(iters)) & 3)
     return MXM_ERR_ALIGNMENT;
-  // x is written only after the loop, but it must not alias what the loop reads
+  // x and the workspace must not alias what the loop reads, nor each other
   const auto overlap = [](const void* p, size_t pb, const void* q, size_t qb) {
     const auto a0 = reinterpret_cast<uintptr_t>(p), b0 = reinterpret_cast<uintptr_t>(q);
     return a0 < b0 + qb && b0 < a0 + pb;
   };
   const size_t vb = static_cast<size_t>(n) * sizeof(double);
-  if (overlap(x, vb, b, vb) ||
-      (nnz > 0 && (overlap(x, vb, matvals, nnz * sizeof(double)) ||
-                   overlap(x, vb, indx, nnz * sizeof(int32_t)))) ||
-      overlap(x, vb, rowp, static_cast<size_t>(n + 1) * sizeof(int32_t)))
-    return MXM_ERR_INVALID_ARG;
+  const size_t wb = engine == MXM_CG_GRAPH ? cg_graph_workspace_bytes(n) : 0;
+  const void* outs[2] = {x, work};
+  const size_t outb[2] = {vb, wb};
+  for (int o = 0; o < 2; ++o) {
+    if (outs[o] == nullptr || outb[o] == 0) continue;
+    if (overlap(outs[o], outb[o], b, vb) ||
+        (nnz > 0 && (overlap(outs[o], outb[o], matvals, nnz * sizeof(double)) ||
+                     overlap(outs[o], outb[o], indx, nnz * sizeof(int32_t)))) ||
+        overlap(outs[o], outb[o], rowp, static_cast<size_t>(n + 1) * sizeof(int32_t)))
+      return MXM_ERR_INVALID_ARG;
+  }
+  if (wb > 0 && overlap(x, vb, work, wb)) return MXM_ERR_INVALID_ARG;
   int* status = device_status_word();
   if (status == nullptr) return MXM_ERR_CUDA;
+  if (engine == MXM_CG_GRAPH)
+    return cg_graph_solve(matvals, indx, rowp, b, x, work, iters, r2, r2_hist, n, nnz, stop,
+                          max_iters, status, static_cast<cudaStream_t>(stream));
   CgArgs a;
   a.vals = matvals;
   a.indx = indx;

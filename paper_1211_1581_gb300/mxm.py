@@ -23,6 +23,7 @@ MXM_ERR_CUDA = 6
 MXM_ERR_NO_WORKSPACE = 7
 MXM_ERR_WORKSPACE_TOO_SMALL = 8
 MXM_ERR_BREAKDOWN = 9
+CG_AUTO, CG_CLUSTER, CG_GRAPH = 0, 1, 2
 
 MODE_F64 = 0
 MODE_EMUL_I8 = 1
@@ -54,9 +55,10 @@ SIGNATURES = {
     "mxm_profile_read": (_I, [ctypes.POINTER(ctypes.c_double), _I, ctypes.POINTER(_I64)]),
     "mxm_f64_emul_noalloc": (_I, [_P, _P, _P, _I64, _I64, _I64, _I, _P]),
     "mxm_spmv": (_I, [_P, _P, _P, _P, _P, _I64, _I64, _I64, _P]),
-    "mxm_cg": (_I, [_P, _P, _P, _P, _P, _I64, _I64, ctypes.c_double, ctypes.c_int32, _P, _P, _P,
-                    _P]),
+    "mxm_cg": (_I, [_P, _P, _P, _P, _P, _I64, _I64, ctypes.c_double, ctypes.c_int32,
+                    ctypes.c_int32, _P, _P, _P, _P, _P]),
     "mxm_cg_max_n": (_I64, []),
+    "mxm_cg_workspace_size": (_SZ, [_I64]),
     "mxm_fft": (_I, [_P, _P, _P, _P, _I64, _I64, _P]),
     "mxm_fft_twiddles": (_I, [_P, _I64, _P]),
     "mxm_fft_max_n": (_I64, []),
@@ -273,11 +275,12 @@ def mxm_spmv(matvals, indx, rowp, x, y, stream=None):
 
 
 def mxm_cg(matvals, indx, rowp, b, x, stop, max_iters, iters=None, r2=None, r2_hist=None,
-           stream=None):
+           stream=None, engine=CG_AUTO, work=None):
     """Conjugate gradients for A x = b (Sec. 3.4), A SPD in CSR (CUDA
     tensors: matvals float64, indx and rowp int32, b and x float64), the
-    whole solve in one launch on ``stream``.  ``iters`` (int32[1]) and
-    ``r2`` (float64[1]) are allocated when not given;
+    loop on the device (``engine``: CG_AUTO, CG_CLUSTER or CG_GRAPH).
+    ``iters`` (int32[1]), ``r2`` (float64[1]) and, for the graph engine,
+    ``work`` (mxm_cg_workspace_size(n) bytes) are allocated when not given;
     ``r2_hist`` (float64[max_iters]) is optional.  Returns (iters, r2) as
     device tensors; read them after the stream (and check
     mxm_get_device_status for MXM_ERR_BREAKDOWN)."""
@@ -295,10 +298,14 @@ def mxm_cg(matvals, indx, rowp, b, x, stop, max_iters, iters=None, r2=None, r2_h
     dev = b.device
     iters = torch.zeros(1, dtype=torch.int32, device=dev) if iters is None else iters
     r2 = torch.zeros(1, dtype=torch.float64, device=dev) if r2 is None else r2
+    if work is None and engine != CG_CLUSTER:
+        nbytes = load().mxm_cg_workspace_size(n)
+        work = torch.empty((nbytes + 7) // 8, dtype=torch.float64, device=dev)
     if r2_hist is not None and (r2_hist.dtype != torch.float64 or r2_hist.numel() < max_iters):
         raise ValueError("r2_hist must be a float64 tensor of max_iters entries")
     _check(load().mxm_cg(matvals.data_ptr(), indx.data_ptr(), rowp.data_ptr(), b.data_ptr(),
                          x.data_ptr(), n, matvals.shape[0], float(stop), int(max_iters),
+                         int(engine), work.data_ptr() if work is not None else None,
                          iters.data_ptr(), r2.data_ptr(),
                          r2_hist.data_ptr() if r2_hist is not None else None,
                          _stream_ptr(stream)), "mxm_cg")

@@ -153,22 +153,30 @@ def test_cg_argument_errors_on_host():
     b = P(0x40000)
     it = P(0x50000)
     r2 = P(0x60000)
+    w = P(0x1000000)
 
     def call(n=8, nnz=8, vals=f, indx=P(0x70000), rowp=P(0x80000), bb=b, xx=x, iters=it, rr=r2,
-             hist=None, max_iters=5):
-        return lib.mxm_cg(vals, indx, rowp, bb, xx, n, nnz, 0.0, max_iters, iters, rr, hist, None)
+             hist=None, max_iters=5, engine=mxm.CG_CLUSTER, work=None):
+        return lib.mxm_cg(vals, indx, rowp, bb, xx, n, nnz, 0.0, max_iters, engine, work, iters,
+                          rr, hist, None)
 
     assert lib.mxm_cg_max_n() >= 1024
+    assert lib.mxm_cg_workspace_size(1000) >= 3 * 1000 * 8 and lib.mxm_cg_workspace_size(0) == 0
     assert call(n=0) == mxm.MXM_ERR_INVALID_ARG
     assert call(n=-1) == mxm.MXM_ERR_INVALID_ARG
     assert call(max_iters=-1) == mxm.MXM_ERR_INVALID_ARG
+    assert call(engine=3) == mxm.MXM_ERR_INVALID_ARG
     assert call(n=lib.mxm_cg_max_n() + 1) == mxm.MXM_ERR_UNSUPPORTED
+    assert call(engine=mxm.CG_GRAPH) == mxm.MXM_ERR_INVALID_ARG               # no work
     assert call(iters=None) == mxm.MXM_ERR_INVALID_ARG
     assert call(rr=None) == mxm.MXM_ERR_INVALID_ARG
     assert call(xx=P(0x30004)) == mxm.MXM_ERR_ALIGNMENT
     assert call(iters=P(0x50002)) == mxm.MXM_ERR_ALIGNMENT
+    assert call(engine=mxm.CG_GRAPH, work=P(0x1000004)) == mxm.MXM_ERR_ALIGNMENT
     assert call(xx=P(0x40000 + 8)) == mxm.MXM_ERR_INVALID_ARG    # x overlaps b
     assert call(xx=f) == mxm.MXM_ERR_INVALID_ARG                 # x aliases the values
+    assert call(engine=mxm.CG_GRAPH, work=P(0x30000)) == mxm.MXM_ERR_INVALID_ARG  # work on x
+    assert call(engine=mxm.CG_GRAPH, work=P(0x40000)) == mxm.MXM_ERR_INVALID_ARG  # work on b
     assert mxm.load().mxm_status_string(mxm.MXM_ERR_BREAKDOWN) == b"MXM_ERR_BREAKDOWN"
 
 

@@ -28,12 +28,12 @@ def dev(a, dt):
     return torch.from_numpy(np.ascontiguousarray(a)).to(dtype=dt).cuda()
 
 
-def run_cg(rowp, indx, vals, b, stop, max_iters, expect=mxm.MXM_OK):
+def run_cg(rowp, indx, vals, b, stop, max_iters, expect=mxm.MXM_OK, engine=mxm.CG_CLUSTER):
     n = len(rowp) - 1
     x = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
     hist = torch.full((max(max_iters, 1),), float("nan"), dtype=torch.float64, device="cuda")
     it, r2 = mxm.mxm_cg(dev(vals, torch.float64), dev(indx, torch.int32), dev(rowp, torch.int32),
-                        dev(b, torch.float64), x, stop, max_iters, r2_hist=hist)
+                        dev(b, torch.float64), x, stop, max_iters, r2_hist=hist, engine=engine)
     torch.cuda.synchronize()
     assert mxm.mxm_get_device_status() == expect
     k = int(it.item())
@@ -44,24 +44,25 @@ def run_cg(rowp, indx, vals, b, stop, max_iters, expect=mxm.MXM_OK):
 def gershgorin(rowp, indx, vals):
     """(lower, upper) Gershgorin bounds of the spectrum."""
     n = len(rowp) - 1
-    hi, lo = 0.0, np.inf
-    for i in range(n):
-        seg = slice(rowp[i], rowp[i + 1])
-        d = vals[seg][indx[seg] == i].sum()
-        off = np.abs(vals[seg][indx[seg] != i]).sum()
-        hi, lo = max(hi, d + off), min(lo, d - off)
-    return lo, hi
+    rows = np.repeat(np.arange(n), np.diff(rowp))
+    diag = np.zeros(n)
+    np.add.at(diag, rows[indx == rows], vals[indx == rows])
+    off = np.zeros(n)
+    np.add.at(off, rows[indx != rows], np.abs(vals[indx != rows]))
+    return float((diag - off).min()), float((diag + off).max())
 
 
 def csr_times(rowp, indx, vals, x):
-    return np.array([vals[rowp[i]:rowp[i + 1]] @ x[indx[rowp[i]:rowp[i + 1]]]
-                     for i in range(len(rowp) - 1)])
+    rows = np.repeat(np.arange(len(rowp) - 1), np.diff(rowp))
+    y = np.zeros(len(rowp) - 1)
+    np.add.at(y, rows, vals * x[indx])
+    return y
 
 
-def compare(rowp, indx, vals, b, stop, max_iters, bw):
+def compare(rowp, indx, vals, b, stop, max_iters, bw, engine=mxm.CG_CLUSTER):
     n = len(rowp) - 1
     want = oracle.cg(rowp, indx, vals, b, stop, max_iters)
-    got = run_cg(rowp, indx, vals, b, stop, max_iters)
+    got = run_cg(rowp, indx, vals, b, stop, max_iters, engine=engine)
     lo, hi = gershgorin(rowp, indx, vals)
     kap = hi / lo
     h = want["hist"]
@@ -93,17 +94,22 @@ def compare(rowp, indx, vals, b, stop, max_iters, bw):
     return got, want
 
 
+ENGINES = [mxm.CG_CLUSTER, mxm.CG_GRAPH]
+
+
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("n,bw", inputs.CG_TABLE2)
-def test_table2_against_oracle(n, bw):
+def test_table2_against_oracle(n, bw, engine):
     rowp, indx, vals = inputs.banded_spd(6, 91, n, bw)
     b = inputs.uniform_pm1(6, 92, (n,))
-    got, want = compare(rowp, indx, vals, b, 1e-24 * float(b @ b), 10 * n, bw)
+    got, want = compare(rowp, indx, vals, b, 1e-24 * float(b @ b), 10 * n, bw, engine)
     assert got["iters"] > 5
 
 
 @pytest.mark.parametrize("n,bw,shift,steps", [(1024, 31, 1e-3, 60), (512, 255, 1e-2, 20),
                                               (300, 7, 1e-4, 100)])
-def test_worse_conditioned(n, bw, shift, steps):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_worse_conditioned(n, bw, shift, steps, engine):
     """Off-diagonals made negative (a shifted graph Laplacian: the constant
     vector is nearly in the null space), so the smallest eigenvalue is close
     to the shift and the solve takes many steps."""
@@ -111,7 +117,7 @@ def test_worse_conditioned(n, bw, shift, steps):
     rows = np.repeat(np.arange(n), np.diff(rowp))
     vals = np.where(indx != rows, -np.abs(vals), vals)
     b = inputs.uniform_pm1(8, 94, (n,))
-    got, _ = compare(rowp, indx, vals, b, 1e-20 * float(b @ b), 10 * n, bw)
+    got, _ = compare(rowp, indx, vals, b, 1e-20 * float(b @ b), 10 * n, bw, engine)
     assert got["iters"] > steps
 
 
@@ -124,50 +130,95 @@ def test_sizes_and_cluster_shapes(n, bw):
     compare(rowp, indx, vals, b, 1e-22 * float(b @ b), 200, bw)
 
 
-def test_fixed_step_counts_and_edges():
+@pytest.mark.parametrize("engine", ENGINES)
+def test_fixed_step_counts_and_edges(engine):
     n, bw = 700, 31
     rowp, indx, vals = inputs.banded_spd(10, 97, n, bw)
     b = inputs.uniform_pm1(10, 98, (n,))
     for k in (1, 2, 5):
-        got, _ = compare(rowp, indx, vals, b, 0.0, k, bw)
+        got, _ = compare(rowp, indx, vals, b, 0.0, k, bw, engine)
         assert got["iters"] == k
     bb = float(b @ b)
-    got = run_cg(rowp, indx, vals, b, 0.0, 0)
+    got = run_cg(rowp, indx, vals, b, 0.0, 0, engine=engine)
     assert got["iters"] == 0 and np.array_equal(got["x"], np.zeros(n))
     assert got["r2"] == pytest.approx(bb, rel=n * U)
-    assert run_cg(rowp, indx, vals, b, 1.5 * bb, 50)["iters"] == 0
-    z = run_cg(rowp, indx, vals, np.zeros(n), 0.0, 50)
+    assert run_cg(rowp, indx, vals, b, 1.5 * bb, 50, engine=engine)["iters"] == 0
+    z = run_cg(rowp, indx, vals, np.zeros(n), 0.0, 50, engine=engine)
     assert z["iters"] == 0 and np.array_equal(z["x"], np.zeros(n))
 
 
-def test_identity_multiple_and_determinism():
+@pytest.mark.parametrize("engine", ENGINES)
+def test_identity_multiple_and_determinism(engine):
     n = 2049
     rowp = np.arange(n + 1, dtype=np.int32)
     indx = np.arange(n, dtype=np.int32)
     b = inputs.uniform_pm1(11, 99, (n,))
-    got = run_cg(rowp, indx, np.full(n, 4.0), b, 1e-20 * float(b @ b), 50)
+    got = run_cg(rowp, indx, np.full(n, 4.0), b, 1e-20 * float(b @ b), 50, engine=engine)
     assert got["iters"] == 1
     assert np.max(np.abs(got["x"] - b / 4.0)) <= 4 * n * U * np.max(np.abs(b))
     rowp, indx, vals = inputs.banded_spd(12, 100, 5000, 63)
     b = inputs.uniform_pm1(12, 101, (5000,))
-    a1 = run_cg(rowp, indx, vals, b, 1e-24 * float(b @ b), 500)
-    a2 = run_cg(rowp, indx, vals, b, 1e-24 * float(b @ b), 500)
+    a1 = run_cg(rowp, indx, vals, b, 1e-24 * float(b @ b), 500, engine=engine)
+    a2 = run_cg(rowp, indx, vals, b, 1e-24 * float(b @ b), 500, engine=engine)
     assert a1["iters"] == a2["iters"] and np.array_equal(a1["x"], a2["x"])
     assert np.array_equal(a1["hist"], a2["hist"])
 
 
-def test_breakdown_and_bad_structure_reported():
+@pytest.mark.parametrize("engine", ENGINES)
+def test_breakdown_and_bad_structure_reported(engine):
     n = 64
     rowp = np.arange(n + 1, dtype=np.int32)
     indx = np.arange(n, dtype=np.int32)
-    got = run_cg(rowp, indx, -np.ones(n), np.ones(n), 0.0, 10, expect=mxm.MXM_ERR_BREAKDOWN)
+    got = run_cg(rowp, indx, -np.ones(n), np.ones(n), 0.0, 10, expect=mxm.MXM_ERR_BREAKDOWN,
+                 engine=engine)
     assert got["iters"] == 0 and np.array_equal(got["x"], np.zeros(n))
     bad = indx.copy()
     bad[7] = 10_000
-    run_cg(rowp, bad, np.ones(n), np.ones(n), 0.0, 3, expect=mxm.MXM_ERR_INVALID_ARG)
+    run_cg(rowp, bad, np.ones(n), np.ones(n), 0.0, 3, expect=mxm.MXM_ERR_INVALID_ARG,
+           engine=engine)
     badp = rowp.copy()
     badp[5] = 1000
-    run_cg(badp, indx, np.ones(n), np.ones(n), 0.0, 3, expect=mxm.MXM_ERR_INVALID_ARG)
+    run_cg(badp, indx, np.ones(n), np.ones(n), 0.0, 3, expect=mxm.MXM_ERR_INVALID_ARG,
+           engine=engine)
     # the context is intact and the status was cleared
-    ok = run_cg(rowp, indx, np.full(n, 2.0), np.ones(n), 1e-30, 10)
+    ok = run_cg(rowp, indx, np.full(n, 2.0), np.ones(n), 1e-30, 10, engine=engine)
     assert ok["iters"] == 1 and np.allclose(ok["x"], 0.5, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("n,bw", [(100_000, 7), (1_000_000, 3), (30_000, 63)])
+def test_graph_engine_large_orders(n, bw):
+    """Orders beyond one cluster's shared memory: the graph engine only."""
+    rowp, indx, vals = inputs.banded_spd(13, 102, n, bw)
+    b = inputs.uniform_pm1(13, 103, (n,))
+    got, want = compare(rowp, indx, vals, b, 1e-22 * float(b @ b), 200, bw, mxm.CG_GRAPH)
+    assert got["iters"] > 5
+
+
+def test_engines_agree_and_auto():
+    """Both engines solve the same system to the same tolerance; the
+    automatic choice runs without a workspace for a small system."""
+    n, bw = 1024, 511
+    rowp, indx, vals = inputs.banded_spd(14, 104, n, bw)
+    b = inputs.uniform_pm1(14, 105, (n,))
+    stop = 1e-24 * float(b @ b)
+    c = run_cg(rowp, indx, vals, b, stop, 500, engine=mxm.CG_CLUSTER)
+    g = run_cg(rowp, indx, vals, b, stop, 500, engine=mxm.CG_GRAPH)
+    a = run_cg(rowp, indx, vals, b, stop, 500, engine=mxm.CG_AUTO)
+    assert c["iters"] == g["iters"] == a["iters"]
+    scale = np.max(np.abs(c["x"]))
+    assert np.max(np.abs(c["x"] - g["x"])) <= 1e-12 * scale
+    lib = mxm.load()
+    d = lambda arr, dt: torch.from_numpy(np.ascontiguousarray(arr)).to(dtype=dt).cuda()  # noqa: E731
+    dv, di, dr, db = d(vals, torch.float64), d(indx, torch.int32), d(rowp, torch.int32), \
+        d(b, torch.float64)
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    it = torch.zeros(1, dtype=torch.int32, device="cuda")
+    r2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    args = (dv.data_ptr(), di.data_ptr(), dr.data_ptr(), db.data_ptr(), x.data_ptr(), n, len(vals),
+            stop, 500)
+    tail = (it.data_ptr(), r2.data_ptr(), None, None)
+    assert lib.mxm_cg(*args, mxm.CG_AUTO, None, *tail) == mxm.MXM_OK
+    assert lib.mxm_cg(*args, mxm.CG_GRAPH, None, *tail) == mxm.MXM_ERR_INVALID_ARG
+    assert lib.mxm_cg(*args, 7, None, *tail) == mxm.MXM_ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert int(it.item()) == c["iters"] and mxm.mxm_get_device_status() == mxm.MXM_OK
