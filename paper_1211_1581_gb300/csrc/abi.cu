@@ -31,6 +31,7 @@ struct DeviceState {
   cudaStream_t h2d = nullptr;  // streams of the pipelined host path: copies in,
   cudaStream_t d2h = nullptr;  // copies out, and a second compute stream
   cudaStream_t c1 = nullptr;
+  cudaStream_t c2 = nullptr;   // scale and split of B's column panels
 };
 
 std::mutex g_mutex;
@@ -289,15 +290,19 @@ mxm_status mxm_f64_emul(const double* A, const double* B, double* C, int64_t m, 
   return mxm_gemm(MXM_MODE_EMUL_I8, A, B, C, m, k, n, slices, stream);
 }
 
-// Host-buffer product of the emulated modes, pipelined over panels of rows
-// of A: B is copied, scaled and split once; the panels of A are copied in
-// order on one copy stream, the panels of C copied back on another, and the
-// panels' scale, split and slice GEMM alternate between two compute streams
-// (the caller's and the library's) with a workspace each, so that the
-// persistent GEMM of one panel starts on the SMs the previous one frees.
-// Rows of A are scaled and split independently (the scale of row i is its
-// own maximum) and the column scales come from all of B, so the panels give
-// the same bits as one call over all rows.
+// Host-buffer product of the emulated modes, pipelined over blocks: P panels
+// of rows of A times Q panels of columns of B.  The copy stream brings B's
+// first column panel, then A's panels with B's other column panels after
+// the first row panel, so the first block product starts once a 1/Q part of
+// B (and one panel of A) has crossed the link; every panel is scaled and
+// split once (a column panel of B into its own digit planes; a row panel of
+// A for the Q products of that row).  Block products alternate between two
+// compute streams (the caller's and the library's) with a workspace each, so
+// that the persistent GEMM of one block starts on the SMs the previous one
+// frees; each block of C goes back by a 2-D copy on a third stream as soon
+// as it is done.  Rows of A and columns of B are scaled independently (the
+// scale of row i is its own maximum, that of column j its own), so the
+// blocks give the same bits as one call over the whole product.
 constexpr int64_t kHostPanels = 8;
 
 // Rows per panel (a multiple of the 128-row tile), or 0 when the product is
@@ -309,22 +314,34 @@ static int64_t host_panel_rows(int64_t m, int64_t n, int sms) {
   return h;
 }
 
+// Columns per panel of B: two panels when each still gives a block of one
+// row panel enough tiles for the GPU, else all columns.
+static int64_t host_panel_cols(int64_t h, int64_t n, int sms) {
+  const int64_t w = align_up((n + 1) / 2, size_t(kOzTileRows));
+  const int64_t tiles = (h / kOzTileRows) * (w / kOzTileRows);
+  if (w >= n || tiles < sms) return n;
+  return w;
+}
+
 static mxm_status gemm_host_panels(DeviceState* ds, int mode, const double* hA, const double* hB,
                                    double* hC, int64_t m, int64_t k, int64_t n, int slices,
                                    int64_t h, cudaStream_t s) {
   const int beta = mode_beta(mode);
-  const OzakiDims dp = ozaki_dims(h, k, n, slices, beta);  // the largest panel, no split-k
+  const int64_t w = host_panel_cols(h, n, ds->sm_count);
+  const int64_t P = (m + h - 1) / h, Q = (n + w - 1) / w;
+  const OzakiDims dp = ozaki_dims(h, k, w, slices, beta);  // the largest block, no split-k
   const OzakiLayout L = ozaki_layout(dp);
-  // per compute stream: row scales, A planes, running sums of one panel
+  // per compute stream: row scales, A planes, running sums of one block
   const size_t rb_bytes = align_up(sizeof(uint64_t) * size_t(h), 1024);
   const size_t ap_bytes = L.bslices - L.aslices;
   const size_t sm_bytes = L.total - L.sums;
   const size_t per_buf = rb_bytes + ap_bytes + sm_bytes;
-  const size_t shared_bytes = (L.aslices - L.colbits) + (L.sums - L.bslices);  // colbits, B planes
+  // per column panel: column scales and B planes
+  const size_t per_col = (L.aslices - L.colbits) + (L.sums - L.bslices);
   const size_t ab = align_up(sizeof(double) * size_t(m) * size_t(k), 1024);
   const size_t bb = align_up(sizeof(double) * size_t(k) * size_t(n), 1024);
   const size_t cb = align_up(sizeof(double) * size_t(m) * size_t(n), 1024);
-  mxm_status st = ensure_workspace(ds, ab + bb + cb + shared_bytes + 2 * per_buf, s);
+  mxm_status st = ensure_workspace(ds, ab + bb + cb + size_t(Q) * per_col + 2 * per_buf, s);
   if (st != MXM_OK) return st;
   if (ds->h2d == nullptr && cudaStreamCreateWithFlags(&ds->h2d, cudaStreamNonBlocking) != cudaSuccess)
     return cuda_fail();
@@ -332,17 +349,17 @@ static mxm_status gemm_host_panels(DeviceState* ds, int mode, const double* hA, 
     return cuda_fail();
   if (ds->c1 == nullptr && cudaStreamCreateWithFlags(&ds->c1, cudaStreamNonBlocking) != cudaSuccess)
     return cuda_fail();
+  if (ds->c2 == nullptr && cudaStreamCreateWithFlags(&ds->c2, cudaStreamNonBlocking) != cudaSuccess)
+    return cuda_fail();
   uint8_t* base = static_cast<uint8_t*>(ds->ws);
   double* dA = reinterpret_cast<double*>(base);
-  double* dB = reinterpret_cast<double*>(base + ab);
-  double* dC = reinterpret_cast<double*>(base + ab + bb);
-  uint8_t* w = base + ab + bb + cb;
-  uint64_t* colbits = reinterpret_cast<uint64_t*>(w);
-  uint8_t* bplanes = w + (L.aslices - L.colbits);
-  uint8_t* bufs = w + shared_bytes;
-  const int64_t P = (m + h - 1) / h;
-  // events: B copied, B split, then per panel: A copied, C computed; done
-  std::vector<cudaEvent_t> ev(2 * P + 3, nullptr);
+  double* dB = reinterpret_cast<double*>(base + ab);  // column panel j at dB + j w k (k x wj)
+  double* dC = reinterpret_cast<double*>(base + ab + bb);  // block (i, j) at dC + (i n + j w h)
+  uint8_t* cols = base + ab + bb + cb;
+  uint8_t* bufs = cols + size_t(Q) * per_col;
+  // events: per column panel B copied, B split; per row panel A copied; per
+  // block C computed; done
+  std::vector<cudaEvent_t> ev(2 * Q + P + P * Q + 2, nullptr);
   mxm_status rc = MXM_OK;
   auto fail = [&]() { rc = cuda_fail(); };
   for (auto& e : ev)
@@ -350,49 +367,87 @@ static mxm_status gemm_host_panels(DeviceState* ds, int mode, const double* hA, 
       e = nullptr;
       fail();
     }
-  cudaEvent_t eB = ev[0], eBs = ev[1], eDone = ev[2];
+  cudaEvent_t* eBc = ev.data();          // Q
+  cudaEvent_t* eBs = ev.data() + Q;      // Q
+  cudaEvent_t* eA = ev.data() + 2 * Q;   // P
+  cudaEvent_t* eC = eA + P;              // P Q
+  cudaEvent_t eDone = ev.back();
+  cudaEvent_t eStart = ev[ev.size() - 2];
   cudaStream_t cs[2] = {s, ds->c1};
-  if (rc == MXM_OK &&
-      (cudaMemcpyAsync(dB, hB, sizeof(double) * size_t(k) * size_t(n), cudaMemcpyHostToDevice,
-                       ds->h2d) != cudaSuccess ||
-       cudaEventRecord(eB, ds->h2d) != cudaSuccess || cudaStreamWaitEvent(s, eB, 0) != cudaSuccess))
+  auto col0 = [&](int64_t j) { return j * w; };
+  auto colw = [&](int64_t j) { return (n - j * w) < w ? (n - j * w) : w; };
+  auto row0 = [&](int64_t i) { return i * h; };
+  auto rowh = [&](int64_t i) { return (m - i * h) < h ? (m - i * h) : h; };
+  auto copy_b = [&](int64_t j) {
+    double* dst = dB + j * w * k;
+    if (cudaMemcpy2DAsync(dst, sizeof(double) * size_t(colw(j)), hB + col0(j),
+                          sizeof(double) * size_t(n), sizeof(double) * size_t(colw(j)),
+                          size_t(k), cudaMemcpyHostToDevice, ds->h2d) != cudaSuccess ||
+        cudaEventRecord(eBc[j], ds->h2d) != cudaSuccess)
+      fail();
+  };
+  auto copy_a = [&](int64_t i) {
+    if (cudaMemcpyAsync(dA + row0(i) * k, hA + row0(i) * k,
+                        sizeof(double) * size_t(rowh(i)) * size_t(k), cudaMemcpyHostToDevice,
+                        ds->h2d) != cudaSuccess ||
+        cudaEventRecord(eA[i], ds->h2d) != cudaSuccess)
+      fail();
+  };
+  // copy order: B_0, A_0, B_1 .. B_{Q-1}, A_1 .. A_{P-1}
+  if (rc == MXM_OK) copy_b(0);
+  if (rc == MXM_OK) copy_a(0);
+  for (int64_t j = 1; j < Q && rc == MXM_OK; ++j) copy_b(j);
+  for (int64_t i = 1; i < P && rc == MXM_OK; ++i) copy_a(i);
+  // column panels of B: scale and split on their own stream as they arrive
+  // (the caller's stream first waits for whatever it had queued)
+  if (rc == MXM_OK && (cudaEventRecord(eStart, s) != cudaSuccess ||
+                       cudaStreamWaitEvent(ds->c2, eStart, 0) != cudaSuccess))
     fail();
-  if (rc == MXM_OK) {
-    const OzakiDims db = ozaki_dims(0, k, n, slices, beta);
-    if (launch_ozaki_scale(nullptr, dB, db, nullptr, colbits, ds->status, s) != cudaSuccess ||
-        launch_ozaki_split(nullptr, dB, db, nullptr, colbits, nullptr, bplanes, s) !=
+  for (int64_t j = 0; j < Q && rc == MXM_OK; ++j) {
+    uint8_t* cw = cols + size_t(j) * per_col;
+    uint64_t* colbits = reinterpret_cast<uint64_t*>(cw);
+    uint8_t* bplanes = cw + (L.aslices - L.colbits);
+    const OzakiDims db = ozaki_dims(0, k, colw(j), slices, beta);
+    if (cudaStreamWaitEvent(ds->c2, eBc[j], 0) != cudaSuccess ||
+        launch_ozaki_scale(nullptr, dB + j * w * k, db, nullptr, colbits, ds->status, ds->c2) !=
             cudaSuccess ||
-        cudaEventRecord(eBs, s) != cudaSuccess || cudaStreamWaitEvent(ds->c1, eBs, 0) != cudaSuccess)
+        launch_ozaki_split(nullptr, dB + j * w * k, db, nullptr, colbits, nullptr, bplanes,
+                           ds->c2) != cudaSuccess ||
+        cudaEventRecord(eBs[j], ds->c2) != cudaSuccess)
       fail();
   }
-  for (int64_t p = 0; p < P && rc == MXM_OK; ++p) {
-    const int64_t r0 = p * h, hp = (m - r0) < h ? (m - r0) : h;
-    if (cudaMemcpyAsync(dA + r0 * k, hA + r0 * k, sizeof(double) * size_t(hp) * size_t(k),
-                        cudaMemcpyHostToDevice, ds->h2d) != cudaSuccess ||
-        cudaEventRecord(ev[3 + p], ds->h2d) != cudaSuccess)
-      fail();
-  }
-  for (int64_t p = 0; p < P && rc == MXM_OK; ++p) {
-    const int64_t r0 = p * h, hp = (m - r0) < h ? (m - r0) : h;
-    cudaStream_t c = cs[p & 1];
-    uint8_t* buf = bufs + (p & 1) * per_buf;
+  for (int64_t i = 0; i < P && rc == MXM_OK; ++i) {
+    const int64_t r0 = row0(i), hp = rowh(i);
+    cudaStream_t c = cs[i & 1];
+    uint8_t* buf = bufs + (i & 1) * per_buf;
     uint64_t* rowbits = reinterpret_cast<uint64_t*>(buf);
     uint8_t* aplanes = buf + rb_bytes;
     uint64_t* sums = reinterpret_cast<uint64_t*>(buf + rb_bytes + ap_bytes);
     const OzakiDims da = ozaki_dims(hp, k, 0, slices, beta);
-    const OzakiDims dg = ozaki_dims(hp, k, n, slices, beta);
-    if (cudaStreamWaitEvent(c, ev[3 + p], 0) != cudaSuccess ||
+    if (cudaStreamWaitEvent(c, eA[i], 0) != cudaSuccess ||
         launch_ozaki_scale(dA + r0 * k, nullptr, da, rowbits, nullptr, ds->status, c) !=
             cudaSuccess ||
         launch_ozaki_split(dA + r0 * k, nullptr, da, rowbits, nullptr, aplanes, nullptr, c) !=
-            cudaSuccess ||
-        launch_ozaki_gemm(aplanes, bplanes, rowbits, colbits, dC + r0 * n, dg, sums, ds->status,
-                          c) != cudaSuccess ||
-        cudaEventRecord(ev[3 + P + p], c) != cudaSuccess ||
-        cudaStreamWaitEvent(ds->d2h, ev[3 + P + p], 0) != cudaSuccess ||
-        cudaMemcpyAsync(hC + r0 * n, dC + r0 * n, sizeof(double) * size_t(hp) * size_t(n),
-                        cudaMemcpyDeviceToHost, ds->d2h) != cudaSuccess)
+            cudaSuccess)
       fail();
+    for (int64_t j = 0; j < Q && rc == MXM_OK; ++j) {
+      uint8_t* cw = cols + size_t(j) * per_col;
+      const uint64_t* colbits = reinterpret_cast<const uint64_t*>(cw);
+      const uint8_t* bplanes = cw + (L.aslices - L.colbits);
+      const int64_t wj = colw(j);
+      double* blk = dC + r0 * n + j * w * hp;  // h x wj, row-major, contiguous
+      const OzakiDims dg = ozaki_dims(hp, k, wj, slices, beta);
+      cudaEvent_t done = eC[i * Q + j];
+      if (cudaStreamWaitEvent(c, eBs[j], 0) != cudaSuccess ||
+          launch_ozaki_gemm(aplanes, bplanes, rowbits, colbits, blk, dg, sums, ds->status, c) !=
+              cudaSuccess ||
+          cudaEventRecord(done, c) != cudaSuccess ||
+          cudaStreamWaitEvent(ds->d2h, done, 0) != cudaSuccess ||
+          cudaMemcpy2DAsync(hC + r0 * n + col0(j), sizeof(double) * size_t(n), blk,
+                            sizeof(double) * size_t(wj), sizeof(double) * size_t(wj), size_t(hp),
+                            cudaMemcpyDeviceToHost, ds->d2h) != cudaSuccess)
+        fail();
+    }
   }
   // the caller's stream ends after the last copy back; every stream is
   // drained before the events go
@@ -401,6 +456,7 @@ static mxm_status gemm_host_panels(DeviceState* ds, int mode, const double* hA, 
     fail();
   if (cudaStreamSynchronize(s) != cudaSuccess) fail();
   cudaStreamSynchronize(ds->c1);
+  cudaStreamSynchronize(ds->c2);
   cudaStreamSynchronize(ds->h2d);
   cudaStreamSynchronize(ds->d2h);
   for (auto& e : ev)

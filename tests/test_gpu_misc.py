@@ -68,13 +68,17 @@ def test_peak_probes_run(kind):
 
 
 @pytest.mark.parametrize("pinned", [True, False])
-@pytest.mark.parametrize("mode,S", [(mxm.MODE_EMUL_I8, 7), (mxm.MODE_EMUL_BF16, 6)])
-def test_host_entry_point_panels(mode, S, pinned):
+@pytest.mark.parametrize("mode,S,m,n", [(mxm.MODE_EMUL_I8, 7, 3000, 6500),
+                                        (mxm.MODE_EMUL_BF16, 6, 3000, 6500),
+                                        (mxm.MODE_EMUL_I8, 7, 4000, 10000)])
+def test_host_entry_point_panels(mode, S, m, n, pinned):
     """Products large enough for the pipelined host path (A and C moved in
-    panels of rows while earlier panels compute): 8 panels of 384 rows, the
-    last one 312 rows; bit-identical to the device call and, on sampled
-    entries, to the CPU emulator."""
-    m, k, n = 3000, 300, 6500
+    blocks while earlier blocks compute): 8 panels of 384 rows, the last
+    one 312 rows, all columns at once; and 8 panels of 512 rows times two
+    column panels of B (5120 and 4880 columns) on a 152-SM GPU.
+    Bit-identical to the device call and, on sampled entries, to the CPU
+    emulator."""
+    k = 300
     A, B = inputs.gemm_operands("spread", m, k, n, seed=0, cfg=12)
     if pinned:
         Ah = torch.from_numpy(A).pin_memory()
@@ -92,6 +96,7 @@ def test_host_entry_point_panels(mode, S, pinned):
     rng = np.random.default_rng(13)
     ii = rng.integers(0, m, 300)
     jj = rng.integers(0, n, 300)
-    ii[:3] = [0, 2999, 2688]  # first row, last row, first row of the last panel
+    ii[:3] = [0, m - 1, (m - 1) // 8 * 8]  # first row, last row, a row of the last panel
+    jj[:3] = [n - 1, 0, n // 2]
     beta = 7 if mode == mxm.MODE_EMUL_I8 else 8
     assert_bitwise(Ch[ii, jj], oracle.ozaki_entries(A, B, ii, jj, S=S, beta=beta), "panels vs oracle")
