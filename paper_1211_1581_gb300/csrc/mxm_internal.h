@@ -113,6 +113,37 @@ struct OzakiLayout {
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Whether the per-diagonal integer sums of a tile with Kt k-blocks fit in
+// int32, the condition of the paired slice GEMM without spills: every digit
+// product is at most (2^beta - 1)^2 and a diagonal has at most S of them
+// per k.
+__host__ __device__ inline bool ozaki_narrow(int S, int beta, int64_t Kt) {
+  const double dmax = static_cast<double>((1 << beta) - 1);
+  return static_cast<double>(S) * dmax * dmax * kOzTileK * static_cast<double>(Kt) <
+         2147483647.0;
+}
+
+// CTAs of the paired slice GEMM that keep a spill area (the grid is capped
+// there when spills are on).
+constexpr int64_t kOzSpillCtas = 256;
+
+// Bytes of the running sums of a product (per C tile 128 x 128 x 8 bytes),
+// or under split-k the partial sums D_g of every k range.
+inline size_t ozaki_sums_bytes(const OzakiDims& d) {
+  const size_t tile8 = (size_t)kOzTileRows * kOzTileRows * 8;
+  return d.splits > 1 ? (size_t)d.splits * d.Mt * d.Nt * d.S * tile8
+                      : (size_t)d.Mt * d.Nt * tile8;
+}
+
+// Spill area of the paired slice GEMM when a diagonal's integer sum can
+// outgrow int32 over all of k (long k, 8-bit digits): per CTA the int64
+// partial sums of the two diagonals in work, 2 x 128 x 128 x 8 bytes.
+inline size_t ozaki_spill_bytes(const OzakiDims& d) {
+  if (d.fp8 || d.splits > 1 || ozaki_narrow(d.S, d.beta, d.Kt)) return 0;
+  const int64_t ctas = d.Mt * d.Nt < kOzSpillCtas ? d.Mt * d.Nt : kOzSpillCtas;
+  return (size_t)ctas * 2 * kOzTileRows * kOzTileRows * 8;
+}
+
 inline OzakiLayout ozaki_layout(const OzakiDims& d) {
   OzakiLayout L;
   size_t off = 0;
@@ -125,23 +156,13 @@ inline OzakiLayout ozaki_layout(const OzakiDims& d) {
   // owns 32 consecutive rows, touches 256 contiguous bytes per column).
   // Under split-k the region holds instead the int64 partial sums D_g of
   // every k range: [splits][Mt x Nt tiles][S diagonals] x 128 x 128,
-  // column-major inside the tile.
-  const size_t tile8 = (size_t)kOzTileRows * kOzTileRows * 8;
-  const size_t sums = d.splits > 1 ? (size_t)d.splits * d.Mt * d.Nt * d.S * tile8
-                                   : (size_t)d.Mt * d.Nt * tile8;
-  L.sums = off; off = align_up(off + sums, 1024);
+  // column-major inside the tile.  The spill area (if any) follows the sums.
+  L.sums = off; off = align_up(off + ozaki_sums_bytes(d), 1024);
+  off = align_up(off + ozaki_spill_bytes(d), 1024);
   L.total = off;
   return L;
 }
 
-// Whether the per-diagonal integer sums of a tile with Kt k-blocks fit in
-// int32, the condition of the paired slice GEMM: every digit product is at
-// most (2^beta - 1)^2 and a diagonal has at most S of them per k.
-__host__ __device__ inline bool ozaki_narrow(int S, int beta, int64_t Kt) {
-  const double dmax = static_cast<double>((1 << beta) - 1);
-  return static_cast<double>(S) * dmax * dmax * kOzTileK * static_cast<double>(Kt) <
-         2147483647.0;
-}
 
 // Largest number of K=16 MMAs whose integer products can be summed in an
 // FP32 accumulator without rounding: every product is at most (2^beta-1)^2

@@ -575,6 +575,8 @@ struct OzSingle {
   int64_t splits;     // k ranges per C tile; > 1: units write partials
   int S;
   int64_t tile_bytes; // operand tile size of the digit carrier
+  long long* spill = nullptr;  // paired kernel: per-CTA int64 partials of the two diagonals
+  int spill_every = 0;         // window drains after which a diagonal's int32 sum spills
   __device__ __forceinline__ int64_t count() const { return Mt * Nt * splits; }
   // Unit t: C tile t / splits, k range t % splits.
   __device__ __forceinline__ OzTile tile(int64_t t) const {
@@ -1028,7 +1030,8 @@ struct Ring {
 
 // The fold of one diagonal g into a running sum held as 64 bits: an exact
 // int64 partial (units of 2^{-beta (S+1)}) while g >= gx, an FP64 value after.
-template <typename Tiles, typename Fmt>
+// kSpill: long k, a diagonal's int32 sums spill to an int64 area (below).
+template <typename Tiles, typename Fmt, bool kSpill = false>
 __global__ void __launch_bounds__(kP2Threads, 1)
     oz_gemm2_kernel(const Tiles tiles, int S, int beta, int window, int* __restrict__ status) {
   constexpr int kRingA = Fmt::kRingA, kRingB = Fmt::kRingB, kTile = Fmt::kTileBytes;
@@ -1227,6 +1230,31 @@ __global__ void __launch_bounds__(kP2Threads, 1)
     uint32_t fulls00 = 0u, fulls01 = 0u, fulls10 = 0u, fulls11 = 0u;
     bool ok = true;
     int D0[64], D1[64];
+    // Long k: a diagonal's int32 sum is moved into this CTA's int64 spill
+    // area every spill_every drains (before it could pass 2^31), and the
+    // fold adds the spilled part back; the integer sum is the same.
+    int nd0 = 0, nd1 = 0;
+    bool sp0 = false, sp1 = false;
+    long long* const spill_base =
+        tiles.spill + static_cast<size_t>(blockIdx.x) * 2 * kOzTileRows * kOzTileRows;
+    auto spill = [&](int x, int (&Dx)[64]) {
+      bool& sp = x ? sp1 : sp0;
+      long long* p = spill_base + (static_cast<size_t>(x) * kOzTileRows + half * 64) * kOzTileRows +
+                     row_in_tile;
+#pragma unroll 1
+      for (int ch = 0; ch < 8; ++ch) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          long long* q = p + static_cast<size_t>(ch * 8 + i) * kOzTileRows;
+          *q = (sp ? *q : 0ll) + Dx[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 56; ++i) Dx[i] = Dx[i + 8];
+#pragma unroll
+        for (int i = 56; i < 64; ++i) Dx[i] = 0;
+      }
+      sp = true;
+    };
     auto drain = [&](int x, int (&Dx)[64]) {
       int& b = x ? buf1 : buf0;
       uint32_t& f = x ? (b ? fulls11 : fulls10) : (b ? fulls01 : fulls00);
@@ -1247,6 +1275,13 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.accempty[a]);
       b ^= 1;
+      if constexpr (kSpill) {
+        int& nd = x ? nd1 : nd0;
+        if (++nd == tiles.spill_every) {
+          nd = 0;
+          spill(x, Dx);
+        }
+      }
       return true;
     };
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -1264,6 +1299,8 @@ __global__ void __launch_bounds__(kP2Threads, 1)
           D0[i] = 0;
           D1[i] = 0;
         }
+        nd0 = nd1 = 0;
+        sp0 = sp1 = false;
         for (int64_t kb = 0; kb < j.Kt && ok; ++kb) {
           if (kb == j.Kt - 1 && q > 0) {
             // the fold at the end of this k-block reads the tile's running
@@ -1317,8 +1354,15 @@ __global__ void __launch_bounds__(kP2Threads, 1)
           }
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            cur[i] = fold_step(cur[i], D0[i], g, gx, S, beta);
-            if (pair) cur[i] = fold_step(cur[i], D1[i], g - 1, gx, S, beta);
+            long long d0 = D0[i], d1 = D1[i];
+            if constexpr (kSpill) {
+              const size_t sc =
+                  static_cast<size_t>(half * 64 + ch * 8 + i) * kOzTileRows + row_in_tile;
+              if (sp0) d0 += spill_base[sc];
+              if (sp1) d1 += spill_base[static_cast<size_t>(kOzTileRows) * kOzTileRows + sc];
+            }
+            cur[i] = fold_step(cur[i], d0, g, gx, S, beta);
+            if (pair) cur[i] = fold_step(cur[i], d1, g - 1, gx, S, beta);
           }
           if (last) {
             const int64_t cbase = col0 + ch * 8;
@@ -1495,17 +1539,26 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
         sums, rowbits, colbits, C, d.m, d.n, d.Mt, d.Nt, d.Kt, splits, d.S, d.beta);
     return cudaGetLastError();
   }
-  if (ozaki_narrow(d.S, d.beta, d.Kt)) {
-    auto kern = oz_gemm2_kernel<OzSingle, FmtBf16>;
-    const size_t kSmem = gemm2_smem_bytes<FmtBf16>();
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(kSmem));
-    if (e != cudaSuccess) return e;
-    kern<<<static_cast<unsigned>(grid), kP2Threads, kSmem, s>>>(tiles, d.S, d.beta, window,
-                                                                status);
-    return cudaGetLastError();
+  // the paired kernel; when a diagonal's sum over all of k may pass int32,
+  // with the spill area that follows the running sums (grid capped to it)
+  int64_t g2 = grid;
+  if (!ozaki_narrow(d.S, d.beta, d.Kt)) {
+    const double dmax = static_cast<double>((1 << d.beta) - 1);
+    const double per_drain = static_cast<double>(window) * kOzTileK * dmax * dmax;
+    tiles.spill_every = static_cast<int>(2147483647.0 / per_drain);
+    if (tiles.spill_every < 1) return cudaErrorNotSupported;
+    tiles.spill = reinterpret_cast<long long*>(reinterpret_cast<uint8_t*>(sums) +
+                                               align_up(ozaki_sums_bytes(d), 1024));
+    if (g2 > kOzSpillCtas) g2 = kOzSpillCtas;
   }
-  return launch_oz_gemm_t<long long, false>(tiles, grid, d.S, d.beta, window, status, s);
+  auto kern = tiles.spill != nullptr ? oz_gemm2_kernel<OzSingle, FmtBf16, true>
+                                     : oz_gemm2_kernel<OzSingle, FmtBf16, false>;
+  const size_t kSmem = gemm2_smem_bytes<FmtBf16>();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kSmem));
+  if (e != cudaSuccess) return e;
+  kern<<<static_cast<unsigned>(g2), kP2Threads, kSmem, s>>>(tiles, d.S, d.beta, window, status);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t /*max_kt*/, int* status,

@@ -194,3 +194,28 @@ def test_emul_one_kblock_many_tiles(shape, S):
     ii = rng.integers(0, m, 400)
     jj = rng.integers(0, n, 400)
     assert_bitwise(C[ii, jj], oracle.ozaki_entries(A, B, ii, jj, S=S, beta=7), f"{shape} S={S}")
+
+
+# Long k in the paired kernel: a diagonal's int32 digit sum would pass 2^31
+# over all of k, so every so many window drains the epilogue moves it into an
+# int64 spill area and the fold adds it back.  The integer sums, and so the
+# results, stay bit-identical to the CPU emulator.
+@pytest.mark.parametrize("mode,S,beta,k", [(mxm.MODE_EMUL_BF16, 6, 8, 8192),
+                                           (mxm.MODE_EMUL_BF16, 8, 8, 12000),
+                                           (mxm.MODE_EMUL_I8, 7, 7, 20000)])
+def test_emul_long_k_spills_bit_identical(mode, S, beta, k):
+    m, n = 2048, 2048 + 64  # enough C tiles for no split-k; a ragged column tile
+    A, B = inputs.gemm_operands("spread", m, k, n, seed=0, cfg=40 + S)
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(B).cuda()
+    C = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    mxm.mxm_gemm(mode, dA, dB, C, slices=S)
+    torch.cuda.synchronize()
+    assert mxm.mxm_get_device_status() == mxm.MXM_OK
+    C = C.cpu().numpy()
+    rng = np.random.default_rng(k)
+    ii = rng.integers(0, m, 160)
+    jj = rng.integers(0, n, 160)
+    ii[:4] = [0, m - 1, 0, m - 1]
+    jj[:4] = [0, n - 1, n - 1, 0]
+    assert_bitwise(C[ii, jj], oracle.ozaki_entries(A, B, ii, jj, S=S, beta=beta), "long k spills")
