@@ -17,6 +17,8 @@ Functions (all take and return numpy arrays, row-major float64):
 * ``entries_dot2_abs`` - Dot2 and |A|.|B| at selected (i, j) only.
 * ``ozaki_split``  - steps 1-2 of the Ozaki split (exponents + digits).
 * ``ozaki_gemm`` / ``ozaki_entries`` - the full emulated product.
+* ``ozaki_split_rn8`` / ``ozaki_gemm_rn8`` / ``ozaki_entries_rn8`` - the same
+  with balanced 8-bit digits (the value rounded once to nearest).
 * ``gemm_f32``, ``round_bf16`` - comparison-mode references.
 * ``spmv`` / ``spmv_dot2`` / ``spmv_abs`` - mod2as (Sec. 3.2), CSR y = A x
   in storage order, by Dot2, and |A||x|.
@@ -98,6 +100,12 @@ def _load():
     lib.oracle_ozaki_gemm.restype = I
     lib.oracle_ozaki_entries.argtypes = [P, P, I64, I64, I64, I, I, I64, P, P, P]
     lib.oracle_ozaki_entries.restype = I
+    lib.oracle_ozaki_split_rn8.argtypes = [P, I64, I64, I, I, P, P]
+    lib.oracle_ozaki_split_rn8.restype = I
+    lib.oracle_ozaki_gemm_rn8.argtypes = [P, P, P, I64, I64, I64, I]
+    lib.oracle_ozaki_gemm_rn8.restype = I
+    lib.oracle_ozaki_entries_rn8.argtypes = [P, P, I64, I64, I64, I, I64, P, P, P]
+    lib.oracle_ozaki_entries_rn8.restype = I
     lib.oracle_round_bf16.argtypes = [P, P, I64]
     lib.oracle_round_bf16.restype = None
     lib.oracle_num_threads.argtypes = []
@@ -222,6 +230,42 @@ def ozaki_entries(A, B, ii, jj, S: int, beta: int = 7):
                                       _ptr(ii), _ptr(jj), _ptr(out))
     if st != OK:
         raise FloatingPointError(f"oracle_ozaki_entries status {st}")
+    return out
+
+
+def ozaki_split_rn8(X, by_col: bool, S: int):
+    """The balanced 8-bit digit split: exponents e + 1 (int32) and digits
+    [S][rows][cols] (int16), sum_s d_s 2^(8(S-s)) = round(x 2^(8S - e - 1))."""
+    X = _f64(X)
+    r, c = X.shape
+    e = np.empty(c if by_col else r, dtype=np.int32)
+    d = np.empty((S, r, c), dtype=np.int16)
+    st = _load().oracle_ozaki_split_rn8(_ptr(X), r, c, int(by_col), S, _ptr(e), _ptr(d))
+    if st != OK:
+        raise FloatingPointError(f"oracle_ozaki_split_rn8 status {st}")
+    return e, d
+
+
+def ozaki_gemm_rn8(A, B, S: int):
+    A, B, m, k, n = _dims(A, B)
+    C = np.empty((m, n), dtype=np.float64)
+    st = _load().oracle_ozaki_gemm_rn8(_ptr(A), _ptr(B), _ptr(C), m, k, n, S)
+    if st != OK:
+        raise FloatingPointError(f"oracle_ozaki_gemm_rn8 status {st}")
+    return C
+
+
+def ozaki_entries_rn8(A, B, ii, jj, S: int):
+    A, B, m, k, n = _dims(A, B)
+    ii = np.ascontiguousarray(ii, dtype=np.int64)
+    jj = np.ascontiguousarray(jj, dtype=np.int64)
+    if ii.size and (ii.min() < 0 or ii.max() >= m or jj.min() < 0 or jj.max() >= n):
+        raise ValueError("entry index out of range")
+    out = np.empty(ii.shape, dtype=np.float64)
+    st = _load().oracle_ozaki_entries_rn8(_ptr(A), _ptr(B), m, k, n, S, ii.size, _ptr(ii),
+                                          _ptr(jj), _ptr(out))
+    if st != OK:
+        raise FloatingPointError(f"oracle_ozaki_entries_rn8 status {st}")
     return out
 
 

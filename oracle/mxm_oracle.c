@@ -30,6 +30,8 @@
  *                       Algorithms 59, 2012; integer-slice form of Ootomo,
  *                       Ozaki, Yokota, IJHPCA 2024) in the steps:
  *                       scale, split, exact slice products, recombination.
+ *                       oracle_ozaki_*_rn8: the same with balanced 8-bit
+ *                       digits, the value rounded once to nearest.
  *   oracle_gemm_f32     FP32 naive loop (comparison mode).
  *   oracle_round_bf16   double -> bfloat16, round to nearest even.
  *   oracle_spmv         mod2as (Sec. 3.2): y = A x, A in the 3-array CSR
@@ -253,19 +255,58 @@ static void split_value(double x, int e, int beta, int S, int16_t* d, int64_t st
   }
 }
 
-/* Steps 1 and 2 for a whole matrix.  digits is [S][rows][cols] int16. */
-int oracle_ozaki_split(const double* X, int64_t rows, int64_t cols, int by_col,
-                       int beta, int S, int32_t* exps, int16_t* digits) {
-  if (beta < 1 || beta > 8 || S < 1) return ORACLE_INVALID;
+/* Step 2 with balanced 8-bit digits, the round-to-nearest variant of the
+ * split (the original Ozaki splitting rounds to nearest too).  The scale
+ * exponent is one more (e' = e + 1, so |x| 2^-e' < 1/2); the value is
+ * rounded once, to the nearest integer with ties to even,
+ *   V = round(x 2^(8S - e')),   |V| <= 2^(8S - 1), exact in int64 (S <= 7),
+ * and written in base 256 from the least significant digit up: each lower
+ * digit is V mod 256 taken in [-128, 127] and V becomes (V - d) / 256; the
+ * top digit is what remains, in [-128, 128].  So sum_s d_s 2^(8(S-s)) = V,
+ * every digit product is at most 2^14 in magnitude, and x is approximated
+ * to within 2^(e' - 8S - 1).  Digit s goes to d[(s - 1) stride].        */
+static void split_value_rn8(double x, int e1, int S, int16_t* d, int64_t stride) {
+  int64_t V = (int64_t)nearbyint(ldexp(x, 8 * S - e1));
+  for (int s = S; s >= 2; --s) {
+    int64_t r = V % 256;
+    if (r < 0) r += 256;
+    const int64_t dig = r >= 128 ? r - 256 : r;
+    d[(s - 1) * stride] = (int16_t)dig;
+    V = (V - dig) / 256;
+  }
+  d[0] = (int16_t)V;
+}
+
+/* Steps 1 and 2 for a whole matrix.  digits is [S][rows][cols] int16.
+ * rn8: balanced 8-bit digits (beta is then 8) with exps = e + 1.      */
+static int ozaki_split_any(const double* X, int64_t rows, int64_t cols, int by_col, int beta,
+                           int S, int rn8, int32_t* exps, int16_t* digits) {
+  if (beta < 1 || beta > 8 || S < 1 || (rn8 && (beta != 8 || S > 7))) return ORACLE_INVALID;
   int st = oracle_ozaki_exponents(X, rows, cols, by_col, exps);
   if (st != ORACLE_OK) return st;
+  const int64_t cnt = by_col ? cols : rows;
+  if (rn8)
+    for (int64_t i = 0; i < cnt; ++i) exps[i] += 1;
   const int64_t plane = rows * cols;
   for (int64_t i = 0; i < rows; ++i)
     for (int64_t l = 0; l < cols; ++l) {
       int e = by_col ? exps[l] : exps[i];
-      split_value(X[i * cols + l], e, beta, S, digits + i * cols + l, plane);
+      if (rn8)
+        split_value_rn8(X[i * cols + l], e, S, digits + i * cols + l, plane);
+      else
+        split_value(X[i * cols + l], e, beta, S, digits + i * cols + l, plane);
     }
   return ORACLE_OK;
+}
+
+int oracle_ozaki_split(const double* X, int64_t rows, int64_t cols, int by_col,
+                       int beta, int S, int32_t* exps, int16_t* digits) {
+  return ozaki_split_any(X, rows, cols, by_col, beta, S, 0, exps, digits);
+}
+
+int oracle_ozaki_split_rn8(const double* X, int64_t rows, int64_t cols, int by_col, int S,
+                           int32_t* exps, int16_t* digits) {
+  return ozaki_split_any(X, rows, cols, by_col, 8, S, 1, exps, digits);
 }
 
 /* Steps 3 and 4 for one entry.  dA is [S][m][k]; dBt holds the digits of
@@ -289,9 +330,10 @@ static double ozaki_entry(const int16_t* dA, const int16_t* dBt, int64_t m,
   return ldexp(acc, e_i + f_j);
 }
 
-/* Full emulated product C = A.B with S slices of beta bits. */
-int oracle_ozaki_gemm(const double* A, const double* B, double* C, int64_t m,
-                      int64_t k, int64_t n, int S, int beta) {
+/* Full emulated product C = A.B with S slices of beta bits (rn8: the
+ * balanced 8-bit digits; steps 3 and 4 are the same). */
+static int ozaki_gemm_any(const double* A, const double* B, double* C, int64_t m, int64_t k,
+                          int64_t n, int S, int beta, int rn8) {
   if (beta < 1 || beta > 8 || S < 1 || S > 16) return ORACLE_INVALID;
   size_t szA = (size_t)(S * m * k > 0 ? S * m * k : 1);
   size_t szB = (size_t)(S * k * n > 0 ? S * k * n : 1);
@@ -302,8 +344,8 @@ int oracle_ozaki_gemm(const double* A, const double* B, double* C, int64_t m,
   int16_t* dBt = (int16_t*)malloc(sizeof(int16_t) * szB);
   int st = ORACLE_OK;
   if (!e || !f || !dA || !dB || !dBt) { st = ORACLE_INVALID; goto done; }
-  st = oracle_ozaki_split(A, m, k, 0, beta, S, e, dA);
-  if (st == ORACLE_OK) st = oracle_ozaki_split(B, k, n, 1, beta, S, f, dB);
+  st = ozaki_split_any(A, m, k, 0, beta, S, rn8, e, dA);
+  if (st == ORACLE_OK) st = ozaki_split_any(B, k, n, 1, beta, S, rn8, f, dB);
   if (st != ORACLE_OK) goto done;
   for (int s = 0; s < S; ++s)
     for (int64_t l = 0; l < k; ++l)
@@ -321,13 +363,24 @@ done:
   return st;
 }
 
+int oracle_ozaki_gemm(const double* A, const double* B, double* C, int64_t m, int64_t k,
+                      int64_t n, int S, int beta) {
+  return ozaki_gemm_any(A, B, C, m, k, n, S, beta, 0);
+}
+
+int oracle_ozaki_gemm_rn8(const double* A, const double* B, double* C, int64_t m, int64_t k,
+                          int64_t n, int S) {
+  return ozaki_gemm_any(A, B, C, m, k, n, S, 8, 1);
+}
+
 /* Selected entries of the emulated product; splits only the rows and
  * columns the sample touches.                                          */
-int oracle_ozaki_entries(const double* A, const double* B, int64_t m, int64_t k,
-                         int64_t n, int S, int beta, int64_t count,
-                         const int64_t* ii, const int64_t* jj, double* out) {
+static int ozaki_entries_any(const double* A, const double* B, int64_t m, int64_t k, int64_t n,
+                             int S, int beta, int rn8, int64_t count, const int64_t* ii,
+                             const int64_t* jj, double* out) {
   (void)m;
-  if (beta < 1 || beta > 8 || S < 1 || S > 16) return ORACLE_INVALID;
+  if (beta < 1 || beta > 8 || S < 1 || S > 16 || (rn8 && (beta != 8 || S > 7)))
+    return ORACLE_INVALID;
   int bad = 0;
   int64_t t;
 #pragma omp parallel for schedule(dynamic, 4) reduction(| : bad)
@@ -344,10 +397,15 @@ int oracle_ozaki_entries(const double* A, const double* B, int64_t m, int64_t k,
     }
     /* the column exponent needs the whole column of B; the row exponent
      * the whole row of A: both were just scanned.                      */
-    int ei = oracle_exponent(ma), fj = oracle_exponent(mb);
+    int ei = oracle_exponent(ma) + rn8, fj = oracle_exponent(mb) + rn8;
     for (int64_t l = 0; l < k; ++l) {
-      split_value(A[i * k + l], ei, beta, S, da + l, k);
-      split_value(B[l * n + j], fj, beta, S, db + l, k);
+      if (rn8) {
+        split_value_rn8(A[i * k + l], ei, S, da + l, k);
+        split_value_rn8(B[l * n + j], fj, S, db + l, k);
+      } else {
+        split_value(A[i * k + l], ei, beta, S, da + l, k);
+        split_value(B[l * n + j], fj, beta, S, db + l, k);
+      }
     }
     double acc = 0.0;
     for (int g = S + 1; g >= 2; --g) {
@@ -363,6 +421,18 @@ int oracle_ozaki_entries(const double* A, const double* B, int64_t m, int64_t k,
     free(da); free(db);
   }
   return bad ? ORACLE_NONFINITE : ORACLE_OK;
+}
+
+int oracle_ozaki_entries(const double* A, const double* B, int64_t m, int64_t k, int64_t n,
+                         int S, int beta, int64_t count, const int64_t* ii, const int64_t* jj,
+                         double* out) {
+  return ozaki_entries_any(A, B, m, k, n, S, beta, 0, count, ii, jj, out);
+}
+
+int oracle_ozaki_entries_rn8(const double* A, const double* B, int64_t m, int64_t k, int64_t n,
+                             int S, int64_t count, const int64_t* ii, const int64_t* jj,
+                             double* out) {
+  return ozaki_entries_any(A, B, m, k, n, S, 8, 1, count, ii, jj, out);
 }
 
 /* ------------------------------------------------------------------ */

@@ -73,11 +73,20 @@ MUTANTS = {
                             "    F[2 * p] = w[2 * p]; (void)r;\n    F[2 * p + 1] = w[2 * p + 1];"),
     "fft_complex_product": ("x1[1] = dr * s + di * c;", "x1[1] = dr * s - di * c;"),
     "dft_conjugated_term": ("im = im + (a * s + b * c);", "im = im + (a * s - b * c);"),
+    # the balanced 8-bit digit split; checked by tests/test_oracle_rn8_pins.py
+    "rn8_truncates": ("int64_t V = (int64_t)nearbyint(ldexp(x, 8 * S - e1));",
+                      "int64_t V = (int64_t)trunc(ldexp(x, 8 * S - e1));"),
+    "rn8_unbalanced_digits": ("const int64_t dig = r >= 128 ? r - 256 : r;",
+                              "const int64_t dig = r;"),
+    "rn8_no_exponent_offset": ("    for (int64_t i = 0; i < cnt; ++i) exps[i] += 1;",
+                               "    for (int64_t i = 0; i < cnt; ++i) exps[i] += 0;"),
+    "rn8_digit_order": ("    d[(s - 1) * stride] = (int16_t)dig;", "    d[(S - s) * stride] = (int16_t)dig;"),
 }
 PINS = {name: "test_oracle_spmv_pins.py" for name in MUTANTS if name.startswith("spmv_")}
 PINS.update({name: "test_oracle_cg_pins.py" for name in MUTANTS if name.startswith("cg_")})
 PINS.update({name: "test_oracle_fft_pins.py" for name in MUTANTS
              if name.startswith(("fft_", "dft_"))})
+PINS.update({name: "test_oracle_rn8_pins.py" for name in MUTANTS if name.startswith("rn8_")})
 
 
 def _compile(src_text, out_dir):
