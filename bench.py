@@ -323,7 +323,8 @@ def run_ours(args):
     modes = {}
     if rank == 0:
         S8 = default_slices(args.kind, 8)
-        for name, mode, s_, steps in (("emul_bf16digits", mxm.MODE_EMUL_BF16, S8, args.steps),):
+        for name, mode, s_, steps in (("emul_bf16digits", mxm.MODE_EMUL_BF16, S8, args.steps),
+                                      ("emul_rn8digits", mxm.MODE_EMUL_RN8, S8, args.steps)):
             for _ in range(2):
                 mxm.mxm_gemm(mode, A, B, C, slices=s_)
             torch.cuda.synchronize()
@@ -341,7 +342,9 @@ def run_ours(args):
             t = a0.elapsed_time(a1) / steps
             p_ = s_ * (s_ + 1) // 2
             gms = ph[2] / max(c_, 1)
-            modes[name] = {"slices": s_, "digit_bits": 8, "ms": round(t, 3),
+            modes[name] = {"slices": s_, "digit_bits": 8,
+                           "digits": "balanced, rounded to nearest" if mode == mxm.MODE_EMUL_RN8
+                           else "truncated", "ms": round(t, 3),
                            "tflops": round(flops / (t * 1e-3) / 1e12, 2),
                            "product_kernel_frac_of_bf16": round(
                                p_ * flops / (gms * 1e-3) / 1e12 / peak, 4)}

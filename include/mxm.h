@@ -58,7 +58,8 @@ typedef enum {
   MXM_MODE_EMUL_BF16 = 2,  /* Ozaki split, 8-bit digits (full BF16 significand) */
   MXM_MODE_F32 = 3,        /* comparison: inputs rounded to FP32, FP32 sums */
   MXM_MODE_BF16_F32ACC = 4, /* comparison: inputs rounded to BF16, FP32 sums */
-  MXM_MODE_EMUL_FP8 = 5    /* Ozaki split, 4-bit digits carried in FP8 E4M3 */
+  MXM_MODE_EMUL_FP8 = 5,   /* Ozaki split, 4-bit digits carried in FP8 E4M3 */
+  MXM_MODE_EMUL_RN8 = 6    /* Ozaki split rounded to nearest: balanced 8-bit digits in BF16 */
 } mxm_mode;
 
 /* One problem of a grouped call (device-resident table of these). */
@@ -110,7 +111,11 @@ mxm_status mxm_f64_emul(const double* A, const double* B, double* C, int64_t m, 
  * (|d| <= 15, exact in FP8 E4M3) on the FP8 tensor path, 1..16 slices, about
  * twice as many as the 7-bit form for the same accuracy, and returns
  * MXM_ERR_UNSUPPORTED when the per-diagonal sums would not fit int32
- * (S 225 k >= 2^31, i.e. k beyond ~600 000) -- it has no grouped form.  The
+ * (S 225 k >= 2^31, i.e. k beyond ~600 000) -- it has no grouped form.
+ * MXM_MODE_EMUL_RN8 rounds each value once to nearest on the grid of its
+ * last digit (scale exponent e + 1) and writes it in balanced 8-bit digits
+ * (|d| <= 128, exact in bf16): the accuracy of 8-bit digits with the long
+ * exact windows of 7-bit digits; 1..7 slices, no grouped form.  The
  * FP32 and BF16 modes round A and B to the narrow type and sum in FP32: they
  * are reported beside the FP64 modes, not FP64-accurate.
  */

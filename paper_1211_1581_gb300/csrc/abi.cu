@@ -140,14 +140,17 @@ mxm_status check_gemm_args(const double* A, const double* B, double* C, int64_t 
   return MXM_OK;
 }
 
-bool emul_mode(int mode) { return mode == MXM_MODE_EMUL_I8 || mode == MXM_MODE_EMUL_BF16; }
-int mode_beta(int mode) { return mode == MXM_MODE_EMUL_BF16 ? 8 : 7; }
+bool emul_mode(int mode) {
+  return mode == MXM_MODE_EMUL_I8 || mode == MXM_MODE_EMUL_BF16 || mode == MXM_MODE_EMUL_RN8;
+}
+int mode_beta(int mode) { return mode == MXM_MODE_EMUL_I8 ? 7 : 8; }
+bool mode_rn(int mode) { return mode == MXM_MODE_EMUL_RN8; }
 
 size_t workspace_bytes(int mode, int64_t m, int64_t k, int64_t n, int slices) {
   if (m <= 0 || n <= 0 || k <= 0) return 0;
   if (mode == MXM_MODE_F64) return f64_workspace(f64_dims(m, k, n));
   if (emul_mode(mode))
-    return ozaki_layout(ozaki_dims_splitk(m, k, n, slices, mode_beta(mode))).total;
+    return ozaki_layout(ozaki_dims_splitk(m, k, n, slices, mode_beta(mode), mode_rn(mode))).total;
   if (mode == MXM_MODE_EMUL_FP8) return ozaki_layout(ozaki_dims_fp8(m, k, n, slices)).total;
   if (mode == MXM_MODE_BF16_F32ACC) return ozaki_layout(ozaki_dims(m, k, n, 1, 8)).total;
   return 0;
@@ -168,7 +171,7 @@ mxm_status run_gemm(int mode, const double* A, const double* B, double* C, int64
     if (e == cudaSuccess) e = launch_f64_gemm(ws, C, d, status, s);
     profile_mark(ce, 3, s);
   } else if (emul_mode(mode)) {
-    const OzakiDims d = ozaki_dims_splitk(m, k, n, slices, mode_beta(mode));
+    const OzakiDims d = ozaki_dims_splitk(m, k, n, slices, mode_beta(mode), mode_rn(mode));
     const OzakiLayout L = ozaki_layout(d);
     uint64_t* rowbits = reinterpret_cast<uint64_t*>(ws + L.rowbits);
     uint64_t* colbits = reinterpret_cast<uint64_t*>(ws + L.colbits);
@@ -220,6 +223,8 @@ mxm_status run_gemm(int mode, const double* A, const double* B, double* C, int64
 
 mxm_status check_mode(int mode, int slices) {
   if (mode == MXM_MODE_F64 || mode == MXM_MODE_F32 || mode == MXM_MODE_BF16_F32ACC) return MXM_OK;
+  if (mode == MXM_MODE_EMUL_RN8)  // the rounded value 2^(8S-1) must fit int64
+    return (slices >= 1 && slices <= kOzMaxSlicesRn8) ? MXM_OK : MXM_ERR_UNSUPPORTED;
   if (emul_mode(mode)) return (slices >= 1 && slices <= kOzMaxSlices) ? MXM_OK : MXM_ERR_UNSUPPORTED;
   if (mode == MXM_MODE_EMUL_FP8)
     return (slices >= 1 && slices <= kOzMaxSlicesE4m3) ? MXM_OK : MXM_ERR_UNSUPPORTED;
@@ -327,9 +332,10 @@ static mxm_status gemm_host_panels(DeviceState* ds, int mode, const double* hA, 
                                    double* hC, int64_t m, int64_t k, int64_t n, int slices,
                                    int64_t h, cudaStream_t s) {
   const int beta = mode_beta(mode);
+  const bool rn = mode_rn(mode);
   const int64_t w = host_panel_cols(h, n, ds->sm_count);
   const int64_t P = (m + h - 1) / h, Q = (n + w - 1) / w;
-  const OzakiDims dp = ozaki_dims(h, k, w, slices, beta);  // the largest block, no split-k
+  const OzakiDims dp = ozaki_dims(h, k, w, slices, beta, rn);  // the largest block, no split-k
   const OzakiLayout L = ozaki_layout(dp);
   // per compute stream: row scales, A planes, running sums of one block
   const size_t rb_bytes = align_up(sizeof(uint64_t) * size_t(h), 1024);
@@ -407,7 +413,7 @@ static mxm_status gemm_host_panels(DeviceState* ds, int mode, const double* hA, 
     uint8_t* cw = cols + size_t(j) * per_col;
     uint64_t* colbits = reinterpret_cast<uint64_t*>(cw);
     uint8_t* bplanes = cw + (L.aslices - L.colbits);
-    const OzakiDims db = ozaki_dims(0, k, colw(j), slices, beta);
+    const OzakiDims db = ozaki_dims(0, k, colw(j), slices, beta, rn);
     if (cudaStreamWaitEvent(ds->c2, eBc[j], 0) != cudaSuccess ||
         launch_ozaki_scale(nullptr, dB + j * w * k, db, nullptr, colbits, ds->status, ds->c2) !=
             cudaSuccess ||
@@ -423,7 +429,7 @@ static mxm_status gemm_host_panels(DeviceState* ds, int mode, const double* hA, 
     uint64_t* rowbits = reinterpret_cast<uint64_t*>(buf);
     uint8_t* aplanes = buf + rb_bytes;
     uint64_t* sums = reinterpret_cast<uint64_t*>(buf + rb_bytes + ap_bytes);
-    const OzakiDims da = ozaki_dims(hp, k, 0, slices, beta);
+    const OzakiDims da = ozaki_dims(hp, k, 0, slices, beta, rn);
     if (cudaStreamWaitEvent(c, eA[i], 0) != cudaSuccess ||
         launch_ozaki_scale(dA + r0 * k, nullptr, da, rowbits, nullptr, ds->status, c) !=
             cudaSuccess ||
@@ -436,7 +442,7 @@ static mxm_status gemm_host_panels(DeviceState* ds, int mode, const double* hA, 
       const uint8_t* bplanes = cw + (L.aslices - L.colbits);
       const int64_t wj = colw(j);
       double* blk = dC + r0 * n + j * w * hp;  // h x wj, row-major, contiguous
-      const OzakiDims dg = ozaki_dims(hp, k, wj, slices, beta);
+      const OzakiDims dg = ozaki_dims(hp, k, wj, slices, beta, rn);
       cudaEvent_t done = eC[i * Q + j];
       if (cudaStreamWaitEvent(c, eBs[j], 0) != cudaSuccess ||
           launch_ozaki_gemm(aplanes, bplanes, rowbits, colbits, blk, dg, sums, ds->status, c) !=

@@ -61,6 +61,7 @@ constexpr int kOzMaxSlices = 12;
 // 16-byte chunk c (k = 16c .. 16c+15) of row r at chunk position c ^ (r % 8).
 constexpr int kOzTileBytesE4m3 = kOzTileRows * kOzTileK;
 constexpr int kOzMaxSlicesE4m3 = 16;
+constexpr int kOzMaxSlicesRn8 = 7;
 __host__ __device__ inline int oz_chunk_offset_e4m3(int r, int c) {
   return r * 128 + ((c ^ (r & 7)) << 4);
 }
@@ -71,9 +72,11 @@ struct OzakiDims {
   int S, beta;
   int64_t splits;      // k ranges per C tile (1: no split-k)
   int fp8;             // 1: digits carried in E4M3 (beta = 4), 0: in bf16
+  int rn;              // 1: balanced 8-bit digits, the value rounded once to
+                       //    nearest (beta = 8, scale exponent + 1, |d| <= 128)
 };
 
-inline OzakiDims ozaki_dims(int64_t m, int64_t k, int64_t n, int S, int beta) {
+inline OzakiDims ozaki_dims(int64_t m, int64_t k, int64_t n, int S, int beta, bool rn = false) {
   OzakiDims d;
   d.m = m; d.k = k; d.n = n;
   d.Mt = (m + kOzTileRows - 1) / kOzTileRows;
@@ -82,8 +85,12 @@ inline OzakiDims ozaki_dims(int64_t m, int64_t k, int64_t n, int S, int beta) {
   d.S = S; d.beta = beta;
   d.splits = 1;
   d.fp8 = 0;
+  d.rn = rn ? 1 : 0;
   return d;
 }
+
+// Largest digit magnitude of a split.
+inline int ozaki_dmax(const OzakiDims& d) { return d.rn ? 128 : (1 << d.beta) - 1; }
 
 // The 4-bit-digit E4M3 engine (paired kernel only: no split-k).
 inline OzakiDims ozaki_dims_fp8(int64_t m, int64_t k, int64_t n, int S) {
@@ -100,8 +107,9 @@ inline size_t ozaki_tile_bytes(const OzakiDims& d) {
 // k range at least 4 k-blocks of 128): the per-range digit-pair sums D_g
 // are exact integers, added exactly, so the result is bit-identical to the
 // unsplit product.
-inline OzakiDims ozaki_dims_splitk(int64_t m, int64_t k, int64_t n, int S, int beta) {
-  OzakiDims d = ozaki_dims(m, k, n, S, beta);
+inline OzakiDims ozaki_dims_splitk(int64_t m, int64_t k, int64_t n, int S, int beta,
+                                   bool rn = false) {
+  OzakiDims d = ozaki_dims(m, k, n, S, beta, rn);
   d.splits = splitk_count(d.Mt * d.Nt, d.Kt, 4);
   return d;
 }
@@ -123,6 +131,13 @@ __host__ __device__ inline bool ozaki_narrow(int S, int beta, int64_t Kt) {
          2147483647.0;
 }
 
+// The same for the dims of a product (the digit bound of its split).
+inline bool ozaki_narrow(const OzakiDims& d) {
+  const double dmax = static_cast<double>(d.rn ? 128 : (1 << d.beta) - 1);
+  return static_cast<double>(d.S) * dmax * dmax * kOzTileK * static_cast<double>(d.Kt) <
+         2147483647.0;
+}
+
 // CTAs of the paired slice GEMM that keep a spill area (the grid is capped
 // there when spills are on).
 constexpr int64_t kOzSpillCtas = 256;
@@ -139,7 +154,7 @@ inline size_t ozaki_sums_bytes(const OzakiDims& d) {
 // outgrow int32 over all of k (long k, 8-bit digits): per CTA the int64
 // partial sums of the two diagonals in work, 2 x 128 x 128 x 8 bytes.
 inline size_t ozaki_spill_bytes(const OzakiDims& d) {
-  if (d.fp8 || d.splits > 1 || ozaki_narrow(d.S, d.beta, d.Kt)) return 0;
+  if (d.fp8 || d.splits > 1 || ozaki_narrow(d)) return 0;
   const int64_t ctas = d.Mt * d.Nt < kOzSpillCtas ? d.Mt * d.Nt : kOzSpillCtas;
   return (size_t)ctas * 2 * kOzTileRows * kOzTileRows * 8;
 }
@@ -168,15 +183,17 @@ inline OzakiLayout ozaki_layout(const OzakiDims& d) {
 // FP32 accumulator without rounding: every product is at most (2^beta-1)^2
 // in magnitude and 16 of them enter per MMA, so the running sum stays within
 // 2^24 (all integers up to 2^24 are exact in FP32).
-inline int ozaki_window_mmas(int beta) {
-  const long long dmax = (1ll << beta) - 1;
+inline int ozaki_window_mmas(int beta, bool rn = false) {
+  const long long dmax = rn ? 128 : (1ll << beta) - 1;
   const long long per_mma = dmax * dmax * 16;
   return static_cast<int>((1ll << 24) / per_mma);
 }
 
 // The same bound in whole k-blocks (kOzTileK / 16 MMAs each), as the kernel
 // counts.
-inline int ozaki_window_stages(int beta) { return ozaki_window_mmas(beta) / (kOzTileK / 16); }
+inline int ozaki_window_stages(int beta, bool rn = false) {
+  return ozaki_window_mmas(beta, rn) / (kOzTileK / 16);
+}
 
 cudaError_t launch_ozaki_scale(const double* A, const double* B, const OzakiDims& d,
                                uint64_t* rowbits, uint64_t* colbits, int* status,

@@ -232,15 +232,69 @@ __device__ __forceinline__ void split_chunk_store_w64(const double (&x)[V], int 
   }
 }
 
+// Balanced 8-bit digits (the round-to-nearest split): with e1 = e + 1,
+// V = round(x 2^(8S - e1)) (ties to even; |V| <= 2^(8S-1), S <= 7), and the
+// digits of V in base 256 with every lower digit in [-128, 127] and the top
+// one in [-128, 128]: with W = V + sum_{i < S-1} 128 256^i, lower digit i is
+// byte i of W minus 128 and the top digit is W >> 8(S-1) (floor) -- the
+// same digits as taking V mod 256 in [-128, 127] from the bottom up.  Each
+// digit is an integer of at most 8 bits, exact in bf16.
+__device__ __forceinline__ void split_chunk_store_rn8(const double (&x)[8], int e1, int S,
+                                                      uint8_t* dst, size_t slice_stride) {
+  long long W[8];
+  const long long Boff =
+      S > 1 ? static_cast<long long>(0x8080808080808080ull >> (8 * (9 - S))) : 0ll;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x[j]));
+    const int be = static_cast<int>((b >> 52) & 0x7FF);
+    const uint64_t mant = b & 0x000FFFFFFFFFFFFFull;
+    const uint64_t M = be ? (mant | 0x0010000000000000ull) : mant;
+    const int sh = (be ? be - 1075 : -1074) - e1 + 8 * S;  // x 2^(8S - e1) = M 2^sh
+    uint64_t q;
+    if (sh >= 0) {
+      q = M << sh;  // |x 2^(8S - e1)| < 2^(8S-1) <= 2^55: no bit leaves the word
+    } else if (-sh >= 64) {
+      q = 0;        // M < 2^53 <= half of 2^64: rounds to 0
+    } else {
+      const int nsh = -sh;
+      q = M >> nsh;
+      const uint64_t rem = M & ((1ull << nsh) - 1ull), half = 1ull << (nsh - 1);
+      if (rem > half || (rem == half && (q & 1ull))) ++q;
+    }
+    const long long V = (b >> 63) ? -static_cast<long long>(q) : static_cast<long long>(q);
+    W[j] = V + Boff;
+  }
+  for (int s = 1; s <= S; ++s) {
+    const int p = 8 * (S - s);
+    uint32_t packed[4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      uint32_t bits2[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int dg = s == 1 ? static_cast<int>(W[j + h] >> p)
+                              : static_cast<int>((W[j + h] >> p) & 255) - 128;
+        bits2[h] = dg ? (__float_as_uint(__int2float_rn(dg)) >> 16) : 0u;
+      }
+      packed[j >> 1] = bits2[0] | (bits2[1] << 16);
+    }
+    *reinterpret_cast<uint4*>(dst + static_cast<size_t>(s - 1) * slice_stride) =
+        make_uint4(packed[0], packed[1], packed[2], packed[3]);
+  }
+}
+
 __device__ __forceinline__ void split_chunk(const double (&x)[8], int e, int S, int beta,
-                                            uint8_t* dst, size_t slice_stride) {
-  if (beta * S <= 64)
+                                            uint8_t* dst, size_t slice_stride, bool rn = false) {
+  if (rn)
+    split_chunk_store_rn8(x, e + 1, S, dst, slice_stride);
+  else if (beta * S <= 64)
     split_chunk_store_w64<8>(x, e, S, beta, dst, slice_stride);
   else
     split_chunk_store(x, e, S, beta, dst, slice_stride);
 }
 __device__ __forceinline__ void split_chunk(const double (&x)[16], int e, int S, int beta,
-                                            uint8_t* dst, size_t slice_stride) {
+                                            uint8_t* dst, size_t slice_stride, bool = false) {
   split_chunk_store_w64<16>(x, e, S, beta, dst, slice_stride);  // beta = 4, S <= 16
 }
 
@@ -262,7 +316,7 @@ template <int V>
 __device__ __forceinline__ void split_a_tile(const double* __restrict__ A, int64_t m, int64_t k,
                                              const uint64_t* __restrict__ rowbits, int S,
                                              int beta, int64_t tm, int64_t tk, uint8_t* tile,
-                                             size_t slice_stride) {
+                                             size_t slice_stride, bool rn = false) {
   using G = SplitGeo<V>;
   const bool pairs = ((k & 1) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
 #pragma unroll 2
@@ -285,7 +339,7 @@ __device__ __forceinline__ void split_a_tile(const double* __restrict__ A, int64
 #pragma unroll
       for (int j = 0; j < V; ++j) v[j] = (row < m && k0 + j < k) ? __ldg(src + j) : 0.0;
     }
-    split_chunk(v, e, S, beta, tile + G::offset(r, c), slice_stride);
+    split_chunk(v, e, S, beta, tile + G::offset(r, c), slice_stride, rn);
   }
 }
 
@@ -299,7 +353,7 @@ __device__ __forceinline__ void split_b_tile(const double* __restrict__ B, int64
                                              const uint64_t* __restrict__ colbits, int S,
                                              int beta, int64_t tn, int64_t tk, uint8_t* tile,
                                              size_t slice_stride,
-                                             double (*sb)[kOzTileRows + 1]) {
+                                             double (*sb)[kOzTileRows + 1], bool rn = false) {
   using G = SplitGeo<V>;
   const int64_t col0 = tn * kOzTileRows;
   for (int pass = 0; pass < kOzTileK / kSplitBRows; ++pass) {
@@ -318,7 +372,7 @@ __device__ __forceinline__ void split_b_tile(const double* __restrict__ B, int64
       double v[V];
 #pragma unroll
       for (int j = 0; j < V; ++j) v[j] = sb[cl * V + j][r];
-      split_chunk(v, f, S, beta, tile + G::offset(r, pass * kChunks + cl), slice_stride);
+      split_chunk(v, f, S, beta, tile + G::offset(r, pass * kChunks + cl), slice_stride, rn);
     }
     __syncthreads();
   }
@@ -328,25 +382,25 @@ __device__ __forceinline__ void split_b_tile(const double* __restrict__ B, int64
 template <int V>
 __global__ void __launch_bounds__(256) oz_split_a_kernel(
     const double* __restrict__ A, int64_t m, int64_t k, const uint64_t* __restrict__ rowbits,
-    int S, int beta, int64_t Mt, int64_t Kt, uint8_t* __restrict__ aslices) {
+    int S, int beta, int64_t Mt, int64_t Kt, uint8_t* __restrict__ aslices, bool rn) {
   constexpr size_t kTile = SplitGeo<V>::kTileBytes;
   const int64_t tk = blockIdx.x, tm = blockIdx.y;
   split_a_tile<V>(A, m, k, rowbits, S, beta, tm, tk,
                   aslices + (static_cast<size_t>(tm) * Kt + tk) * kTile,
-                  static_cast<size_t>(Mt) * Kt * kTile);
+                  static_cast<size_t>(Mt) * Kt * kTile, rn);
 }
 
 // B -> B_t tiles [S][Nt][Kt].
 template <int V>
 __global__ void __launch_bounds__(256) oz_split_b_kernel(
     const double* __restrict__ B, int64_t k, int64_t n, const uint64_t* __restrict__ colbits,
-    int S, int beta, int64_t Nt, int64_t Kt, uint8_t* __restrict__ bslices) {
+    int S, int beta, int64_t Nt, int64_t Kt, uint8_t* __restrict__ bslices, bool rn) {
   constexpr size_t kTile = SplitGeo<V>::kTileBytes;
   __shared__ double sb[kSplitBRows][kOzTileRows + 1];
   const int64_t tk = blockIdx.x, tn = blockIdx.y;
   split_b_tile<V>(B, k, n, colbits, S, beta, tn, tk,
                   bslices + (static_cast<size_t>(tn) * Kt + tk) * kTile,
-                  static_cast<size_t>(Nt) * Kt * kTile, sb);
+                  static_cast<size_t>(Nt) * Kt * kTile, sb, rn);
 }
 
 // ---------------------------------------------------------------- grouped steps 1-2
@@ -577,6 +631,7 @@ struct OzSingle {
   int64_t tile_bytes; // operand tile size of the digit carrier
   long long* spill = nullptr;  // paired kernel: per-CTA int64 partials of the two diagonals
   int spill_every = 0;         // window drains after which a diagonal's int32 sum spills
+  int eoff = 0;                // added to e_i + f_j in the final scaling (2: balanced digits)
   __device__ __forceinline__ int64_t count() const { return Mt * Nt * splits; }
   // Unit t: C tile t / splits, k range t % splits.
   __device__ __forceinline__ OzTile tile(int64_t t) const {
@@ -1371,7 +1426,8 @@ __global__ void __launch_bounds__(kP2Threads, 1)
               const int64_t col = cbase + i;
               if (row_ok && col < j.n)
                 j.C[row * j.n + col] =
-                    final_scale(cur[i], er + exponent_from_absbits(__ldg(j.colbits + col)));
+                    final_scale(cur[i], er + exponent_from_absbits(__ldg(j.colbits + col)) +
+                                            tiles.eoff);
             }
           } else {
 #pragma unroll
@@ -1433,19 +1489,19 @@ cudaError_t launch_ozaki_split(const double* A, const double* B, const OzakiDims
     dim3 grid(static_cast<unsigned>(d.Kt), static_cast<unsigned>(d.Mt));
     if (d.fp8)
       oz_split_a_kernel<16><<<grid, 256, 0, s>>>(A, d.m, d.k, rowbits, d.S, d.beta, d.Mt, d.Kt,
-                                                 aslices);
+                                                 aslices, false);
     else
       oz_split_a_kernel<8><<<grid, 256, 0, s>>>(A, d.m, d.k, rowbits, d.S, d.beta, d.Mt, d.Kt,
-                                                aslices);
+                                                aslices, d.rn != 0);
   }
   if (d.Nt > 0) {
     dim3 grid(static_cast<unsigned>(d.Kt), static_cast<unsigned>(d.Nt));
     if (d.fp8)
       oz_split_b_kernel<16><<<grid, 256, 0, s>>>(B, d.k, d.n, colbits, d.S, d.beta, d.Nt, d.Kt,
-                                                 bslices);
+                                                 bslices, false);
     else
       oz_split_b_kernel<8><<<grid, 256, 0, s>>>(B, d.k, d.n, colbits, d.S, d.beta, d.Nt, d.Kt,
-                                                bslices);
+                                                bslices, d.rn != 0);
   }
   return cudaGetLastError();
 }
@@ -1484,7 +1540,7 @@ static cudaError_t launch_oz_gemm_t(const Tiles& tiles, int64_t grid, int S, int
 __global__ void __launch_bounds__(256) oz_splitk_fold_kernel(
     const uint64_t* __restrict__ P, const uint64_t* __restrict__ rowbits,
     const uint64_t* __restrict__ colbits, double* __restrict__ C, int64_t m, int64_t n,
-    int64_t Mt, int64_t Nt, int64_t Kt, int64_t splits, int S, int beta) {
+    int64_t Mt, int64_t Nt, int64_t Kt, int64_t splits, int S, int beta, int eoff) {
   const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= m * n) return;
   const int64_t col = idx / m, row = idx - (idx / m) * m;
@@ -1501,8 +1557,8 @@ __global__ void __launch_bounds__(256) oz_splitk_fold_kernel(
     for (int64_t sp = 0; sp < splits; ++sp) dval += static_cast<long long>(__ldcs(q + sp * range_stride));
     st = fold_step(st, dval, g, gx, S, beta);
   }
-  C[row * n + col] =
-      final_scale(st, exponent_from_absbits(rowbits[row]) + exponent_from_absbits(colbits[col]));
+  C[row * n + col] = final_scale(
+      st, exponent_from_absbits(rowbits[row]) + exponent_from_absbits(colbits[col]) + eoff);
 }
 
 
@@ -1510,7 +1566,7 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
                               const uint64_t* rowbits, const uint64_t* colbits, double* C,
                               const OzakiDims& d, uint64_t* sums, int* status, cudaStream_t s) {
   if (d.Mt == 0 || d.Nt == 0) return cudaSuccess;
-  const int window = ozaki_window_stages(d.beta);
+  const int window = ozaki_window_stages(d.beta, d.rn != 0);
   const int64_t splits = d.splits > 1 ? d.splits : 1;
   OzSingle tiles{aslices, bslices, rowbits, colbits, C,      d.m, d.n,
                  d.Mt,    d.Nt,    d.Kt,    sums,    splits, d.S,
@@ -1536,14 +1592,16 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
     if (e != cudaSuccess) return e;
     const int64_t total = d.m * d.n;
     oz_splitk_fold_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
-        sums, rowbits, colbits, C, d.m, d.n, d.Mt, d.Nt, d.Kt, splits, d.S, d.beta);
+        sums, rowbits, colbits, C, d.m, d.n, d.Mt, d.Nt, d.Kt, splits, d.S, d.beta,
+        d.rn ? 2 : 0);
     return cudaGetLastError();
   }
   // the paired kernel; when a diagonal's sum over all of k may pass int32,
   // with the spill area that follows the running sums (grid capped to it)
   int64_t g2 = grid;
-  if (!ozaki_narrow(d.S, d.beta, d.Kt)) {
-    const double dmax = static_cast<double>((1 << d.beta) - 1);
+  tiles.eoff = d.rn ? 2 : 0;
+  if (!ozaki_narrow(d)) {
+    const double dmax = static_cast<double>(ozaki_dmax(d));
     const double per_drain = static_cast<double>(window) * kOzTileK * dmax * dmax;
     tiles.spill_every = static_cast<int>(2147483647.0 / per_drain);
     if (tiles.spill_every < 1) return cudaErrorNotSupported;

@@ -31,6 +31,7 @@ MODE_EMUL_BF16 = 2
 MODE_F32 = 3
 MODE_BF16_F32ACC = 4
 MODE_EMUL_FP8 = 5
+MODE_EMUL_RN8 = 6
 
 # Every symbol include/mxm.h declares, with (restype, argtypes).
 _P = ctypes.c_void_p

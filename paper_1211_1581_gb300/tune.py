@@ -3,7 +3,8 @@
 Several engines compute C = A.B (Sec. 3.1) to FP64 accuracy: the native
 FP64 tensor path (DMMA) and the Ozaki split (Ozaki, Ogita, Oishi, Rump 2012;
 integer-slice form of Ootomo, Ozaki, Yokota 2024) with S slices of 7-bit
-digits (MODE_EMUL_I8) or 8-bit digits (MODE_EMUL_BF16) on the bf16 tensor
+digits (MODE_EMUL_I8), 8-bit digits (MODE_EMUL_BF16) or balanced 8-bit
+digits of the value rounded to nearest (MODE_EMUL_RN8) on the bf16 tensor
 pipe, or of 4-bit digits on the FP8 tensor pipe (MODE_EMUL_FP8).  The cost of the split grows as S(S+1)/2 digit products;
 the slice count needed for FP64 accuracy depends on the data: a term
 a_il b_lj far below the row / column maxima 2^{e_i}, 2^{f_j} loses its low
@@ -38,9 +39,11 @@ from . import mxm
 U = 2.0 ** -53
 REFERENCE = (mxm.MODE_EMUL_BF16, 12)
 MODE_NAMES = {mxm.MODE_F64: "f64", mxm.MODE_EMUL_I8: "emul_i8", mxm.MODE_EMUL_BF16: "emul_bf16",
-              mxm.MODE_EMUL_FP8: "emul_fp8"}
-MAX_SLICES = {mxm.MODE_EMUL_I8: 12, mxm.MODE_EMUL_BF16: 12, mxm.MODE_EMUL_FP8: 16}
-ENGINES = (mxm.MODE_F64, mxm.MODE_EMUL_I8, mxm.MODE_EMUL_BF16, mxm.MODE_EMUL_FP8)
+              mxm.MODE_EMUL_FP8: "emul_fp8", mxm.MODE_EMUL_RN8: "emul_rn8"}
+MAX_SLICES = {mxm.MODE_EMUL_I8: 12, mxm.MODE_EMUL_BF16: 12, mxm.MODE_EMUL_FP8: 16,
+              mxm.MODE_EMUL_RN8: 7}
+ENGINES = (mxm.MODE_F64, mxm.MODE_EMUL_I8, mxm.MODE_EMUL_BF16, mxm.MODE_EMUL_FP8,
+           mxm.MODE_EMUL_RN8)
 
 
 @dataclass

@@ -21,11 +21,13 @@ def fake_measure(need, cost, calls):
 
 def test_select_fastest_accurate():
     calls = []
-    m = fake_measure({mxm.MODE_EMUL_I8: 7, mxm.MODE_EMUL_BF16: 6, mxm.MODE_EMUL_FP8: 13},
+    m = fake_measure({mxm.MODE_EMUL_I8: 7, mxm.MODE_EMUL_BF16: 6, mxm.MODE_EMUL_FP8: 13,
+                      mxm.MODE_EMUL_RN8: 6},
                      {mxm.MODE_F64: 100.0, mxm.MODE_EMUL_I8: 1.0, mxm.MODE_EMUL_BF16: 1.5,
-                      mxm.MODE_EMUL_FP8: 0.6}, calls)
+                      mxm.MODE_EMUL_FP8: 0.6, mxm.MODE_EMUL_RN8: 1.4}, calls)
     c = tune.select(m, tol=1.0)
-    # i8: 28 pairs x 1.0 = 28; bf16: 21 pairs x 1.5 = 31.5; fp8: 91 x 0.6 = 54.6; f64 100
+    # i8: 28 pairs x 1.0 = 28; bf16: 21 x 1.5 = 31.5; fp8: 91 x 0.6 = 54.6; rn8: 21 x 1.4 =
+    # 29.4; f64 100
     assert (c.mode, c.slices, c.ms) == (mxm.MODE_EMUL_I8, 7, 28.0)
     # each emulated scan stopped at its first accurate count
     assert [s for (mo, s) in calls if mo == mxm.MODE_EMUL_I8] == list(range(1, 8))
@@ -35,17 +37,19 @@ def test_select_fastest_accurate():
 
 def test_select_native_wins_when_faster():
     calls = []
-    m = fake_measure({mxm.MODE_EMUL_I8: 9, mxm.MODE_EMUL_BF16: 8, mxm.MODE_EMUL_FP8: 16},
+    m = fake_measure({mxm.MODE_EMUL_I8: 9, mxm.MODE_EMUL_BF16: 8, mxm.MODE_EMUL_FP8: 16,
+                      mxm.MODE_EMUL_RN8: 7},
                      {mxm.MODE_F64: 20.0, mxm.MODE_EMUL_I8: 1.0, mxm.MODE_EMUL_BF16: 1.0,
-                      mxm.MODE_EMUL_FP8: 1.0}, calls)
+                      mxm.MODE_EMUL_FP8: 1.0, mxm.MODE_EMUL_RN8: 1.0}, calls)
     c = tune.select(m, tol=1.0)
     assert (c.mode, c.slices) == (mxm.MODE_F64, 0) and c.name == "f64"
 
 
 def test_select_tolerance_moves_the_count():
-    m = fake_measure({mxm.MODE_EMUL_I8: 7, mxm.MODE_EMUL_BF16: 6, mxm.MODE_EMUL_FP8: 14},
+    m = fake_measure({mxm.MODE_EMUL_I8: 7, mxm.MODE_EMUL_BF16: 6, mxm.MODE_EMUL_FP8: 14,
+                      mxm.MODE_EMUL_RN8: 6},
                      {mxm.MODE_F64: 1e9, mxm.MODE_EMUL_I8: 1.0, mxm.MODE_EMUL_BF16: 9.0,
-                      mxm.MODE_EMUL_FP8: 9.0}, [])
+                      mxm.MODE_EMUL_FP8: 9.0, mxm.MODE_EMUL_RN8: 9.0}, [])
     assert tune.select(m, tol=1.0).slices == 7
     assert tune.select(m, tol=2.0 ** 7).slices == 6  # one slice fewer is 2^7 worse
 
@@ -67,6 +71,7 @@ def test_select_scans_each_engine_to_its_own_limit():
         tune.select(never, tol=1.0)
     assert max(s for mo, s in calls if mo == mxm.MODE_EMUL_I8) == 12
     assert max(s for mo, s in calls if mo == mxm.MODE_EMUL_FP8) == 16
+    assert max(s for mo, s in calls if mo == mxm.MODE_EMUL_RN8) == 7
 
 
 def test_shape_class_and_key():
