@@ -463,7 +463,8 @@ def run_suite(args):
     stream = torch.cuda.current_stream()
     peaks, _ = load_peaks()
     names = {mxm.MODE_F64: "f64", mxm.MODE_EMUL_I8: "emul_i8", mxm.MODE_EMUL_BF16: "emul_bf16",
-             mxm.MODE_F32: "f32", mxm.MODE_BF16_F32ACC: "bf16_f32acc", mxm.MODE_EMUL_FP8: "emul_fp8"}
+             mxm.MODE_F32: "f32", mxm.MODE_BF16_F32ACC: "bf16_f32acc", mxm.MODE_EMUL_FP8: "emul_fp8",
+             mxm.MODE_EMUL_RN8: "emul_rn8"}
 
     def emit(**d):
         print(json.dumps(dict(suite=True, **d)), flush=True)
@@ -510,6 +511,7 @@ def run_suite(args):
     for n in (4096, 8192):
         runs = ([(mxm.MODE_EMUL_I8, S) for S in range(5, 10)] +
                 [(mxm.MODE_EMUL_BF16, S) for S in range(4, 9)] +
+                [(mxm.MODE_EMUL_RN8, S) for S in range(4, 8)] +
                 [(mxm.MODE_EMUL_FP8, S) for S in range(11, 17)] +
                 [(mxm.MODE_F32, 0), (mxm.MODE_BF16_F32ACC, 0), (mxm.MODE_F64, 0)])
         one("emul_slices", "spread", n, n, n, runs, reps=3 if n == 4096 else 2)
