@@ -300,6 +300,7 @@ def run_ours(args):
     roofline = {"bound": "tensor", "kernel": "oz_gemm2_kernel", "achieved": round(achieved, 1),
                 "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                 "peak_source": f"bf16_tflops_sustained of {peak_src} (MEASURED_PEAKS.json)",
+                "frac_of_burst_peak": round(achieved / peaks.get("bf16_tflops", peak), 4),
                 "traffic": profiled_traffic() if (n == 8192 and S == 7) else None,
                 "traffic_unit": "bytes per launch (dram read + write, ncu)",
                 "algorithmic": f"{pairs} digit-pair products x 2mnk bf16 flops per launch",
@@ -534,11 +535,12 @@ def run_suite(args):
     rng = np.random.default_rng(6)
     sample = sorted(set(by_k[:3] + by_k[-2:] + list(rng.choice(len(dims), 8, replace=False))))
     s_i8 = tune.grouped_slices([(ds[p][0], ds[p][1]) for p in sample], mxm.MODE_EMUL_I8)
+    s_rn8 = tune.grouped_slices([(ds[p][0], ds[p][1]) for p in sample], mxm.MODE_EMUL_RN8)
     table_h = mxm.problem_table(ds)
     table_d = table_h.cuda()
     check = np.random.default_rng(5).choice(len(dims), 24, replace=False)
     refs = [tune.accuracy_reference(ds[p][0], ds[p][1], stream) for p in check]
-    for mode, S in ((mxm.MODE_F64, 0), (mxm.MODE_EMUL_I8, s_i8)):
+    for mode, S in ((mxm.MODE_F64, 0), (mxm.MODE_EMUL_I8, s_i8), (mxm.MODE_EMUL_RN8, s_rn8)):
         ws = torch.empty(max(1, mxm.mxm_grouped_workspace_size(table_h, mode, S)),
                          dtype=torch.uint8, device="cuda")
         side = torch.cuda.Stream()

@@ -159,7 +159,7 @@ mxm_status mxm_grouped_workspace_size(int64_t count, const mxm_problem* h_proble
 /*
  * mxm_grouped -- `count` independent products C_p = A_p.B_p of uneven sizes
  * in one persistent launch sequence, from a DEVICE-resident table of
- * mxm_problem.  mode is MXM_MODE_F64 or MXM_MODE_EMUL_I8 / _BF16.  d_ws is
+ * mxm_problem.  mode is MXM_MODE_F64 or MXM_MODE_EMUL_I8 / _BF16 / _RN8.  d_ws is
  * caller workspace of ws_bytes (see mxm_grouped_workspace_size); the call
  * allocates nothing and synchronises nothing, so it can be captured in a
  * CUDA graph.  Tile offsets are computed on the device; a table that needs

@@ -156,6 +156,7 @@ bool grouped_mode_ok(int mode, int slices) {
   if (mode == MXM_MODE_F64) return true;
   if (mode == MXM_MODE_EMUL_I8 || mode == MXM_MODE_EMUL_BF16)
     return slices >= 1 && slices <= kOzMaxSlices;
+  if (mode == MXM_MODE_EMUL_RN8) return slices >= 1 && slices <= kOzMaxSlicesRn8;
   return false;
 }
 
@@ -237,6 +238,7 @@ extern "C" mxm_status mxm_grouped(int64_t count, const mxm_problem* d_problems, 
   if (mode == MXM_MODE_F64)
     e = launch_f64_grouped(ws, status, s);
   else
-    e = launch_ozaki_grouped(ws, slices, mode == MXM_MODE_EMUL_BF16 ? 8 : 7, 0, status, s);
+    e = launch_ozaki_grouped(ws, slices, mode == MXM_MODE_EMUL_I8 ? 7 : 8, 0, status, s,
+                             mode == MXM_MODE_EMUL_RN8);
   return e == cudaSuccess ? MXM_OK : MXM_ERR_CUDA;
 }

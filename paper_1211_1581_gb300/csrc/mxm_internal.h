@@ -305,7 +305,7 @@ __device__ __forceinline__ int64_t grouped_find(const Rec* recs, int64_t count, 
 cudaError_t launch_grouped_plan(const void* table, int64_t count, int emul, int S,
                                 size_t ws_bytes, uint8_t* ws, int* status, cudaStream_t s);
 cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t max_kt, int* status,
-                                 cudaStream_t s);
+                                 cudaStream_t s, bool rn = false);
 cudaError_t launch_f64_grouped(uint8_t* ws, int* status, cudaStream_t s);
 int sm_count();
 

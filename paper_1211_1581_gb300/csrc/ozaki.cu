@@ -482,7 +482,7 @@ __global__ void oz_grouped_colmax_kernel(const uint8_t* __restrict__ ws, int* __
 }
 
 __global__ void __launch_bounds__(256) oz_grouped_split_kernel(uint8_t* __restrict__ ws, int S,
-                                                               int beta) {
+                                                               int beta, bool rn) {
   const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
   if (!hdr->valid) return;
   const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
@@ -496,14 +496,14 @@ __global__ void __launch_bounds__(256) oz_grouped_split_kernel(uint8_t* __restri
       const int64_t local = t - p.atile_begin;
       split_a_tile<8>(p.A, p.m, p.k, rowbits + p.row_begin, S, beta, local / p.Kt, local % p.Kt,
                    ws + hdr->off_a + static_cast<size_t>(t) * kOzTileBytes,
-                   static_cast<size_t>(na) * kOzTileBytes);
+                   static_cast<size_t>(na) * kOzTileBytes, rn);
     } else {
       const int64_t tb = t - na;
       const GroupedProblem& p = recs[grouped_find(recs, hdr->count, tb, &GroupedProblem::btile_begin)];
       const int64_t local = tb - p.btile_begin;
       split_b_tile<8>(p.B, p.k, p.n, colbits + p.col_begin, S, beta, local / p.Kt, local % p.Kt,
                    ws + hdr->off_b + static_cast<size_t>(tb) * kOzTileBytes,
-                   static_cast<size_t>(nb) * kOzTileBytes, sb);
+                   static_cast<size_t>(nb) * kOzTileBytes, sb, rn);
     }
   }
 }
@@ -615,6 +615,7 @@ struct OzTile {
   int64_t row0, col0;        // origin of the tile in C
   uint64_t* sums;            // 128 x 128 running sums, column-major (paired kernel)
   uint64_t* partial;         // split-k: this range's D_g, [S - 1 diagonals][128 x 128]
+  int eoff;                  // added to e_i + f_j in the final scaling (2: balanced digits)
 };
 
 // Tiles of one product.
@@ -652,6 +653,7 @@ struct OzSingle {
     j.n = n;
     j.row0 = tm * kOzTileRows;
     j.col0 = tn * kOzTileRows;
+    j.eoff = eoff;
     const size_t tile_words = kOzTileRows * kOzTileRows;
     if (splits > 1) {
       j.sums = nullptr;
@@ -671,6 +673,7 @@ struct OzGrouped {
   const GroupedHeader* hdr;
   const GroupedProblem* recs;
   const uint8_t* ws;
+  int eoff;  // 2 for balanced 8-bit digits
   __device__ __forceinline__ int64_t count() const { return hdr->valid ? hdr->tiles : 0; }
   __device__ __forceinline__ OzTile tile(int64_t t) const {
     const int64_t p = grouped_find(recs, hdr->count, t, &GroupedProblem::tile_begin);
@@ -692,6 +695,7 @@ struct OzGrouped {
     j.col0 = tn * kOzTileRows;
     j.sums = nullptr;
     j.partial = nullptr;
+    j.eoff = eoff;
     return j;
   }
 };
@@ -986,7 +990,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                   if constexpr (kFloat)
                     crow[col] = __longlong_as_double(static_cast<long long>(st[i]));
                   else
-                    crow[col] = final_scale(st[i], er + exponent_from_absbits(j.colbits[col]));
+                    crow[col] =
+                        final_scale(st[i], er + exponent_from_absbits(j.colbits[col]) + j.eoff);
                 }
               }
             }
@@ -1427,7 +1432,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
               if (row_ok && col < j.n)
                 j.C[row * j.n + col] =
                     final_scale(cur[i], er + exponent_from_absbits(__ldg(j.colbits + col)) +
-                                            tiles.eoff);
+                                            j.eoff);
             }
           } else {
 #pragma unroll
@@ -1571,6 +1576,7 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
   OzSingle tiles{aslices, bslices, rowbits, colbits, C,      d.m, d.n,
                  d.Mt,    d.Nt,    d.Kt,    sums,    splits, d.S,
                  static_cast<int64_t>(ozaki_tile_bytes(d))};
+  tiles.eoff = d.rn ? 2 : 0;
   const int64_t count = d.Mt * d.Nt * splits;
   const int64_t grid = count < sm_count() ? count : sm_count();
   if (d.fp8) {
@@ -1599,7 +1605,6 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
   // the paired kernel; when a diagonal's sum over all of k may pass int32,
   // with the spill area that follows the running sums (grid capped to it)
   int64_t g2 = grid;
-  tiles.eoff = d.rn ? 2 : 0;
   if (!ozaki_narrow(d)) {
     const double dmax = static_cast<double>(ozaki_dmax(d));
     const double per_drain = static_cast<double>(window) * kOzTileK * dmax * dmax;
@@ -1620,18 +1625,18 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
 }
 
 cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t /*max_kt*/, int* status,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, bool rn) {
   const int sms = sm_count();
   oz_grouped_rowmax_kernel<<<sms * 4, 256, 0, s>>>(ws, status);
   oz_grouped_colmax_kernel<<<sms * 4, 256, 0, s>>>(ws, status);
-  oz_grouped_split_kernel<<<sms * 8, 256, 0, s>>>(ws, S, beta);
+  oz_grouped_split_kernel<<<sms * 8, 256, 0, s>>>(ws, S, beta, rn);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
   const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
-  OzGrouped tiles{hdr, recs, ws};
+  OzGrouped tiles{hdr, recs, ws, rn ? 2 : 0};
   // the host does not see the table: 64-bit running sums are safe for any k
-  return launch_oz_gemm_t<long long, false>(tiles, sms, S, beta, ozaki_window_stages(beta),
+  return launch_oz_gemm_t<long long, false>(tiles, sms, S, beta, ozaki_window_stages(beta, rn),
                                             status, s);
 }
 

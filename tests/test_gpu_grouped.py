@@ -52,7 +52,7 @@ DIMS = [(1, 1, 1), (17, 5, 33), (128, 64, 128), (129, 65, 131), (300, 200, 257),
 
 @pytest.mark.parametrize("graph", [False, True])
 @pytest.mark.parametrize("mode,S", [(mxm.MODE_EMUL_I8, 7), (mxm.MODE_EMUL_BF16, 6),
-                                    (mxm.MODE_F64, 0)])
+                                    (mxm.MODE_EMUL_RN8, 6), (mxm.MODE_F64, 0)])
 def test_grouped_matches_oracle(mode, S, graph):
     hs, ds = make_group(DIMS, kind="spread" if mode != mxm.MODE_F64 else "uniform")
     assert run_group(ds, mode, S, graph=graph) == mxm.MXM_OK
@@ -61,6 +61,9 @@ def test_grouped_matches_oracle(mode, S, graph):
         if mode == mxm.MODE_F64:
             assert_within_bound(got, oracle.gemm_dot2(A, B), oracle.gemm_abs(A, B), A.shape[1],
                                 f"grouped f64 {A.shape}x{B.shape}")
+        elif mode == mxm.MODE_EMUL_RN8:
+            assert_bitwise(got, oracle.ozaki_gemm_rn8(A, B, S),
+                           f"grouped rn8 {A.shape}x{B.shape}")
         else:
             beta = 8 if mode == mxm.MODE_EMUL_BF16 else 7
             assert_bitwise(got, oracle.ozaki_gemm(A, B, S=S, beta=beta),
