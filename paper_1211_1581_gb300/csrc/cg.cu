@@ -8,7 +8,11 @@
 // owns the rows [c n / C, (c + 1) n / C); every CTA keeps the whole search
 // direction p in its shared memory (two buffers), so the sparse product
 // gathers p from shared memory, and its own rows of q, r and x there too
-// (x goes to global memory once, after the loop).  One step:
+// (x goes to global memory once, after the loop).  The CTA's rows of A are
+// copied to shared memory at the start when the rest of it holds them, so
+// that every later product streams them from there rather than from L2
+// (the same values in the same order: the rounding does not change).
+// One step:
 //
 //   1. q = A p on the CTA's rows (lane groups of G as in the mod2as kernel);
 //      the CTA's share of (p, q) goes to slot c of every CTA's table
@@ -36,6 +40,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "mxm.h"
 #include "mxm_internal.h"
@@ -140,6 +145,7 @@ struct CgArgs {
   double* x;
   int64_t n, nnz;
   int64_t rows_cap;  // ceil(n / C): own rows of q, r, x in shared memory
+  int64_t nnz_cap;   // values of the CTA's rows that fit the shared-memory copy (0: none)
   double stop;
   int32_t max_iters;
   int32_t* iters_out;  // device, 1
@@ -161,6 +167,11 @@ __global__ void __launch_bounds__(kCgThreads, 1) cg_cluster_kernel(const CgArgs 
   double* const qs = dsm + 2 * n;
   double* const rs = qs + a.rows_cap;
   double* const xs = rs + a.rows_cap;
+  // the CTA's rows of A, copied once when they fit: the product of every
+  // step then reads shared memory instead of L2
+  double* const mvals = xs + a.rows_cap;
+  int32_t* const mindx = reinterpret_cast<int32_t*>(mvals + a.nnz_cap);
+  int32_t* const mrowp = mindx + a.nnz_cap;
   const uint32_t rank = cluster_rank(), C = cluster_size();
   const int64_t lo = static_cast<int64_t>(rank) * n / C;
   const int64_t hi = static_cast<int64_t>(rank + 1) * n / C;
@@ -168,6 +179,18 @@ __global__ void __launch_bounds__(kCgThreads, 1) cg_cluster_kernel(const CgArgs 
   const int active = own < kCgThreads ? static_cast<int>(own) : kCgThreads;  // threads with rows
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int sub = lane & (G - 1), grp = lane / G;
+  const int64_t jb = __ldg(a.rowp + lo), je = __ldg(a.rowp + hi);
+  const bool cached = a.nnz_cap > 0 && jb >= 0 && je >= jb && je <= a.nnz && je - jb <= a.nnz_cap;
+  if (cached) {  // the same for all threads of the CTA
+    for (int64_t i = tid; i <= own; i += kCgThreads) {
+      const int64_t v = static_cast<int64_t>(__ldg(a.rowp + lo + i)) - jb;
+      mrowp[i] = static_cast<int32_t>(v < 0 ? -1 : (v > je - jb ? je - jb + 1 : v));
+    }
+    for (int64_t j = tid; j < je - jb; j += kCgThreads) {
+      mvals[j] = __ldg(a.vals + jb + j);
+      mindx[j] = __ldg(a.indx + jb + j);
+    }
+  }
 
   // x0 = 0, r0 = b on the own rows; p0 = b everywhere; r2 = (b, b), summed
   // by every CTA over all n in the same order
@@ -195,42 +218,60 @@ __global__ void __launch_bounds__(kCgThreads, 1) cg_cluster_kernel(const CgArgs 
     const double* p = dsm + cur * n;
     double* pn = dsm + (cur ^ 1) * n;
     // 1. q = A p on the own rows, then the CTA's share of (p, q)
-    for (int64_t base = lo + static_cast<int64_t>(warp) * kRowsPerWarp; base < hi;
-         base += static_cast<int64_t>(kCgWarps) * kRowsPerWarp) {
-      const int64_t row = base + grp;
-      int64_t rb = 0, re = 0;
-      if (row < hi) {
-        rb = __ldg(a.rowp + row);
-        re = __ldg(a.rowp + row + 1);
-        if (rb < 0 || re < rb || re > a.nnz) {
-          bad = true;
-          re = rb;
+    auto product = [&](auto in_smem) {
+      constexpr bool kSm = decltype(in_smem)::value;
+      const int64_t lim = kSm ? je - jb : a.nnz;
+      for (int64_t base = lo + static_cast<int64_t>(warp) * kRowsPerWarp; base < hi;
+           base += static_cast<int64_t>(kCgWarps) * kRowsPerWarp) {
+        const int64_t row = base + grp;
+        int64_t rb = 0, re = 0;
+        if (row < hi) {
+          if constexpr (kSm) {
+            rb = mrowp[row - lo];
+            re = mrowp[row - lo + 1];
+          } else {
+            rb = __ldg(a.rowp + row);
+            re = __ldg(a.rowp + row + 1);
+          }
+          if (rb < 0 || re < rb || re > lim) {
+            bad = true;
+            re = rb;
+          }
         }
+        // kCgBatch values per lane per round (positions j0, j0 + G, ...):
+        // the loads first, so that many are in flight, then the fused
+        // multiply-adds in storage order
+        double t = 0.0;
+        for (int64_t j0 = rb + sub; j0 < re; j0 += G * kCgBatch) {
+          int32_t c[kCgBatch];
+          double v[kCgBatch];
+#pragma unroll
+          for (int u = 0; u < kCgBatch; ++u) {
+            const int64_t j = j0 + static_cast<int64_t>(u) * G;
+            if constexpr (kSm) {
+              c[u] = j < re ? mindx[j] : -1;
+              v[u] = j < re ? mvals[j] : 0.0;
+            } else {
+              c[u] = j < re ? __ldg(a.indx + j) : -1;
+              v[u] = j < re ? __ldg(a.vals + j) : 0.0;
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kCgBatch; ++u) {
+            const bool ok = c[u] >= 0 && c[u] < n;
+            bad |= !ok && j0 + static_cast<int64_t>(u) * G < re;
+            if (ok) t = fma(v[u], p[c[u]], t);
+          }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+        if (row < hi && sub == 0) qs[row - lo] = t;
       }
-      // kCgBatch values per lane per round (positions j0, j0 + G, ...):
-      // the loads first, so that the matrix streams from L2 with many
-      // loads in flight, then the fused multiply-adds in storage order
-      double t = 0.0;
-      for (int64_t j0 = rb + sub; j0 < re; j0 += G * kCgBatch) {
-        int32_t c[kCgBatch];
-        double v[kCgBatch];
-#pragma unroll
-        for (int u = 0; u < kCgBatch; ++u) {
-          const int64_t j = j0 + static_cast<int64_t>(u) * G;
-          c[u] = j < re ? __ldg(a.indx + j) : -1;
-          v[u] = j < re ? __ldg(a.vals + j) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < kCgBatch; ++u) {
-          const bool ok = c[u] >= 0 && c[u] < n;
-          bad |= !ok && j0 + static_cast<int64_t>(u) * G < re;
-          if (ok) t = fma(v[u], p[c[u]], t);
-        }
-      }
-#pragma unroll
-      for (int o = G / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
-      if (row < hi && sub == 0) qs[row - lo] = t;
-    }
+    };
+    if (cached)
+      product(std::true_type{});
+    else
+      product(std::false_type{});
     __syncthreads();
     double pq = 0.0;
     for (int64_t i = tid; i < own; i += kCgThreads) pq = fma(p[lo + i], qs[i], pq);
@@ -292,17 +333,38 @@ __global__ void __launch_bounds__(kCgThreads, 1) cg_cluster_kernel(const CgArgs 
   cluster_barrier();  // no CTA leaves while a peer may still address its shared memory
 }
 
-// Dynamic shared memory of a cluster of C for order n.
-size_t cg_smem_bytes(int64_t n, int C) {
+// Dynamic shared memory of a CTA of a cluster of C for order n: p twice, q,
+// r and x of the own rows, then (nnz_cap > 0) the copy of the CTA's rows of
+// A: nnz_cap values and columns and the rows' pointers.
+size_t cg_smem_bytes(int64_t n, int C, int64_t nnz_cap) {
   const int64_t rows_cap = (n + C - 1) / C;
-  return static_cast<size_t>(2 * n + 3 * rows_cap) * sizeof(double);
+  size_t bytes = static_cast<size_t>(2 * n + 3 * rows_cap) * sizeof(double);
+  if (nnz_cap > 0)
+    bytes += static_cast<size_t>(nnz_cap) * (sizeof(double) + sizeof(int32_t)) +
+             static_cast<size_t>(rows_cap + 1) * sizeof(int32_t);
+  return bytes;
 }
 
 template <int G>
 cudaError_t launch_cg_g(CgArgs a, int C, cudaStream_t s) {
-  const size_t smem = cg_smem_bytes(a.n, C);
+  // the copy of A takes what shared memory is left, up to the whole matrix;
+  // a CTA whose rows hold more values reads them from L2 instead
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, cg_cluster_kernel<G>);
+  if (e != cudaSuccess) return e;
   a.rows_cap = (a.n + C - 1) / C;
-  cudaError_t e = cudaFuncSetAttribute(cg_cluster_kernel<G>,
+  const int64_t room = static_cast<int64_t>(optin) - static_cast<int64_t>(fa.sharedSizeBytes) -
+                       static_cast<int64_t>(cg_smem_bytes(a.n, C, 0)) -
+                       (a.rows_cap + 1) * static_cast<int64_t>(sizeof(int32_t));
+  a.nnz_cap = room > 0 ? room / static_cast<int64_t>(sizeof(double) + sizeof(int32_t)) : 0;
+  if (a.nnz_cap > a.nnz) a.nnz_cap = a.nnz;
+  const size_t smem = cg_smem_bytes(a.n, C, a.nnz_cap);
+  e = cudaFuncSetAttribute(cg_cluster_kernel<G>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
@@ -440,6 +502,7 @@ extern "C" mxm_status mxm_cg(const double* matvals, const int32_t* indx, const i
   a.x = x;
   a.n = n;
   a.rows_cap = n;
+  a.nnz_cap = 0;
   a.nnz = nnz;
   a.stop = stop;
   a.max_iters = max_iters;

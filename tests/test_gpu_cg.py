@@ -130,6 +130,32 @@ def test_sizes_and_cluster_shapes(n, bw):
     compare(rowp, indx, vals, b, 1e-22 * float(b @ b), 200, bw)
 
 
+def test_rows_partly_held_in_shared_memory():
+    """At the largest order the shared memory left over holds a diagonal
+    block of 768 rows but not a tridiagonal one: the CTA owning the first
+    768 rows (tridiagonal there) streams its rows from global memory while
+    the 15 others use their copies; the solve is the oracle's all the same.
+    The diagonal is random in [2, 8) (distinct eigenvalues: with only a few
+    distinct ones the late residuals of any two summation orders drift
+    apart beyond the tolerance)."""
+    n, head = 12288, 768
+    d = 5.0 + 3.0 * inputs.uniform_pm1(15, 107, (n,))
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        for j in (i - 1, i, i + 1):
+            if j == i:
+                rows.append(i), cols.append(j), vals.append(d[i] + (2.0 if i < head else 0.0))
+            elif i < head and 0 <= j < head:
+                rows.append(i), cols.append(j), vals.append(-1.0)
+    rowp = np.zeros(n + 1, dtype=np.int32)
+    np.add.at(rowp, np.asarray(rows) + 1, 1)
+    rowp = np.cumsum(rowp).astype(np.int32)
+    indx, vals = np.asarray(cols, dtype=np.int32), np.asarray(vals)
+    b = inputs.uniform_pm1(15, 106, (n,))
+    got, _ = compare(rowp, indx, vals, b, 1e-24 * float(b @ b), 500, 1)
+    assert got["iters"] > 5
+
+
 @pytest.mark.parametrize("engine", ENGINES)
 def test_fixed_step_counts_and_edges(engine):
     n, bw = 700, 31
