@@ -413,7 +413,8 @@ static mxm_status gemm_host_panels(DeviceState* ds, int mode, const double* hA, 
     uint8_t* cw = cols + size_t(j) * per_col;
     uint64_t* colbits = reinterpret_cast<uint64_t*>(cw);
     uint8_t* bplanes = cw + (L.aslices - L.colbits);
-    const OzakiDims db = ozaki_dims(0, k, colw(j), slices, beta, rn);
+    OzakiDims db = ozaki_dims(0, k, colw(j), slices, beta, rn);
+    db.pair = dp.pair;  // every block's product reads these B planes
     if (cudaStreamWaitEvent(ds->c2, eBc[j], 0) != cudaSuccess ||
         launch_ozaki_scale(nullptr, dB + j * w * k, db, nullptr, colbits, ds->status, ds->c2) !=
             cudaSuccess ||
@@ -429,7 +430,8 @@ static mxm_status gemm_host_panels(DeviceState* ds, int mode, const double* hA, 
     uint64_t* rowbits = reinterpret_cast<uint64_t*>(buf);
     uint8_t* aplanes = buf + rb_bytes;
     uint64_t* sums = reinterpret_cast<uint64_t*>(buf + rb_bytes + ap_bytes);
-    const OzakiDims da = ozaki_dims(hp, k, 0, slices, beta, rn);
+    OzakiDims da = ozaki_dims(hp, k, 0, slices, beta, rn);
+    da.pair = dp.pair;
     if (cudaStreamWaitEvent(c, eA[i], 0) != cudaSuccess ||
         launch_ozaki_scale(dA + r0 * k, nullptr, da, rowbits, nullptr, ds->status, c) !=
             cudaSuccess ||
@@ -442,7 +444,8 @@ static mxm_status gemm_host_panels(DeviceState* ds, int mode, const double* hA, 
       const uint8_t* bplanes = cw + (L.aslices - L.colbits);
       const int64_t wj = colw(j);
       double* blk = dC + r0 * n + j * w * hp;  // h x wj, row-major, contiguous
-      const OzakiDims dg = ozaki_dims(hp, k, wj, slices, beta, rn);
+      OzakiDims dg = ozaki_dims(hp, k, wj, slices, beta, rn);
+      dg.pair = dp.pair;
       cudaEvent_t done = eC[i * Q + j];
       if (cudaStreamWaitEvent(c, eBs[j], 0) != cudaSuccess ||
           launch_ozaki_gemm(aplanes, bplanes, rowbits, colbits, blk, dg, sums, ds->status, c) !=

@@ -55,6 +55,16 @@ __host__ __device__ inline int oz_chunk_offset(int r, int c) {
 }
 constexpr int kOzMaxSlices = 12;
 
+// B tiles for the CTA-pair product (cta_group::2, M = 256): the tile's rows
+// (columns of B) in two halves of 64, each half contiguous (16 KiB: its two
+// atoms along k of 64 rows x 128 bytes, 8 KiB each), so that each CTA of a
+// pair fetches its half with one bulk copy.  Same swizzle: chunk c of row r
+// at chunk position c ^ (r % 8).
+__host__ __device__ inline int oz_chunk_offset_halves(int r, int c) {
+  return (r >> 6) * (kOzTileBytes / 2) + (c >> 3) * (kOzAtomBytes / 2) + (r & 63) * 128 +
+         (((c & 7) ^ (r & 7)) << 4);
+}
+
 // The 4-bit-digit engine: digits |d| <= 15 carried in FP8 E4M3 (every
 // integer up to 16 is exact there) through tcgen05 kind::f8f6f4.  A tile is
 // 128 rows x 128 k of one byte: a single 128-byte-swizzle atom of 16 KiB, the
@@ -74,6 +84,8 @@ struct OzakiDims {
   int fp8;             // 1: digits carried in E4M3 (beta = 4), 0: in bf16
   int rn;              // 1: balanced 8-bit digits, the value rounded once to
                        //    nearest (beta = 8, scale exponent + 1, |d| <= 128)
+  int pair;            // 1: the slice GEMM runs on CTA pairs (cta_group::2) and
+                       //    the B digit tiles are written in the halves layout
 };
 
 inline OzakiDims ozaki_dims(int64_t m, int64_t k, int64_t n, int S, int beta, bool rn = false) {
@@ -86,6 +98,7 @@ inline OzakiDims ozaki_dims(int64_t m, int64_t k, int64_t n, int S, int beta, bo
   d.splits = 1;
   d.fp8 = 0;
   d.rn = rn ? 1 : 0;
+  d.pair = d.Mt >= 2 ? 1 : 0;
   return d;
 }
 
@@ -96,6 +109,7 @@ inline int ozaki_dmax(const OzakiDims& d) { return d.rn ? 128 : (1 << d.beta) - 
 inline OzakiDims ozaki_dims_fp8(int64_t m, int64_t k, int64_t n, int S) {
   OzakiDims d = ozaki_dims(m, k, n, S, 4);
   d.fp8 = 1;
+  d.pair = 0;
   return d;
 }
 
@@ -111,7 +125,18 @@ inline OzakiDims ozaki_dims_splitk(int64_t m, int64_t k, int64_t n, int S, int b
                                    bool rn = false) {
   OzakiDims d = ozaki_dims(m, k, n, S, beta, rn);
   d.splits = splitk_count(d.Mt * d.Nt, d.Kt, 4);
+  if (d.splits > 1) d.pair = 0;
   return d;
+}
+
+// Whether the B digit tiles are written in the halves layout above, and
+// whether the paired slice GEMM runs on CTA pairs (cta_group::2, 256-row C
+// tiles): bf16 digits without split-k, chosen where the dims are made (two
+// or more tile-rows of A; products that share B planes share the choice,
+// a single tile-row then leaving the second CTA of its pairs idle).
+inline bool ozaki_b_halves(const OzakiDims& d) { return d.pair != 0 && !d.fp8; }
+inline bool ozaki_cta2(const OzakiDims& d) {
+  return ozaki_b_halves(d) && d.splits <= 1 && d.Mt >= 1;
 }
 
 // Workspace layout of one emulated product (offsets in bytes, 1 KiB aligned).

@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "mxm_internal.h"
 #include "ptx.cuh"
@@ -353,7 +354,8 @@ __device__ __forceinline__ void split_b_tile(const double* __restrict__ B, int64
                                              const uint64_t* __restrict__ colbits, int S,
                                              int beta, int64_t tn, int64_t tk, uint8_t* tile,
                                              size_t slice_stride,
-                                             double (*sb)[kOzTileRows + 1], bool rn = false) {
+                                             double (*sb)[kOzTileRows + 1], bool rn = false,
+                                             bool halves = false) {
   using G = SplitGeo<V>;
   const int64_t col0 = tn * kOzTileRows;
   for (int pass = 0; pass < kOzTileK / kSplitBRows; ++pass) {
@@ -372,7 +374,9 @@ __device__ __forceinline__ void split_b_tile(const double* __restrict__ B, int64
       double v[V];
 #pragma unroll
       for (int j = 0; j < V; ++j) v[j] = sb[cl * V + j][r];
-      split_chunk(v, f, S, beta, tile + G::offset(r, pass * kChunks + cl), slice_stride, rn);
+      const int c = pass * kChunks + cl;
+      const int off = (V == 8 && halves) ? oz_chunk_offset_halves(r, c) : G::offset(r, c);
+      split_chunk(v, f, S, beta, tile + off, slice_stride, rn);
     }
     __syncthreads();
   }
@@ -390,17 +394,18 @@ __global__ void __launch_bounds__(256) oz_split_a_kernel(
                   static_cast<size_t>(Mt) * Kt * kTile, rn);
 }
 
-// B -> B_t tiles [S][Nt][Kt].
+// B -> B_t tiles [S][Nt][Kt]; halves: the CTA-pair layout of each tile.
 template <int V>
 __global__ void __launch_bounds__(256) oz_split_b_kernel(
     const double* __restrict__ B, int64_t k, int64_t n, const uint64_t* __restrict__ colbits,
-    int S, int beta, int64_t Nt, int64_t Kt, uint8_t* __restrict__ bslices, bool rn) {
+    int S, int beta, int64_t Nt, int64_t Kt, uint8_t* __restrict__ bslices, bool rn,
+    bool halves) {
   constexpr size_t kTile = SplitGeo<V>::kTileBytes;
   __shared__ double sb[kSplitBRows][kOzTileRows + 1];
   const int64_t tk = blockIdx.x, tn = blockIdx.y;
   split_b_tile<V>(B, k, n, colbits, S, beta, tn, tk,
                   bslices + (static_cast<size_t>(tn) * Kt + tk) * kTile,
-                  static_cast<size_t>(Nt) * Kt * kTile, sb, rn);
+                  static_cast<size_t>(Nt) * Kt * kTile, sb, rn, halves);
 }
 
 // ---------------------------------------------------------------- grouped steps 1-2
@@ -639,6 +644,19 @@ struct OzSingle {
     const int64_t tt = t / splits, sp = t - tt * splits;
     int64_t tm, tn;
     tile_coords(tt, Mt, Nt, tm, tn);
+    return tile_at(tm, tn, sp);
+  }
+  // CTA pairs (no split-k): unit t is the 256 x 128 C tile of tile-rows
+  // 2 tp, 2 tp + 1; CTA `rank` of the pair takes tile-row 2 tp + rank, which
+  // lies past the last one (row0 >= m: nothing to load or store) when Mt is
+  // odd.
+  __device__ __forceinline__ int64_t pair_count() const { return (Mt + 1) / 2 * Nt; }
+  __device__ __forceinline__ OzTile pair_tile(int64_t t, uint32_t rank) const {
+    int64_t tp, tn;
+    tile_coords(t, (Mt + 1) / 2, Nt, tp, tn);
+    return tile_at(2 * tp + rank, tn, 0);
+  }
+  __device__ __forceinline__ OzTile tile_at(int64_t tm, int64_t tn, int64_t sp) const {
     const int64_t kb0 = Kt * sp / splits, kb1 = Kt * (sp + 1) / splits;
     OzTile j;
     j.a_slice = static_cast<size_t>(Mt) * Kt * tile_bytes;
@@ -737,6 +755,35 @@ __device__ __noinline__ uint64_t fold_step(uint64_t st, long long dval, int g, i
   const double acc = __longlong_as_double(static_cast<long long>(st));
   const double term = i64_times_pow2(dval, -beta * g);  // exact
   return static_cast<uint64_t>(__double_as_longlong(__dadd_rn(acc, term)));
+}
+
+// The kind of a diagonal's fold step: exact int64 partial while g > gx, the
+// last exact step and the conversion to FP64 at g == gx, an FP64 addition
+// below.  fold_kind is fold_step with the kind fixed by the caller (inline:
+// the paired kernel folds 8 elements at a time with one kind per diagonal
+// pair, straight-line code); on the first diagonal st is 0.
+constexpr int kFoldInt = 0, kFoldConv = 1, kFoldFp = 2, kFoldNone = 3;
+__device__ __forceinline__ int fold_kind_of(int g, int gx) {
+  return g > gx ? kFoldInt : (g == gx ? kFoldConv : kFoldFp);
+}
+template <int K>
+__device__ __forceinline__ uint64_t fold_kind(uint64_t st, long long d, int g, int S, int beta) {
+  if constexpr (K == kFoldFp) {
+    const double acc = __longlong_as_double(static_cast<long long>(st));
+    return static_cast<uint64_t>(
+        __double_as_longlong(__dadd_rn(acc, i64_times_pow2(d, -beta * g))));  // term exact
+  } else {
+    const long long y = static_cast<long long>(st) + d * (1ll << (beta * (S + 1 - g)));
+    if constexpr (K == kFoldConv)
+      return static_cast<uint64_t>(__double_as_longlong(i64_times_pow2(y, -beta * (S + 1))));
+    else
+      return static_cast<uint64_t>(y);
+  }
+}
+
+// Bring the line holding p into this SM's L1 ahead of a load.
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
 // Register split of the 384-thread slice GEMMs (setmaxnreg acts per
@@ -1038,25 +1085,47 @@ constexpr int kP2Threads = 384;
 // carried in E4M3: 16 KiB tiles (one 128-k atom), 4 MMAs of K = 32, rings
 // twice as deep in the same shared memory.
 struct FmtBf16 {
-  static constexpr int kTileBytes = kOzTileBytes;
+  static constexpr bool kPair = false;
+  static constexpr int kTileBytes = kOzTileBytes, kBTileBytes = kOzTileBytes;
   static constexpr int kMmas = 8;
   static constexpr int kRingA = 3, kRingB = 4;
   __device__ static uint32_t idesc() { return idesc_bf16_f32(128, kOzTileRows); }
   __device__ static uint64_t koff(int kk) {  // k step kk: atom kk / 4, 32 bytes per step inside it
     return static_cast<uint64_t>((kk >> 2) * (kOzAtomBytes >> 4) + (kk & 3) * 2);
   }
+  __device__ static uint64_t kboff(int kk) { return koff(kk); }
   __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     mma_bf16_ss(d, a, b, idesc, acc);
   }
 };
 struct FmtE4m3 {
-  static constexpr int kTileBytes = kOzTileBytesE4m3;
+  static constexpr bool kPair = false;
+  static constexpr int kTileBytes = kOzTileBytesE4m3, kBTileBytes = kOzTileBytesE4m3;
   static constexpr int kMmas = 4;
   static constexpr int kRingA = 6, kRingB = 8;
   __device__ static uint32_t idesc() { return idesc_e4m3_f32(128, kOzTileRows); }
   __device__ static uint64_t koff(int kk) { return static_cast<uint64_t>(kk * 2); }
+  __device__ static uint64_t kboff(int kk) { return koff(kk); }
   __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     mma_e4m3_ss(d, a, b, idesc, acc);
+  }
+};
+// Digits carried in bf16 on a CTA pair (cta_group::2): 256 x 128 C tiles,
+// each CTA with its own 128-row A tile (32 KiB) and one 64-row half of the B
+// tile (16 KiB: two 8 KiB atoms along k), so an SM takes in 48 KiB per step
+// instead of 64 for the same MMA work.  Rings of 4 A tiles and 6 B halves.
+struct FmtBf16Pair {
+  static constexpr bool kPair = true;
+  static constexpr int kTileBytes = kOzTileBytes, kBTileBytes = kOzTileBytes / 2;
+  static constexpr int kMmas = 8;
+  static constexpr int kRingA = 4, kRingB = 6;
+  __device__ static uint32_t idesc() { return idesc_bf16_f32(256, kOzTileRows); }
+  __device__ static uint64_t koff(int kk) { return FmtBf16::koff(kk); }
+  __device__ static uint64_t kboff(int kk) {  // B half: atoms of 64 rows, 8 KiB apart
+    return static_cast<uint64_t>((kk >> 2) * ((kOzAtomBytes / 2) >> 4) + (kk & 3) * 2);
+  }
+  __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    mma_bf16_ss_pair(d, a, b, idesc, acc);
   }
 };
 constexpr int kP2EpiWarps = 8;
@@ -1064,7 +1133,7 @@ constexpr int kP2EpiWarps = 8;
 template <typename Fmt>
 struct __align__(1024) Gemm2Smem {
   uint8_t a[Fmt::kRingA][Fmt::kTileBytes];
-  uint8_t b[Fmt::kRingB][Fmt::kTileBytes];
+  uint8_t b[Fmt::kRingB][Fmt::kBTileBytes];
   uint64_t a_full[Fmt::kRingA], a_empty[Fmt::kRingA];
   uint64_t b_full[Fmt::kRingB], b_empty[Fmt::kRingB];
   uint64_t accfull[4], accempty[4];  // accumulator 2x + buffer; x = 0: diagonal g, 1: g-1
@@ -1091,42 +1160,71 @@ struct Ring {
 // The fold of one diagonal g into a running sum held as 64 bits: an exact
 // int64 partial (units of 2^{-beta (S+1)}) while g >= gx, an FP64 value after.
 // kSpill: long k, a diagonal's int32 sums spill to an int64 area (below).
+//
+// kPair (FmtBf16Pair): the kernel runs on clusters of two CTAs, one per SM,
+// with the MMAs of cta_group::2.  Both CTAs copy their operand tiles (rank
+// r: A of tile-row 2 tp + r, half r of the B tile) and run the epilogue of
+// their own 128 rows; rank 0's two issuers issue every MMA.  A tile is ready
+// for rank 0 when its own copy has landed and rank 1 (warp 1, the relay)
+// has seen its copy land and arrived on rank 0's full barrier; MMA commits
+// arrive in both CTAs (multicast) and free the slots and windows there;
+// rank 1's epilogue warps arrive on rank 0's window barriers.
 template <typename Tiles, typename Fmt, bool kSpill = false>
 __global__ void __launch_bounds__(kP2Threads, 1)
     oz_gemm2_kernel(const Tiles tiles, int S, int beta, int window, int* __restrict__ status) {
   constexpr int kRingA = Fmt::kRingA, kRingB = Fmt::kRingB, kTile = Fmt::kTileBytes;
+  constexpr int kBTile = Fmt::kBTileBytes;
+  constexpr bool kPair = Fmt::kPair;
   extern __shared__ uint8_t smem_raw[];
   Gemm2Smem<Fmt>& sm = *reinterpret_cast<Gemm2Smem<Fmt>*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  const uint32_t rank = kPair ? cluster_cta_rank() : 0u;
+  const bool leader = rank == 0;
 
   if (threadIdx.x == 0) {
+    const uint32_t full_count = (kPair && leader) ? 2 : 1;  // + the relay's arrival
     for (int i = 0; i < kRingA; ++i) {
-      mbar_init(&sm.a_full[i], 1);
+      mbar_init(&sm.a_full[i], full_count);
       mbar_init(&sm.a_empty[i], 2);  // one arrival per MMA issuer
     }
     for (int i = 0; i < kRingB; ++i) {
-      mbar_init(&sm.b_full[i], 1);
+      mbar_init(&sm.b_full[i], full_count);
       mbar_init(&sm.b_empty[i], 2);
     }
     for (int i = 0; i < 4; ++i) {
       mbar_init(&sm.accfull[i], 1);
-      mbar_init(&sm.accempty[i], kP2EpiWarps);
+      mbar_init(&sm.accempty[i], kPair ? 2 * kP2EpiWarps : kP2EpiWarps);
     }
     sm.abort_flag = 0;
     fence_mbar_init();
   }
+  if constexpr (kPair) cluster_sync_all();  // barriers initialised before any peer arrives
   if (warp == 1) {
-    tmem_alloc(&sm.tmem_base, kTmemCols);
-    tmem_relinquish();
+    if constexpr (kPair) {
+      tmem_alloc_pair(&sm.tmem_base, kTmemCols);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(&sm.tmem_base, kTmemCols);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sm.tmem_base;
   volatile int* abort_flag = &sm.abort_flag;
-  const int64_t ntiles = tiles.count();
+  // work units: C tiles, or (pairs) 256-row C tiles shared by the cluster
+  const int64_t nunits = kPair ? tiles.pair_count() : tiles.count();
+  const int64_t unit0 = kPair ? (blockIdx.x >> 1) : blockIdx.x;
+  const int64_t unit_step = kPair ? (gridDim.x >> 1) : gridDim.x;
+  auto unit_tile = [&](int64_t t) {
+    if constexpr (kPair)
+      return tiles.pair_tile(t, rank);
+    else
+      return tiles.tile(t);
+  };
   const int ngroups = (S + 1) / 2;
 
   if (warp < 4) {
@@ -1136,25 +1234,37 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       Ring<kRingA> ra;
       Ring<kRingB> rb;
       bool ok = true;
-      auto load = [&](auto& r, uint8_t (*buf)[Fmt::kTileBytes], uint64_t* full, uint64_t* empty,
-                      const uint8_t* src) {
-        if (!mbar_wait_bounded(&empty[r.slot], r.phase ^ 1u, abort_flag, status)) return false;
-        mbar_arrive_expect_tx(&full[r.slot], kTile);
-        bulk_g2s(buf[r.slot], src, kTile, &full[r.slot]);
+      // src == nullptr: nothing to copy (rank 1 past the last tile-row); the
+      // slot is marked full all the same
+      auto load = [&](auto& r, auto buf, uint64_t* full, uint64_t* empty, const uint8_t* src,
+                      uint32_t bytes) {
+        if (!mbar_wait_bounded(&empty[r.slot], r.phase ^ 1u, abort_flag, status))
+          return false;
+        if (src != nullptr) {
+          mbar_arrive_expect_tx(&full[r.slot], bytes);
+          bulk_g2s(buf[r.slot], src, bytes, &full[r.slot]);
+        } else {
+          mbar_arrive(&full[r.slot]);
+        }
         r.advance();
         return true;
       };
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const OzTile j = tiles.tile(t);
+      for (int64_t t = unit0; t < nunits && ok; t += unit_step) {
+        const OzTile j = unit_tile(t);
+        const bool live = !kPair || j.row0 < j.m;
+        const size_t bhalf = kPair ? static_cast<size_t>(rank) * kBTile : 0;
         for (int q = 0; q < ngroups && ok; ++q) {
           const int g = S + 1 - 2 * q;
           for (int64_t kb = 0; kb < j.Kt && ok; ++kb) {
             const size_t koff = static_cast<size_t>(kb) * kTile;
-            ok = load(rb, sm.b, sm.b_full, sm.b_empty, j.b + (g - 2) * j.b_slice + koff);
+            ok = load(rb, sm.b, sm.b_full, sm.b_empty, j.b + (g - 2) * j.b_slice + koff + bhalf,
+                      kBTile);
             for (int s = 1; s <= g - 1 && ok; ++s) {
-              ok = load(ra, sm.a, sm.a_full, sm.a_empty, j.a + (s - 1) * j.a_slice + koff);
+              ok = load(ra, sm.a, sm.a_full, sm.a_empty,
+                        live ? j.a + (s - 1) * j.a_slice + koff : nullptr, kTile);
               if (ok && s <= g - 2)
-                ok = load(rb, sm.b, sm.b_full, sm.b_empty, j.b + (g - 2 - s) * j.b_slice + koff);
+                ok = load(rb, sm.b, sm.b_full, sm.b_empty,
+                          j.b + (g - 2 - s) * j.b_slice + koff + bhalf, kBTile);
             }
           }
         }
@@ -1162,14 +1272,42 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       // tail: wait until every slot is released so no copy or commit lands
       // after the block has exited
       for (int i = 0; i < kRingA; ++i) {
-        if (!mbar_wait_bounded(&sm.a_empty[ra.slot], ra.phase ^ 1u, abort_flag, status)) break;
+        if (!mbar_wait_bounded(&sm.a_empty[ra.slot], ra.phase ^ 1u, abort_flag, status))
+          break;
         ra.advance();
       }
       for (int i = 0; i < kRingB; ++i) {
-        if (!mbar_wait_bounded(&sm.b_empty[rb.slot], rb.phase ^ 1u, abort_flag, status)) break;
+        if (!mbar_wait_bounded(&sm.b_empty[rb.slot], rb.phase ^ 1u, abort_flag, status))
+          break;
         rb.advance();
       }
-    } else if ((warp == 1 || warp == 2) && lane == 0) {
+    } else if (kPair && !leader && warp == 1 && lane == 0) {
+      // ------------------------------------------------ relay (rank 1)
+      // Walks the producer's sequence: when a tile of this CTA has landed,
+      // arrive on the same slot's full barrier of rank 0.
+      Ring<kRingA> ra;
+      Ring<kRingB> rb;
+      bool ok = true;
+      auto relay = [&](auto& r, uint64_t* full) {
+        if (!mbar_wait_bounded(&full[r.slot], r.phase, abort_flag, status)) return false;
+        mbar_arrive_cluster(smem_in_cta(&full[r.slot], 0));
+        r.advance();
+        return true;
+      };
+      for (int64_t t = unit0; t < nunits && ok; t += unit_step) {
+        const int64_t Kt = unit_tile(t).Kt;
+        for (int q = 0; q < ngroups && ok; ++q) {
+          const int g = S + 1 - 2 * q;
+          for (int64_t kb = 0; kb < Kt && ok; ++kb) {
+            ok = relay(rb, sm.b_full);
+            for (int s = 1; s <= g - 1 && ok; ++s) {
+              ok = relay(ra, sm.a_full);
+              if (ok && s <= g - 2) ok = relay(rb, sm.b_full);
+            }
+          }
+        }
+      }
+    } else if ((warp == 1 || warp == 2) && lane == 0 && leader) {
       // ------------------------------------------------ MMA issuers
       // Two issuing threads: warp 1 issues the products of diagonal g (its
       // accumulators 0/1), warp 2 those of diagonal g-1 (accumulators 2/3).
@@ -1177,7 +1315,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       // core retires them; two interleave and keep it busy.  Both walk the
       // same stage sequence; every ring slot is released by two arrivals,
       // one per issuer (a commit after its MMAs, or a plain arrival for a
-      // tile it does not read).
+      // tile it does not read).  On a pair both go to both CTAs.
       const int x = warp - 1;
       const uint32_t idesc = Fmt::idesc();
       const uint64_t adesc0 = sw128_kmajor_desc(smem_u32(sm.a[0]));
@@ -1188,11 +1326,22 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       bool acq = false;
       uint32_t uses0 = 0u, uses1 = 0u;  // windows started in this issuer's two buffers
       bool ok = true;
+      auto commit = [&](uint64_t* bar) {
+        if constexpr (kPair)
+          mma_commit_pair(bar, static_cast<uint16_t>(0x3));
+        else
+          mma_commit(bar);
+      };
+      auto release = [&](uint64_t* bar) {
+        mbar_arrive(bar);
+        if constexpr (kPair) mbar_arrive_cluster(smem_in_cta(bar, 1));
+      };
       auto acquire = [&]() {
         if (acq) return true;
         const uint32_t u = buf ? uses1 : uses0;
         const int a = 2 * x + buf;
-        if (u > 0 && !mbar_wait_bounded(&sm.accempty[a], (u - 1u) & 1u, abort_flag, status))
+        if (u > 0 &&
+            !mbar_wait_bounded(&sm.accempty[a], (u - 1u) & 1u, abort_flag, status))
           return false;
         tc_fence_after();
         if (buf) ++uses1; else ++uses0;
@@ -1202,24 +1351,22 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       };
       auto mma8 = [&](int aslot, int bslot) {
         const uint64_t da = adesc0 + static_cast<uint64_t>(aslot) * (kTile >> 4);
-        const uint64_t db = bdesc0 + static_cast<uint64_t>(bslot) * (kTile >> 4);
+        const uint64_t db = bdesc0 + static_cast<uint64_t>(bslot) * (kBTile >> 4);
         const uint32_t d = tmem + static_cast<uint32_t>((2 * x + buf) * kBN);
         const uint32_t acc0 = cnt > 0 ? 1u : 0u;
 #pragma unroll
-        for (int kk = 0; kk < Fmt::kMmas; ++kk) {
-          const uint64_t off = Fmt::koff(kk);
-          Fmt::mma(d, da + off, db + off, idesc, kk > 0 ? 1u : acc0);
-        }
+        for (int kk = 0; kk < Fmt::kMmas; ++kk)
+          Fmt::mma(d, da + Fmt::koff(kk), db + Fmt::kboff(kk), idesc, kk > 0 ? 1u : acc0);
       };
       auto finish = [&](bool last) {
         if (++cnt == window || last) {
-          mma_commit(&sm.accfull[2 * x + buf]);
+          commit(&sm.accfull[2 * x + buf]);
           buf ^= 1;
           acq = false;
         }
       };
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int64_t Kt = tiles.tile(t).Kt;
+      for (int64_t t = unit0; t < nunits && ok; t += unit_step) {
+        const int64_t Kt = unit_tile(t).Kt;
         for (int q = 0; q < ngroups && ok; ++q) {
           const int g = S + 1 - 2 * q;
           const bool pair = g - 1 >= 2;
@@ -1230,7 +1377,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
             }
             int bprev = rb.slot;  // B_{g-1}: read by diagonal g only
             rb.advance();
-            if (x == 1) mbar_arrive(&sm.b_empty[bprev]);
+            if (x == 1) release(&sm.b_empty[bprev]);
             for (int s = 1; s <= g - 1; ++s) {
               if (!mbar_wait_bounded(&sm.a_full[ra.slot], ra.phase, abort_flag, status)) {
                 ok = false;
@@ -1240,7 +1387,8 @@ __global__ void __launch_bounds__(kP2Threads, 1)
               ra.advance();
               int bnew = -1;
               if (s <= g - 2) {
-                if (!mbar_wait_bounded(&sm.b_full[rb.slot], rb.phase, abort_flag, status)) {
+                if (!mbar_wait_bounded(&sm.b_full[rb.slot], rb.phase, abort_flag,
+                                              status)) {
                   ok = false;
                   break;
                 }
@@ -1256,8 +1404,8 @@ __global__ void __launch_bounds__(kP2Threads, 1)
                 }
                 mma8(aslot, bprev);
                 finish(kb == Kt - 1 && s == g - 1);
-                mma_commit(&sm.a_empty[aslot]);
-                mma_commit(&sm.b_empty[bprev]);
+                commit(&sm.a_empty[aslot]);
+                commit(&sm.b_empty[bprev]);
               } else if (pair && s <= g - 2) {
                 // diagonal g-1: A_s x B_{g-1-s}
                 if (!acquire()) {
@@ -1266,11 +1414,11 @@ __global__ void __launch_bounds__(kP2Threads, 1)
                 }
                 mma8(aslot, bnew);
                 finish(kb == Kt - 1 && s == g - 2);
-                mma_commit(&sm.a_empty[aslot]);
-                mma_commit(&sm.b_empty[bnew]);
+                commit(&sm.a_empty[aslot]);
+                commit(&sm.b_empty[bnew]);
               } else {
-                mbar_arrive(&sm.a_empty[aslot]);
-                if (bnew >= 0) mbar_arrive(&sm.b_empty[bnew]);
+                release(&sm.a_empty[aslot]);
+                if (bnew >= 0) release(&sm.b_empty[bnew]);
               }
               bprev = bnew;
             }
@@ -1333,7 +1481,12 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&sm.accempty[a]);
+      if (lane == 0) {
+        if (kPair && !leader)
+          mbar_arrive_cluster(smem_in_cta(&sm.accempty[a], 0));  // the issuers are in rank 0
+        else
+          mbar_arrive(&sm.accempty[a]);
+      }
       b ^= 1;
       if constexpr (kSpill) {
         int& nd = x ? nd1 : nd0;
@@ -1344,8 +1497,11 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       }
       return true;
     };
-    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const OzTile j = tiles.tile(t);
+    for (int64_t t = unit0; t < nunits && ok; t += unit_step) {
+      const OzTile j = unit_tile(t);
+      // a CTA of a pair past the last tile-row drains its windows (its sums
+      // are not used) and touches no memory of the product
+      const bool live = !kPair || j.row0 < j.m;
       // diagonals g >= gx fold exactly in int64 (see oz_gemm_kernel)
       const int gx = oz_exact_from(S, beta, j.Kt);
       const int64_t row = j.row0 + row_in_tile;
@@ -1362,7 +1518,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
         nd0 = nd1 = 0;
         sp0 = sp1 = false;
         for (int64_t kb = 0; kb < j.Kt && ok; ++kb) {
-          if (kb == j.Kt - 1 && q > 0) {
+          if (kb == j.Kt - 1 && q > 0 && live) {
             // the fold at the end of this k-block reads the tile's running
             // sums: bring them into L2 while the last windows finish
             const uint64_t* ps =
@@ -1390,6 +1546,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
           }
         }
         if (!ok) break;
+        if (!live) continue;
         // fold D_g (then D_{g-1}) into the running sum kept in C
         const bool first = (q == 0);
         const bool last = (g - (pair ? 1 : 0) == 2);
@@ -1398,53 +1555,79 @@ __global__ void __launch_bounds__(kP2Threads, 1)
         // the running sums live in the tile's column-major scratch: for each
         // column the warp's 32 lanes (32 consecutive rows) touch 256
         // contiguous bytes.  8 columns per step of a rolled loop (the next 8
-        // loaded while these fold); the digit sums are rotated down by 8
-        // after each step so the loop body only names D[0..7]: a compact
-        // loop keeps the kernel inside the instruction caches.
+        // prefetched into L1 while these fold: prefetched values held in
+        // registers instead pushed the epilogue past its register budget);
+        // the digit sums are rotated down by 8 after each step so the loop
+        // body only names D[0..7]: a compact loop keeps the kernel inside the
+        // instruction caches.  The kinds of the two fold steps are fixed per
+        // diagonal pair (one loop per combination), so the 8 elements of a
+        // step are independent straight-line code.  Each thread reads only
+        // the sums it wrote itself.
         uint64_t* tsum = j.sums + static_cast<size_t>(half * 64) * kOzTileRows + row_in_tile;
-        uint64_t cur[8], nxt[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) cur[i] = first ? 0ull : __ldcg(tsum + i * kOzTileRows);
+        auto fold_pass = [&](auto k0c, auto k1c) {
+          constexpr int K0 = decltype(k0c)::value, K1 = decltype(k1c)::value;
+          // diagonal 2 (the last) is never in the int64-only phase
+          constexpr bool kMayLast =
+              K1 == kFoldConv || K1 == kFoldFp || (K1 == kFoldNone && K0 != kFoldInt);
+          uint64_t cur[8];
 #pragma unroll 1
-        for (int ch = 0; ch < 8; ++ch) {
-          uint64_t* tch = tsum + static_cast<size_t>(ch * 8) * kOzTileRows;
-          if (ch < 7 && !first) {
+          for (int ch = 0; ch < 8; ++ch) {
+            uint64_t* tch = tsum + static_cast<size_t>(ch * 8) * kOzTileRows;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) nxt[i] = __ldcg(tch + (8 + i) * kOzTileRows);
-          }
+            for (int i = 0; i < 8; ++i) cur[i] = first ? 0ull : __ldca(tch + i * kOzTileRows);
+            if (ch < 7 && !first) {
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            long long d0 = D0[i], d1 = D1[i];
-            if constexpr (kSpill) {
-              const size_t sc =
-                  static_cast<size_t>(half * 64 + ch * 8 + i) * kOzTileRows + row_in_tile;
-              if (sp0) d0 += spill_base[sc];
-              if (sp1) d1 += spill_base[static_cast<size_t>(kOzTileRows) * kOzTileRows + sc];
+              for (int i = 0; i < 8; ++i) prefetch_l1(tch + (8 + i) * kOzTileRows);
             }
-            cur[i] = fold_step(cur[i], d0, g, gx, S, beta);
-            if (pair) cur[i] = fold_step(cur[i], d1, g - 1, gx, S, beta);
-          }
-          if (last) {
-            const int64_t cbase = col0 + ch * 8;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              const int64_t col = cbase + i;
-              if (row_ok && col < j.n)
-                j.C[row * j.n + col] =
-                    final_scale(cur[i], er + exponent_from_absbits(__ldg(j.colbits + col)) +
-                                            j.eoff);
+              long long d0 = D0[i], d1 = D1[i];
+              if constexpr (kSpill) {
+                const size_t sc =
+                    static_cast<size_t>(half * 64 + ch * 8 + i) * kOzTileRows + row_in_tile;
+                if (sp0) d0 += spill_base[sc];
+                if (sp1) d1 += spill_base[static_cast<size_t>(kOzTileRows) * kOzTileRows + sc];
+              }
+              cur[i] = fold_kind<K0>(cur[i], d0, g, S, beta);
+              if constexpr (K1 != kFoldNone) cur[i] = fold_kind<K1>(cur[i], d1, g - 1, S, beta);
             }
-          } else {
+            if (kMayLast && last) {
+              const int64_t cbase = col0 + ch * 8;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) __stcg(tch + i * kOzTileRows, cur[i]);
+              for (int i = 0; i < 8; ++i) {
+                const int64_t col = cbase + i;
+                if (row_ok && col < j.n)
+                  j.C[row * j.n + col] =
+                      ldexp_rn(__longlong_as_double(static_cast<long long>(cur[i])),
+                               er + exponent_from_absbits(__ldg(j.colbits + col)) + j.eoff);
+              }
+            } else {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) __stcg(tch + i * kOzTileRows, cur[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 56; ++i) {
+              D0[i] = D0[i + 8];
+              D1[i] = D1[i + 8];
+            }
           }
-#pragma unroll
-          for (int i = 0; i < 56; ++i) {
-            D0[i] = D0[i + 8];
-            D1[i] = D1[i + 8];
-          }
-#pragma unroll
-          for (int i = 0; i < 8; ++i) cur[i] = first ? 0ull : nxt[i];
+        };
+        using FInt = std::integral_constant<int, kFoldInt>;
+        using FConv = std::integral_constant<int, kFoldConv>;
+        using FFp = std::integral_constant<int, kFoldFp>;
+        using FNone = std::integral_constant<int, kFoldNone>;
+        // g > gx: int64 (g - 1 >= gx: int64 or the conversion); g == gx: the
+        // conversion (g - 1: FP64); g < gx: FP64 for both
+        const int k0 = fold_kind_of(g, gx);
+        const int k1 = pair ? fold_kind_of(g - 1, gx) : kFoldNone;
+        switch (k0 * 4 + k1) {
+          case kFoldInt * 4 + kFoldInt: fold_pass(FInt{}, FInt{}); break;
+          case kFoldInt * 4 + kFoldConv: fold_pass(FInt{}, FConv{}); break;
+          case kFoldConv * 4 + kFoldFp: fold_pass(FConv{}, FFp{}); break;
+          case kFoldFp * 4 + kFoldFp: fold_pass(FFp{}, FFp{}); break;
+          case kFoldInt * 4 + kFoldNone: fold_pass(FInt{}, FNone{}); break;
+          case kFoldConv * 4 + kFoldNone: fold_pass(FConv{}, FNone{}); break;
+          default: fold_pass(FFp{}, FNone{}); break;  // g < gx, alone
         }
       }
     }
@@ -1452,8 +1635,16 @@ __global__ void __launch_bounds__(kP2Threads, 1)
 
   tc_fence_before();
   __syncthreads();
+  // pairs: neither CTA leaves (nor frees its tensor memory) while the other
+  // may still arrive on its barriers or run MMAs into it
+  if constexpr (kPair) cluster_sync_all();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+  if (warp == 1) {
+    if constexpr (kPair)
+      tmem_dealloc_pair(tmem, kTmemCols);
+    else
+      tmem_dealloc(tmem, kTmemCols);
+  }
 }
 
 __global__ void zero_fill_kernel(double* __restrict__ C, int64_t count) {
@@ -1503,10 +1694,10 @@ cudaError_t launch_ozaki_split(const double* A, const double* B, const OzakiDims
     dim3 grid(static_cast<unsigned>(d.Kt), static_cast<unsigned>(d.Nt));
     if (d.fp8)
       oz_split_b_kernel<16><<<grid, 256, 0, s>>>(B, d.k, d.n, colbits, d.S, d.beta, d.Nt, d.Kt,
-                                                 bslices, false);
+                                                 bslices, false, false);
     else
       oz_split_b_kernel<8><<<grid, 256, 0, s>>>(B, d.k, d.n, colbits, d.S, d.beta, d.Nt, d.Kt,
-                                                bslices, d.rn != 0);
+                                                bslices, d.rn != 0, ozaki_b_halves(d));
   }
   return cudaGetLastError();
 }
@@ -1567,6 +1758,41 @@ __global__ void __launch_bounds__(256) oz_splitk_fold_kernel(
 }
 
 
+// The paired kernel on clusters of two CTAs (cta_group::2): one cluster per
+// 256 x 128 C tile at a time, as many clusters as fit (at most max_ctas / 2).
+static cudaError_t launch_gemm2_pairs(const OzSingle& tiles, const OzakiDims& d,
+                                      int64_t max_ctas, int window, int* status,
+                                      cudaStream_t s) {
+  auto kern = tiles.spill != nullptr ? oz_gemm2_kernel<OzSingle, FmtBf16Pair, true>
+                                     : oz_gemm2_kernel<OzSingle, FmtBf16Pair, false>;
+  const size_t kSmem = gemm2_smem_bytes<FmtBf16Pair>();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kSmem));
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kP2Threads, 1, 1);
+  cfg.dynamicSmemBytes = kSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(2, 1, 1);
+  int clusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+  if (e != cudaSuccess) return e;
+  if (clusters < 1) return cudaErrorLaunchOutOfResources;
+  const int64_t units = (d.Mt + 1) / 2 * d.Nt;
+  int64_t pairs = units < clusters ? units : clusters;
+  if (pairs > max_ctas / 2) pairs = max_ctas / 2;
+  if (pairs < 1) pairs = 1;
+  cfg.gridDim = dim3(static_cast<unsigned>(2 * pairs), 1, 1);
+  return cudaLaunchKernelEx(&cfg, kern, tiles, d.S, d.beta, window, status);
+}
+
 cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
                               const uint64_t* rowbits, const uint64_t* colbits, double* C,
                               const OzakiDims& d, uint64_t* sums, int* status, cudaStream_t s) {
@@ -1614,6 +1840,9 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
                                                align_up(ozaki_sums_bytes(d), 1024));
     if (g2 > kOzSpillCtas) g2 = kOzSpillCtas;
   }
+  if (ozaki_cta2(d))
+    return launch_gemm2_pairs(tiles, d, tiles.spill != nullptr ? kOzSpillCtas : INT64_MAX,
+                              window, status, s);
   auto kern = tiles.spill != nullptr ? oz_gemm2_kernel<OzSingle, FmtBf16, true>
                                      : oz_gemm2_kernel<OzSingle, FmtBf16, false>;
   const size_t kSmem = gemm2_smem_bytes<FmtBf16>();

@@ -219,3 +219,24 @@ def test_emul_long_k_spills_bit_identical(mode, S, beta, k):
     ii[:4] = [0, m - 1, 0, m - 1]
     jj[:4] = [0, n - 1, n - 1, 0]
     assert_bitwise(C[ii, jj], oracle.ozaki_entries(A, B, ii, jj, S=S, beta=beta), "long k spills")
+
+
+# Products with two or more tile-rows of A run on CTA pairs (256-row C
+# tiles); with an odd number of tile-rows the second CTA of the last pair
+# has no rows and only feeds its half of B.  More 256-row tiles than pairs
+# on the GPU: several tiles per pair.
+@pytest.mark.parametrize("shape,S", [((9 * 128 + 5, 640, 700), 7), ((33 * 128, 256, 2048), 5),
+                                     ((2 * 128, 1000, 129), 7), ((3 * 128 - 1, 130, 4 * 128), 8)])
+def test_emul_cta_pairs_odd_tile_rows(shape, S):
+    m, k, n = shape
+    A, B = inputs.gemm_operands("spread", m, k, n, seed=0, cfg=60 + S)
+    C = run_emul(A, B, S)
+    assert_bitwise(run_emul(A, B, S), C, "run to run")
+    rng = np.random.default_rng(m + k + n)
+    ii = rng.integers(0, m, 300)
+    jj = rng.integers(0, n, 300)
+    # the last rows (the odd tile-row), the first rows of each CTA's half of
+    # a pair tile, the last columns
+    ii[:6] = [m - 1, m - 1, 128, 255, 256 % m, (m - 1) // 128 * 128]
+    jj[:6] = [n - 1, 0, 63, 64, n - 1, 127 % n]
+    assert_bitwise(C[ii, jj], oracle.ozaki_entries(A, B, ii, jj, S=S, beta=7), f"{shape} S={S}")
