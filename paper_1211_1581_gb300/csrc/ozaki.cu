@@ -1143,6 +1143,13 @@ struct __align__(1024) Gemm2Smem {
 
 template <typename Fmt>
 constexpr size_t gemm2_smem_bytes() { return sizeof(Gemm2Smem<Fmt>) + 1024; }
+// every form fits the 227 KiB of shared memory a CTA may have on this GPU
+static_assert(gemm2_smem_bytes<FmtBf16>() <= 232448, "paired kernel: shared memory");
+static_assert(gemm2_smem_bytes<FmtE4m3>() <= 232448, "paired kernel (E4M3): shared memory");
+static_assert(gemm2_smem_bytes<FmtBf16Pair>() <= 232448, "paired kernel (pairs): shared memory");
+// slots stay 1024-byte aligned for the 128-byte-swizzle descriptors
+static_assert(FmtBf16Pair::kBTileBytes % 1024 == 0 && FmtBf16Pair::kTileBytes % 1024 == 0,
+              "pair tiles: alignment");
 
 // One ring of N shared-memory slots with full/empty barriers.
 template <int N>
