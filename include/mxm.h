@@ -73,7 +73,10 @@ typedef struct {
 /* Library version: major*10000 + minor*100 + patch. */
 int mxm_version(void);
 
-/* Human-readable name of a status code (static string, never NULL). */
+/* Human-readable name of a status code (static string, never NULL): the
+ * enumerator's own name, e.g. "MXM_ERR_ALIGNMENT", or "MXM_ERR_UNKNOWN" for a
+ * value outside mxm_status.  The paper has no counterpart: error reporting is
+ * the library's contract around the Sec. 3.1 operation. */
 const char* mxm_status_string(mxm_status s);
 
 /*
@@ -136,7 +139,16 @@ mxm_status mxm_gemm(int mode, const double* A, const double* B, double* C, int64
 mxm_status mxm_gemm_host(int mode, const double* hA, const double* hB, double* hC, int64_t m,
                          int64_t k, int64_t n, int slices, void* stream);
 
-/* Bytes of device workspace one mxm_gemm call of this shape needs. */
+/*
+ * mxm_workspace_size -- bytes of device workspace one mxm_gemm call of mode
+ * `mode` on an m x k by k x n product (Sec. 3.1 shapes) with `slices` slices
+ * needs (the FP64 path: zero-padded tile copies of A and B, plus split-k
+ * partials; the emulated modes: row and column scales, the digit planes of
+ * the Ozaki split, the running sums or split-k partials).  Host arithmetic
+ * only, no device call.  Returns 0 for an empty product (m, n or k <= 0),
+ * an unknown mode or a slice count the mode does not take.  The paper has no
+ * counterpart; size a buffer for mxm_set_workspace with it.
+ */
 size_t mxm_workspace_size(int mode, int64_t m, int64_t k, int64_t n, int slices);
 
 /*
@@ -145,9 +157,18 @@ size_t mxm_workspace_size(int mode, int64_t m, int64_t k, int64_t n, int slices)
  * library then never allocates for mxm_f64 / mxm_f64_emul / mxm_gemm, which
  * makes them safe to capture in a CUDA graph.  d_ws == NULL returns to the
  * library-owned workspace (grown with cudaMalloc on demand, outside
- * capture).  The caller keeps d_ws alive while calls that use it run.
+ * capture).  The paper has no counterpart (its calls take arrays the caller
+ * owns and nothing else); this is the library's memory contract.
+ *   stream  the stream the caller's next calls run on: the switch waits for
+ *           the work already queued there (which may still use the previous
+ *           workspace), and frees a library-owned previous workspace after
+ *           the device is idle.  Calls on other streams must not be using the
+ *           workspace meanwhile.
+ * Errors: d_ws misaligned: MXM_ERR_ALIGNMENT; `stream` capturing (the switch
+ * synchronises): MXM_ERR_UNSUPPORTED; a failed synchronisation:
+ * MXM_ERR_CUDA.  The caller keeps d_ws alive while calls that use it run.
  */
-mxm_status mxm_set_workspace(void* d_ws, size_t bytes);
+mxm_status mxm_set_workspace(void* d_ws, size_t bytes, void* stream);
 
 /*
  * mxm_grouped_workspace_size -- bytes of workspace mxm_grouped needs for
@@ -157,7 +178,8 @@ mxm_status mxm_grouped_workspace_size(int64_t count, const mxm_problem* h_proble
                                       int slices, size_t* bytes);
 
 /*
- * mxm_grouped -- `count` independent products C_p = A_p.B_p of uneven sizes
+ * mxm_grouped -- `count` independent products C_p = A_p.B_p (each the
+ * Sec. 3.1 operation c_ij = sum_k a_ik b_kj on its own operands) of uneven sizes
  * in one persistent launch sequence, from a DEVICE-resident table of
  * mxm_problem.  mode is MXM_MODE_F64 or MXM_MODE_EMUL_I8 / _BF16 / _RN8.  d_ws is
  * caller workspace of ws_bytes (see mxm_grouped_workspace_size); the call

@@ -272,6 +272,7 @@ size_t mxm_workspace_size(int mode, int64_t m, int64_t k, int64_t n, int slices)
 
 mxm_status mxm_gemm(int mode, const double* A, const double* B, double* C, int64_t m, int64_t k,
                     int64_t n, int slices, void* stream) {
+  NvtxRange nvtx_range("mxm_gemm");
   mxm_status st = check_mode(mode, slices);
   if (st != MXM_OK) return st;
   st = check_gemm_args(A, B, C, m, k, n);
@@ -475,6 +476,7 @@ static mxm_status gemm_host_panels(DeviceState* ds, int mode, const double* hA, 
 
 mxm_status mxm_gemm_host(int mode, const double* hA, const double* hB, double* hC, int64_t m,
                          int64_t k, int64_t n, int slices, void* stream) {
+  NvtxRange nvtx_range("mxm_gemm_host");
   mxm_status st = check_mode(mode, slices);
   if (st != MXM_OK) return st;
   if (m < 0 || k < 0 || n < 0) return MXM_ERR_INVALID_ARG;
@@ -512,12 +514,18 @@ mxm_status mxm_gemm_host(int mode, const double* hA, const double* hB, double* h
   return cudaStreamSynchronize(s) == cudaSuccess ? MXM_OK : cuda_fail();
 }
 
-mxm_status mxm_set_workspace(void* d_ws, size_t bytes) {
+mxm_status mxm_set_workspace(void* d_ws, size_t bytes, void* stream) {
+  NvtxRange nvtx_range("mxm_set_workspace");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> lock(g_mutex);
   DeviceState* ds = nullptr;
   mxm_status st = current_state(&ds);
   if (st != MXM_OK) return st;
   if (d_ws != nullptr && (reinterpret_cast<uintptr_t>(d_ws) & 255)) return MXM_ERR_ALIGNMENT;
+  // the switch synchronises: not while `stream` is being captured
+  if (stream_capturing(s)) return MXM_ERR_UNSUPPORTED;
+  // work already queued on `stream` may still use the previous workspace
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail();
   if (ds->ws_owned && ds->ws) {
     if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail();
     cudaFree(ds->ws);
@@ -535,6 +543,7 @@ mxm_status mxm_set_workspace(void* d_ws, size_t bytes) {
 }
 
 mxm_status mxm_get_device_status(void* stream) {
+  NvtxRange nvtx_range("mxm_get_device_status");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DeviceState* ds = nullptr;
   {

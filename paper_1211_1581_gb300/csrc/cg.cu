@@ -452,6 +452,7 @@ extern "C" mxm_status mxm_cg(const double* matvals, const int32_t* indx, const i
                              const double* b, double* x, int64_t n, int64_t nnz, double stop,
                              int32_t max_iters, int32_t engine, double* work, int32_t* iters,
                              double* r2, double* r2_hist, void* stream) {
+  NvtxRange nvtx_range("mxm_cg");
   if (n < 0 || nnz < 0 || max_iters < 0) return MXM_ERR_INVALID_ARG;
   if (n == 0) return MXM_ERR_INVALID_ARG;
   if (engine != MXM_CG_AUTO && engine != MXM_CG_CLUSTER && engine != MXM_CG_GRAPH)

@@ -341,6 +341,7 @@ using namespace mxm;
 extern "C" int64_t mxm_fft_max_n(void) { return kFftMaxN; }
 
 extern "C" mxm_status mxm_fft_twiddles(double* table, int64_t n, void* stream) {
+  NvtxRange nvtx_range("mxm_fft_twiddles");
   if (!pow2(n) || n > kFftMaxN) return MXM_ERR_INVALID_ARG;
   if (n < 2) return MXM_OK;  // no twiddle
   if (table == nullptr) return MXM_ERR_INVALID_ARG;
@@ -355,6 +356,7 @@ extern "C" mxm_status mxm_fft_twiddles(double* table, int64_t n, void* stream) {
 
 extern "C" mxm_status mxm_fft(const double* in, double* out, double* work, const double* table,
                               int64_t table_n, int64_t n, void* stream) {
+  NvtxRange nvtx_range("mxm_fft");
   if (!pow2(n) || n > kFftMaxN) return MXM_ERR_INVALID_ARG;
   if (in == nullptr || out == nullptr) return MXM_ERR_INVALID_ARG;
   if (n >= 2 && (table == nullptr || !pow2(table_n) || table_n < n || table_n > kFftMaxN))

@@ -217,6 +217,7 @@ int* device_status_word();
 
 extern "C" mxm_status mxm_grouped(int64_t count, const mxm_problem* d_problems, int mode,
                                   int slices, void* d_ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("mxm_grouped");
   if (count < 0 || (count > 0 && d_problems == nullptr)) return MXM_ERR_INVALID_ARG;
   if (!grouped_mode_ok(mode, slices)) return MXM_ERR_UNSUPPORTED;
   if (count == 0) return MXM_OK;

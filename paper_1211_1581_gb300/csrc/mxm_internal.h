@@ -5,8 +5,19 @@
 #include <cstdint>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace mxm {
+
+// A named NVTX range around one ABI call (scope-bound), so that a profiler's
+// timeline shows which call launched which kernels.  Without a profiler
+// attached NVTX calls return at once.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Bits of the sticky device status word (OR-ed by kernels).
 constexpr int kStatusNonFinite = 1;
@@ -203,6 +214,17 @@ inline OzakiLayout ozaki_layout(const OzakiDims& d) {
   return L;
 }
 
+
+// The plan of ozaki_dims_splitk when its workspace fits `cap` bytes, else
+// the same product without split-k (the split-k partials are exact integers
+// added exactly, so both plans give the same bits).  The caller checks
+// whether the returned plan fits.
+inline OzakiDims ozaki_dims_capped(int64_t m, int64_t k, int64_t n, int S, int beta,
+                                   size_t cap) {
+  OzakiDims d = ozaki_dims_splitk(m, k, n, S, beta);
+  if (d.splits > 1 && ozaki_layout(d).total > cap) d = ozaki_dims(m, k, n, S, beta);
+  return d;
+}
 
 // Largest number of K=16 MMAs whose integer products can be summed in an
 // FP32 accumulator without rounding: every product is at most (2^beta-1)^2

@@ -73,8 +73,13 @@ using namespace mxm;
 extern "C" mxm_status mxm_f64_emul_noalloc(const double* A, const double* B, double* C,
                                            int64_t m, int64_t k, int64_t n, int slices,
                                            void* stream) {
+  NvtxRange nvtx_range("mxm_f64_emul_noalloc");
   if (slices < 1 || slices > kOzMaxSlices) return MXM_ERR_UNSUPPORTED;
   if (m < 0 || k < 0 || n < 0) return MXM_ERR_INVALID_ARG;
+  // the same size limits as mxm_f64_emul: beyond them the byte counts below
+  // could wrap around in 64 bits
+  if (m > (int64_t(1) << 31) || n > (int64_t(1) << 31) || k > (int64_t(1) << 31))
+    return MXM_ERR_UNSUPPORTED;
   if (m == 0 || n == 0) return MXM_OK;
   if (C == nullptr || (k > 0 && (A == nullptr || B == nullptr))) return MXM_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) |
@@ -84,7 +89,14 @@ extern "C" mxm_status mxm_f64_emul_noalloc(const double* A, const double* B, dou
   if (ranges_overlap(C, cb, A, sizeof(double) * size_t(m) * size_t(k)) ||
       ranges_overlap(C, cb, B, sizeof(double) * size_t(k) * size_t(n)))
     return MXM_ERR_INVALID_ARG;
-  const OzakiDims d = ozaki_dims(m, k, n, slices, 7);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (k == 0) {
+    // the empty sum: zeros, no scratch needed
+    return launch_zero_fill(C, m * n, s) == cudaSuccess ? MXM_OK : MXM_ERR_CUDA;
+  }
+  // the plan of mxm_f64_emul when its scratch fits, else the same product
+  // without split-k (same bits); refused when neither fits
+  const OzakiDims d = ozaki_dims_capped(m, k, n, slices, 7, kNoAllocScratchBytes);
   const OzakiLayout L = ozaki_layout(d);
   if (L.total > kNoAllocScratchBytes) return MXM_ERR_WORKSPACE_TOO_SMALL;
 
@@ -93,14 +105,12 @@ extern "C" mxm_status mxm_f64_emul_noalloc(const double* A, const double* B, dou
   if (st != MXM_OK) return st;
   int* status = device_status_word();
   if (status == nullptr) return MXM_ERR_CUDA;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (k == 0) return launch_zero_fill(C, m * n, s) == cudaSuccess ? MXM_OK : MXM_ERR_CUDA;
 
   uint64_t* rowbits = reinterpret_cast<uint64_t*>(ws + L.rowbits);
   uint64_t* colbits = reinterpret_cast<uint64_t*>(ws + L.colbits);
   // launch_ozaki_scale zeroes the column maxima before reducing into them;
-  // the row maxima, every digit-plane byte (padding included) and the
-  // running sums are written before they are read.
+  // the row maxima, every digit-plane byte (padding included), the running
+  // sums and the split-k partials are written before they are read.
   cudaError_t e = launch_ozaki_scale(A, B, d, rowbits, colbits, status, s);
   if (e == cudaSuccess)
     e = launch_ozaki_split(A, B, d, rowbits, colbits, ws + L.aslices, ws + L.bslices, s);

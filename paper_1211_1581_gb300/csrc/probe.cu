@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(128, 1) probe_umma_kernel(int iters, int* stat
 using namespace mxm;
 
 extern "C" mxm_status mxm_peak_probe(int kind, double* tflops) {
+  NvtxRange nvtx_range("mxm_peak_probe");
   if (tflops == nullptr || kind < 0 || kind > 4) return MXM_ERR_INVALID_ARG;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MXM_ERR_CUDA;

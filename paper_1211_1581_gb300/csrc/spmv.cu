@@ -141,6 +141,7 @@ using namespace mxm;
 extern "C" mxm_status mxm_spmv(const double* matvals, const int32_t* indx, const int32_t* rowp,
                                const double* x, double* y, int64_t nrows, int64_t ncols,
                                int64_t nnz, void* stream) {
+  NvtxRange nvtx_range("mxm_spmv");
   if (nrows < 0 || ncols < 0 || nnz < 0) return MXM_ERR_INVALID_ARG;
   if (nrows > INT32_MAX || ncols > INT32_MAX || nnz > INT32_MAX) return MXM_ERR_UNSUPPORTED;
   if (nrows == 0) return MXM_OK;

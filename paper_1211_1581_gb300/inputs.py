@@ -35,32 +35,92 @@ def _mix(z: np.ndarray) -> np.ndarray:
     return z
 
 
-def words(seed: int, stream: int, count: int, *, start: int = 0,
-          chunk: int = 1 << 24) -> np.ndarray:
-    """``count`` 64-bit words of stream (seed, stream), from word ``start``."""
+_CHUNK = 1 << 21
+
+
+def _key(seed: int, stream: int):
     with np.errstate(over="ignore"):
         s = np.array([seed & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64)
         st = np.array([(stream + 1) & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64)
-        key = _mix(s * GAMMA ^ st * STREAM_MUL)[0]
-        out = np.empty(count, dtype=np.uint64)
-        for lo in range(0, count, chunk):
-            hi = min(count, lo + chunk)
-            ctr = np.arange(start + lo + 1, start + hi + 1, dtype=np.uint64)
-            out[lo:hi] = _mix(key + ctr * GAMMA)
+        return _mix(s * GAMMA ^ st * STREAM_MUL)[0]
+
+
+def _words_chunk(key, start: int, lo: int, hi: int) -> np.ndarray:
+    """Words lo .. hi - 1 (after ``start``) of the stream with this key."""
+    with np.errstate(over="ignore"):
+        z = np.arange(start + lo + 1, start + hi + 1, dtype=np.uint64)
+        z *= GAMMA
+        z += key
+        t = np.empty_like(z)
+        np.right_shift(z, np.uint64(30), out=t)
+        z ^= t
+        z *= _M1
+        np.right_shift(z, np.uint64(27), out=t)
+        z ^= t
+        z *= _M2
+        np.right_shift(z, np.uint64(31), out=t)
+        z ^= t
+    return z
+
+
+def _chunked(count: int, fill) -> None:
+    """fill(lo, hi) over chunks of [0, count), by a pool of host threads
+    (numpy releases the interpreter lock inside its array operations, and
+    the output pages are first touched by the thread that fills them).
+    Every value depends only on its own counter: the chunking changes
+    nothing."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    starts = range(0, count, _CHUNK)
+    if count <= _CHUNK:
+        for lo in starts:
+            fill(lo, min(count, lo + _CHUNK))
+        return
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(lambda lo: fill(lo, min(count, lo + _CHUNK)), starts))
+
+
+def words(seed: int, stream: int, count: int, *, start: int = 0) -> np.ndarray:
+    """``count`` 64-bit words of stream (seed, stream), from word ``start``."""
+    key = _key(seed, stream)
+    out = np.empty(count, dtype=np.uint64)
+
+    def fill(lo, hi):
+        out[lo:hi] = _words_chunk(key, start, lo, hi)
+
+    _chunked(count, fill)
     return out
+
+
+def _unit_of(w: np.ndarray) -> np.ndarray:
+    return (w >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
 
 
 def unit(seed: int, stream: int, count: int) -> np.ndarray:
     """Uniform doubles in [0, 1): top 53 bits of each word times 2^-53."""
-    w = words(seed, stream, count)
-    return (w >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    key = _key(seed, stream)
+    out = np.empty(count, dtype=np.float64)
+
+    def fill(lo, hi):
+        out[lo:hi] = _unit_of(_words_chunk(key, 0, lo, hi))
+
+    _chunked(count, fill)
+    return out
 
 
 def uniform_pm1(seed: int, stream: int, shape) -> np.ndarray:
     """Entries uniform in [-1, 1): 2u - 1 (exact in FP64)."""
     shape = tuple(shape)
-    u = unit(seed, stream, int(np.prod(shape)))
-    return (2.0 * u - 1.0).reshape(shape)
+    count = int(np.prod(shape))
+    key = _key(seed, stream)
+    out = np.empty(count, dtype=np.float64)
+
+    def fill(lo, hi):
+        out[lo:hi] = 2.0 * _unit_of(_words_chunk(key, 0, lo, hi)) - 1.0
+
+    _chunked(count, fill)
+    return out.reshape(shape)
 
 
 def int_uniform(seed: int, stream: int, shape, lo: int, hi: int) -> np.ndarray:
@@ -77,12 +137,20 @@ def exp_spread(seed: int, stream: int, shape, emin: int = -20, emax: int = 20) -
     a second word of the same counter (stream + 1000003)."""
     shape = tuple(shape)
     cnt = int(np.prod(shape))
-    u = 1.0 + unit(seed, stream, cnt)
-    w2 = words(seed, stream + 1000003, cnt)
-    sign = np.where((w2 & np.uint64(1)) == 1, -1.0, 1.0)
+    k1 = _key(seed, stream)
+    k2 = _key(seed, stream + 1000003)
     span = np.uint64(emax - emin + 1)
-    e = ((w2 >> np.uint64(1)) % span).astype(np.int64) + emin
-    return (sign * np.ldexp(u, e)).reshape(shape)
+    out = np.empty(cnt, dtype=np.float64)
+
+    def fill(lo, hi):
+        u = 1.0 + _unit_of(_words_chunk(k1, 0, lo, hi))
+        w2 = _words_chunk(k2, 0, lo, hi)
+        sign = np.where((w2 & np.uint64(1)) == 1, -1.0, 1.0)
+        e = ((w2 >> np.uint64(1)) % span).astype(np.int64) + emin
+        out[lo:hi] = sign * np.ldexp(u, e)
+
+    _chunked(cnt, fill)
+    return out.reshape(shape)
 
 
 def permutation(seed: int, stream: int, n: int) -> np.ndarray:

@@ -46,7 +46,7 @@ SIGNATURES = {
     "mxm_gemm": (_I, [_I, _P, _P, _P, _I64, _I64, _I64, _I, _P]),
     "mxm_gemm_host": (_I, [_I, _P, _P, _P, _I64, _I64, _I64, _I, _P]),
     "mxm_workspace_size": (_SZ, [_I, _I64, _I64, _I64, _I]),
-    "mxm_set_workspace": (_I, [_P, _SZ]),
+    "mxm_set_workspace": (_I, [_P, _SZ, _P]),
     "mxm_grouped_workspace_size": (_I, [_I64, _P, _I, _I, ctypes.POINTER(_SZ)]),
     "mxm_grouped": (_I, [_I64, _P, _I, _I, _P, _SZ, _P]),
     "mxm_get_device_status": (_I, [_P]),
@@ -189,13 +189,14 @@ def mxm_workspace_size(mode: int, m: int, k: int, n: int, slices: int = 7) -> in
     return int(load().mxm_workspace_size(int(mode), m, k, n, int(slices)))
 
 
-def mxm_set_workspace(ws=None):
-    """Use a caller-owned uint8 CUDA tensor as workspace (None: library-owned)."""
+def mxm_set_workspace(ws=None, stream=None):
+    """Use a caller-owned uint8 CUDA tensor as workspace (None: library-owned);
+    the switch waits for the work queued on ``stream``."""
     if ws is None:
-        _check(load().mxm_set_workspace(None, 0), "mxm_set_workspace")
+        _check(load().mxm_set_workspace(None, 0, _stream_ptr(stream)), "mxm_set_workspace")
     else:
-        _check(load().mxm_set_workspace(ws.data_ptr(), ws.numel() * ws.element_size()),
-               "mxm_set_workspace")
+        _check(load().mxm_set_workspace(ws.data_ptr(), ws.numel() * ws.element_size(),
+                                        _stream_ptr(stream)), "mxm_set_workspace")
 
 
 def problem_table(problems):

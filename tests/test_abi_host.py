@@ -67,6 +67,23 @@ def test_argument_errors_need_no_device():
     assert lib.mxm_f64_emul(fake, fake, fake, 4, 4, 4, 0, None) == mxm.MXM_ERR_UNSUPPORTED
 
 
+def test_noalloc_size_limits_need_no_device():
+    """Sizes beyond 2^31 are refused before any byte count is formed (their
+    products would wrap around in 64 bits), as by mxm_f64_emul; nothing is
+    launched."""
+    lib = mxm.load()
+    P = ctypes.c_void_p
+    a, b, c = P(0x100000), P(0x200000), P(0x300000)
+    for m, k, n in ((1 << 61, 1, 1), (1, 1 << 40, 1), (1, 1, (1 << 31) + 1)):
+        assert lib.mxm_f64_emul_noalloc(a, b, c, m, k, n, 7, None) == mxm.MXM_ERR_UNSUPPORTED
+        assert lib.mxm_f64_emul(a, b, c, m, k, n, 7, None) == mxm.MXM_ERR_UNSUPPORTED
+    assert lib.mxm_f64_emul_noalloc(a, b, c, -1, 4, 4, 7, None) == mxm.MXM_ERR_INVALID_ARG
+    assert lib.mxm_f64_emul_noalloc(a, b, c, 4, 4, 4, 13, None) == mxm.MXM_ERR_UNSUPPORTED
+    assert lib.mxm_f64_emul_noalloc(P(0x100004), b, c, 4, 4, 4, 7, None) == mxm.MXM_ERR_ALIGNMENT
+    assert lib.mxm_f64_emul_noalloc(a, b, P(0x100008), 4, 4, 4, 7, None) == mxm.MXM_ERR_INVALID_ARG
+    assert lib.mxm_f64_emul_noalloc(None, None, None, 0, 4, 4, 7, None) == mxm.MXM_OK
+
+
 def test_workspace_size_is_host_arithmetic():
     # FP64: zero-padded 128x16 tiles of A and B
     assert mxm.mxm_workspace_size(0, 128, 16, 128) == 2 * 128 * 16 * 8

@@ -91,3 +91,24 @@ def test_graph_engine_refuses_capture():
     g.replay()
     torch.cuda.synchronize()
     assert torch.all(xs == 1.0)
+
+
+def test_set_workspace_refuses_a_capturing_stream():
+    """Switching the workspace synchronises its stream, so it is refused while
+    that stream is being captured (MXM_ERR_UNSUPPORTED) and the capture goes
+    on; the switch itself works outside the capture."""
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    mxm.mxm_set_workspace(ws)
+    mxm.mxm_set_workspace(None)
+    y = torch.zeros(8, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        with pytest.raises(mxm.MxmError) as err:
+            mxm.mxm_set_workspace(ws, stream=s)
+        y.fill_(2.0)
+    assert err.value.status == mxm.MXM_ERR_UNSUPPORTED
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.all(y == 2.0)

@@ -138,22 +138,25 @@ def test_emul_int64_running_sums_long_k():
     assert_within_bound(C[ii, jj], d2, ab, k, "long k bound")
 
 
-@pytest.mark.parametrize("kind,S", [("uniform", 7), ("spread", 8)])
-def test_emul_n8192_sampled(kind, S):
+@pytest.mark.parametrize("kind,slices", [("uniform", (7,)), ("spread", (7, 8))])
+def test_emul_n8192_sampled(kind, slices):
     """The benchmark configuration (m = k = n = 8192) in the call bench.py
-    times: sampled entries bit-identical to the CPU emulator and within the
-    bound of Dot2."""
+    times; the spread inputs are the benchmark's own (seed 0, streams 4
+    and 5) and S = 7 is its slice count: sampled entries bit-identical to the
+    CPU emulator and within the bound of Dot2."""
     n = 8192
     A, B = inputs.gemm_operands(kind, n, n, n, seed=0, cfg=2)
-    C = run_emul(A, B, S)
     rng = np.random.default_rng(8192)
-    ii = rng.integers(0, n, 256)
-    jj = rng.integers(0, n, 256)
-    ii[:4] = [0, n - 1, 0, n - 1]
-    jj[:4] = [0, n - 1, n - 1, 0]
-    assert_bitwise(C[ii, jj], oracle.ozaki_entries(A, B, ii, jj, S=S, beta=7), "n=8192")
+    ii = rng.integers(0, n, 300)
+    jj = rng.integers(0, n, 300)
+    ii[:8] = [0, n - 1, 0, n - 1, 127, 128, 255, 256]
+    jj[:8] = [0, n - 1, n - 1, 0, 128, 127, 256, 255]
     d2, ab = oracle.entries_dot2_abs(A, B, ii, jj)
-    assert_within_bound(C[ii, jj], d2, ab, n, "n=8192 bound")
+    for S in slices:
+        C = run_emul(A, B, S)
+        assert_bitwise(C[ii, jj], oracle.ozaki_entries(A, B, ii, jj, S=S, beta=7),
+                       f"n=8192 {kind} S={S}")
+        assert_within_bound(C[ii, jj], d2, ab, n, f"n=8192 {kind} S={S} bound")
 
 
 # Split-k of the emulated product: the exact per-range D_g are added exactly

@@ -80,19 +80,49 @@ def test_f64_deterministic():
     assert_bitwise(run_f64(A, B), run_f64(A, B), "run to run")
 
 
-@pytest.mark.parametrize("n", [1024, 2048])
+def _sample(n_rows, n_cols, count, seed):
+    """Seeded entries of an n_rows x n_cols result: `count` at random plus
+    the corners of the matrix and of the 128 x 128 tiles around its middle
+    and its last tile row and column (the edges a tiling gets wrong)."""
+    rng = np.random.default_rng(seed)
+    ii = list(rng.integers(0, n_rows, count))
+    jj = list(rng.integers(0, n_cols, count))
+    for r in (0, 127, 128, 129, n_rows // 2, n_rows - 129, n_rows - 128, n_rows - 1):
+        for c in (0, 127, 128, n_cols // 2, n_cols - 128, n_cols - 1):
+            if 0 <= r < n_rows and 0 <= c < n_cols:
+                ii.append(r)
+                jj.append(c)
+    return np.array(ii, dtype=np.int64), np.array(jj, dtype=np.int64)
+
+
+@pytest.mark.parametrize("n", [1024, 2048, 4096, 8192])
 def test_f64_sweep_sampled(n):
-    """The square sweep sizes: entries sampled by seed (every tile row and
-    column is hit) checked one by one against Dot2."""
+    """The square sweep sizes: seeded entries (random, and the tile corners)
+    checked one by one against Dot2 with the bound 2 k u (|A||B|)."""
     A, B = inputs.gemm_operands("uniform", n, n, n, seed=0, cfg=1)
     C = run_f64(A, B)
-    rng = np.random.default_rng(n)
-    ii = rng.integers(0, n, 600)
-    jj = rng.integers(0, n, 600)
-    ii[:8] = [0, n - 1, 0, n - 1, 127, 128, 129, n // 2]
-    jj[:8] = [0, n - 1, n - 1, 0, 128, 127, 255, n // 2]
+    ii, jj = _sample(n, n, 600, n)
     d2, ab = oracle.entries_dot2_abs(A, B, ii, jj)
     assert_within_bound(C[ii, jj], d2, ab, n, f"f64 n={n}")
+
+
+def test_f64_sweep_n16384_sampled():
+    """The largest sweep size, 16384^3 (2 GiB per operand): 300 seeded
+    entries and the tile corners against Dot2."""
+    n = 16384
+    A, B = inputs.gemm_operands("uniform", n, n, n, seed=0, cfg=1)
+    dA, dB = dev(A), dev(B)
+    C = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    mxm.mxm_f64(dA, dB, C)
+    torch.cuda.synchronize()
+    assert mxm.mxm_get_device_status() == mxm.MXM_OK
+    del dA, dB
+    ii, jj = _sample(n, n, 300, n)
+    got = C[torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()].cpu().numpy()
+    del C
+    torch.cuda.empty_cache()
+    d2, ab = oracle.entries_dot2_abs(A, B, ii, jj)
+    assert_within_bound(got, d2, ab, n, "f64 n=16384")
 
 
 def test_f64_rectangular_sampled():

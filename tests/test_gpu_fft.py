@@ -72,6 +72,61 @@ def test_wide_exponent_range(p):
     assert rel(gpu_fft(f), oracle.fft(f)) <= bound(N)
 
 
+def bin_bound(N, mu):
+    """Per-bin (componentwise) error of a radix-2 FFT with twiddles accurate
+    to mu: every entry of the product of the stages' absolute butterfly
+    matrices is 1 (one path from each input to each output, twiddles of
+    modulus 1), so the first-order error analysis behind Higham's Thm. 24.2
+    gives, for every output bin, |F'(k) - F(k)| <= L eta / (1 - L eta) ||f||_1
+    with L = log2 N + 1 levels (one more for the twiddle between the two
+    passes) and eta = mu + gamma_4 (sqrt 2 + mu)."""
+    eta = mu + 4 * U / (1 - 4 * U) * (math.sqrt(2) + mu)
+    t = (math.log2(max(N, 1)) + 1) * eta
+    return t / (1 - t)
+
+
+def dft_bin_bound(N):
+    """Per-component error of the oracle's term-by-term DFT (Eq. 1, n in
+    order): the twiddle of angle 2 pi m / N has an absolute error of at most
+    ~ (4 pi + 1) u <= 14 u per component (the rounded angle, then libm), each
+    term a c - b s adds gamma_2 |f(n)|, and the recursive sum of N terms
+    gamma_{N-1} sum |term|: in all (gamma_{N+1} + sqrt 2 * 14 u) ||f||_1."""
+    g = (N + 1) * U / (1 - (N + 1) * U)
+    return g + math.sqrt(2) * 14 * U
+
+
+def assert_bins(got, want, tol, what):
+    err = np.maximum(np.abs(got.real - want.real), np.abs(got.imag - want.imag))
+    bad = ~(err <= tol)
+    assert not bad.any(), (f"{what}: {int(bad.sum())} bins beyond {tol:.3e}; worst "
+                           f"{err.max():.3e} at bin {int(np.argmax(err))}")
+
+
+@pytest.mark.parametrize("p", list(range(0, 13)))
+@pytest.mark.parametrize("spread", [False, True])
+def test_every_bin_against_the_definition(p, spread):
+    """Bin by bin against the DFT of Eq. 1 summed term by term (the plain
+    definition, O(N^2)), N = 2^0 ... 2^12: every bin within the GPU's per-bin
+    FFT bound plus the definition's own rounding, both times ||f||_1."""
+    N = 1 << p
+    f = cplx(3, 230 + p + (40 if spread else 0), N, spread=spread)
+    got = gpu_fft(f)
+    tol = (bin_bound(N, 2 * U) + dft_bin_bound(N)) * np.sum(np.abs(f))
+    assert_bins(got, oracle.dft(f), tol, f"N={N} spread={spread}")
+
+
+@pytest.mark.parametrize("p", [13, 14, 16, 18, 20, 22])
+def test_every_bin_against_oracle_fft(p):
+    """The larger orders bin by bin against the oracle's radix-2 recursion:
+    each within its per-bin bound of the exact transform (the GPU's table
+    from sincospi, mu ~ 2u; the oracle's from libm of a rounded angle,
+    mu ~ 8u)."""
+    N = 1 << p
+    f = cplx(4, 260 + p, N)
+    tol = (bin_bound(N, 2 * U) + bin_bound(N, 8 * U)) * np.sum(np.abs(f))
+    assert_bins(gpu_fft(f), oracle.fft(f), tol, f"N={N}")
+
+
 @pytest.mark.parametrize("p", [1, 6, 10, 11, 17, 22])
 def test_exact_delta_and_constant(p):
     N = 1 << p

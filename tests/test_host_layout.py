@@ -12,7 +12,9 @@ by compiling the library's internal header with the host compiler (no GPU):
   choose pairs by themselves, which is why the host-buffer pipeline copies the
   choice of its largest block to every split and product sharing B's planes;
 * the workspace does not depend on the choice (the halves layout fills the
-  same bytes)."""
+  same bytes);
+* the plan of the no-allocation call: the split-k plan of the grown-workspace
+  call when it fits the fixed scratch, else the unsplit product."""
 import os
 import shutil
 import subprocess
@@ -75,6 +77,20 @@ int main() {
     OzakiDims dg = ozaki_dims(100, 8192, 4096, 7, 7);  // a short last panel of A ...
     dg.pair = 1;                                       // ... given the shared choice
     CHECK(ozaki_cta2(dg) && dg.Mt == 1);               // runs on pairs, rank 1 idle
+  }
+  // the no-allocation plan: mxm_f64_emul's split-k plan when it fits the
+  // cap, else the unsplit product; either way within the cap or refused
+  {
+    const size_t cap = size_t(64) << 20;
+    OzakiDims d = ozaki_dims_capped(256, 2048, 256, 7, 7, cap);    // 4 tiles x 4 ranges
+    CHECK(d.splits == 4 && ozaki_layout(d).total <= cap);
+    CHECK(d.splits == ozaki_dims_splitk(256, 2048, 256, 7, 7).splits);
+    d = ozaki_dims_capped(1024, 1024, 1024, 7, 7, cap);           // split plan too big
+    CHECK(ozaki_dims_splitk(1024, 1024, 1024, 7, 7).splits == 2);
+    CHECK(ozaki_layout(ozaki_dims_splitk(1024, 1024, 1024, 7, 7)).total > cap);
+    CHECK(d.splits == 1 && ozaki_layout(d).total <= cap);
+    d = ozaki_dims_capped(2048, 2048, 2048, 7, 7, cap);           // refused by the caller
+    CHECK(ozaki_layout(d).total > cap);
   }
   // the workspace does not depend on the choice
   {
