@@ -126,6 +126,50 @@ mxm_status mxm_gemm(int mode, const double* A, const double* B, double* C, int64
                     int64_t n, int slices, void* stream);
 
 /*
+ * mxm_plan -- how one product is laid out on the GPU, for the tuner
+ * (paper_1211_1581_gb300/tune.py) and for callers that tune by hand.  A
+ * zero-filled plan (or NULL) is the library's own rule.  The result does not
+ * depend on the plan except through the summation order of the native FP64
+ * path under split-k (within the same bound); every emulated mode gives the
+ * same bits whatever the plan (its partial sums are exact integers).  The
+ * paper has no counterpart (Sec. 3.1 states the operation, not its layout).
+ *   raster    C tiles are walked by the persistent grid in groups of
+ *             `raster` tile-rows (tile-row pairs on CTA pairs), column by
+ *             column inside a group, so that the CTAs working at the same
+ *             time share operand tiles in L2; 0: 8 (4 tile-row pairs).
+ *   kb_order  the k-block order of the slice GEMM: 0 the default (2), 1
+ *             every diagonal (pair) walks k forwards, 2 every other one
+ *             walks k backwards (it starts on the tiles the previous one
+ *             read last, still in L2).
+ *   cta       the slice GEMM on bf16 digits: 0 the rule (CTA pairs,
+ *             cta_group::2 with 256 x 128 C tiles, for two or more tile-rows
+ *             of A without split-k), 1 single CTAs (128 x 128 C tiles).
+ *   splitk    k ranges per C tile: 0 the rule (products with fewer C tiles
+ *             than 152 split k towards 304 work units), 1 never, s > 1 that
+ *             many (at most the number of k-blocks: 16-wide for the native
+ *             path, 128-wide for the emulated modes; not for MXM_MODE_EMUL_FP8).
+ */
+typedef struct {
+  int32_t raster;
+  int32_t kb_order;
+  int32_t cta;
+  int32_t splitk;
+} mxm_plan;
+
+/*
+ * mxm_gemm_plan -- mxm_gemm under an explicit plan (NULL: the default).
+ * Errors as mxm_gemm, and MXM_ERR_INVALID_ARG for a plan field out of range
+ * (negative, kb_order > 2, cta > 1) or split-k asked of MXM_MODE_EMUL_FP8.
+ */
+mxm_status mxm_gemm_plan(int mode, const double* A, const double* B, double* C, int64_t m,
+                         int64_t k, int64_t n, int slices, const mxm_plan* plan, void* stream);
+
+/* mxm_workspace_size_plan -- mxm_workspace_size for a product under `plan`
+ * (split-k changes it); 0 also for an invalid plan. */
+size_t mxm_workspace_size_plan(int mode, int64_t m, int64_t k, int64_t n, int slices,
+                               const mxm_plan* plan);
+
+/*
  * mxm_gemm_host -- mxm_gemm on HOST buffers: copies A and B to the device,
  * computes, copies C back, and returns after C is in host memory (the
  * stream is synchronised).  Device buffers come from the library's

@@ -146,24 +146,71 @@ bool emul_mode(int mode) {
 int mode_beta(int mode) { return mode == MXM_MODE_EMUL_I8 ? 7 : 8; }
 bool mode_rn(int mode) { return mode == MXM_MODE_EMUL_RN8; }
 
-size_t workspace_bytes(int mode, int64_t m, int64_t k, int64_t n, int slices) {
+// The default plan: every field zero.
+constexpr mxm_plan kNoPlan = {0, 0, 0, 0};
+
+bool plan_ok(int mode, const mxm_plan& p) {
+  if (p.raster < 0 || p.kb_order < 0 || p.kb_order > 2 || p.cta < 0 || p.cta > 1 ||
+      p.splitk < 0)
+    return false;
+  if (mode == MXM_MODE_EMUL_FP8 && p.splitk > 1) return false;
+  return true;
+}
+
+// Dims of a native product under a plan.
+F64Dims native_dims(int64_t m, int64_t k, int64_t n, const mxm_plan& p) {
+  F64Dims d = f64_dims(m, k, n);
+  if (p.splitk == 1) d.splits = 1;
+  else if (p.splitk > 1) d.splits = p.splitk < d.Kt ? p.splitk : (d.Kt > 0 ? d.Kt : 1);
+  if (p.raster > 0) d.raster = p.raster;
+  return d;
+}
+
+// Dims of an emulated product (bf16 digits) under a plan.
+OzakiDims emul_dims(int mode, int64_t m, int64_t k, int64_t n, int slices, const mxm_plan& p) {
+  OzakiDims d = ozaki_dims_splitk(m, k, n, slices, mode_beta(mode), mode_rn(mode));
+  if (p.splitk == 1) {
+    d.splits = 1;
+    d.pair = d.Mt >= 2 ? 1 : 0;
+  } else if (p.splitk > 1) {
+    d.splits = p.splitk < d.Kt ? p.splitk : (d.Kt > 0 ? d.Kt : 1);
+    if (d.splits > 1) d.pair = 0;
+  }
+  if (p.cta == 1) d.pair = 0;
+  // measured at m = k = n = 8192, S = 7 on CTA pairs: groups of 4 pair-rows
+  // with alternating k-block directions read 47.7 GB from DRAM per product
+  // against 73.4 GB for groups of 8 going forwards (same time within 0.5 %)
+  d.raster = p.raster > 0 ? p.raster : (d.pair ? kPairRaster : kDefaultRaster);
+  d.kb_alt = p.kb_order == 1 ? 0 : 1;
+  return d;
+}
+
+OzakiDims fp8_dims(int64_t m, int64_t k, int64_t n, int slices, const mxm_plan& p) {
+  OzakiDims d = ozaki_dims_fp8(m, k, n, slices);
+  if (p.raster > 0) d.raster = p.raster;
+  d.kb_alt = p.kb_order == 1 ? 0 : 1;
+  return d;
+}
+
+size_t workspace_bytes(int mode, int64_t m, int64_t k, int64_t n, int slices,
+                       const mxm_plan& p = kNoPlan) {
   if (m <= 0 || n <= 0 || k <= 0) return 0;
-  if (mode == MXM_MODE_F64) return f64_workspace(f64_dims(m, k, n));
-  if (emul_mode(mode))
-    return ozaki_layout(ozaki_dims_splitk(m, k, n, slices, mode_beta(mode), mode_rn(mode))).total;
-  if (mode == MXM_MODE_EMUL_FP8) return ozaki_layout(ozaki_dims_fp8(m, k, n, slices)).total;
+  if (mode == MXM_MODE_F64) return f64_workspace(native_dims(m, k, n, p));
+  if (emul_mode(mode)) return ozaki_layout(emul_dims(mode, m, k, n, slices, p)).total;
+  if (mode == MXM_MODE_EMUL_FP8) return ozaki_layout(fp8_dims(m, k, n, slices, p)).total;
   if (mode == MXM_MODE_BF16_F32ACC) return ozaki_layout(ozaki_dims(m, k, n, 1, 8)).total;
   return 0;
 }
 
 // Launch sequence of one product whose workspace is already in place.
 mxm_status run_gemm(int mode, const double* A, const double* B, double* C, int64_t m, int64_t k,
-                    int64_t n, int slices, uint8_t* ws, int* status, cudaStream_t s) {
+                    int64_t n, int slices, uint8_t* ws, int* status, cudaStream_t s,
+                    const mxm_plan& plan = kNoPlan) {
   if (m == 0 || n == 0) return MXM_OK;
   if (k == 0) return launch_zero_fill(C, m * n, s) == cudaSuccess ? MXM_OK : cuda_fail();
   cudaError_t e = cudaSuccess;
   if (mode == MXM_MODE_F64) {
-    const F64Dims d = f64_dims(m, k, n);
+    const F64Dims d = native_dims(m, k, n, plan);
     CallEvents* ce = profile_begin(s);
     profile_mark(ce, 1, s);
     e = launch_f64_pack(A, B, d, ws, s);
@@ -171,7 +218,7 @@ mxm_status run_gemm(int mode, const double* A, const double* B, double* C, int64
     if (e == cudaSuccess) e = launch_f64_gemm(ws, C, d, status, s);
     profile_mark(ce, 3, s);
   } else if (emul_mode(mode)) {
-    const OzakiDims d = ozaki_dims_splitk(m, k, n, slices, mode_beta(mode), mode_rn(mode));
+    const OzakiDims d = emul_dims(mode, m, k, n, slices, plan);
     const OzakiLayout L = ozaki_layout(d);
     uint64_t* rowbits = reinterpret_cast<uint64_t*>(ws + L.rowbits);
     uint64_t* colbits = reinterpret_cast<uint64_t*>(ws + L.colbits);
@@ -186,7 +233,7 @@ mxm_status run_gemm(int mode, const double* A, const double* B, double* C, int64
                             reinterpret_cast<uint64_t*>(ws + L.sums), status, s);
     profile_mark(ce, 3, s);
   } else if (mode == MXM_MODE_EMUL_FP8) {
-    const OzakiDims d = ozaki_dims_fp8(m, k, n, slices);
+    const OzakiDims d = fp8_dims(m, k, n, slices, plan);
     if (!ozaki_narrow(d.S, d.beta, d.Kt)) return MXM_ERR_UNSUPPORTED;
     const OzakiLayout L = ozaki_layout(d);
     uint64_t* rowbits = reinterpret_cast<uint64_t*>(ws + L.rowbits);
@@ -270,20 +317,35 @@ size_t mxm_workspace_size(int mode, int64_t m, int64_t k, int64_t n, int slices)
   return workspace_bytes(mode, m, k, n, slices);
 }
 
-mxm_status mxm_gemm(int mode, const double* A, const double* B, double* C, int64_t m, int64_t k,
-                    int64_t n, int slices, void* stream) {
+mxm_status mxm_gemm_plan(int mode, const double* A, const double* B, double* C, int64_t m,
+                         int64_t k, int64_t n, int slices, const mxm_plan* plan, void* stream) {
   NvtxRange nvtx_range("mxm_gemm");
+  const mxm_plan p = plan ? *plan : kNoPlan;
   mxm_status st = check_mode(mode, slices);
   if (st != MXM_OK) return st;
+  if (!plan_ok(mode, p)) return MXM_ERR_INVALID_ARG;
   st = check_gemm_args(A, B, C, m, k, n);
   if (st != MXM_OK || m == 0 || n == 0) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> lock(g_mutex);
   DeviceState* ds = nullptr;
   if ((st = current_state(&ds)) != MXM_OK) return st;
-  const size_t need = workspace_bytes(mode, m, k, n, slices);
+  const size_t need = workspace_bytes(mode, m, k, n, slices, p);
   if ((st = ensure_workspace(ds, need, s)) != MXM_OK) return st;
-  return run_gemm(mode, A, B, C, m, k, n, slices, static_cast<uint8_t*>(ds->ws), ds->status, s);
+  return run_gemm(mode, A, B, C, m, k, n, slices, static_cast<uint8_t*>(ds->ws), ds->status, s,
+                  p);
+}
+
+mxm_status mxm_gemm(int mode, const double* A, const double* B, double* C, int64_t m, int64_t k,
+                    int64_t n, int slices, void* stream) {
+  return mxm_gemm_plan(mode, A, B, C, m, k, n, slices, nullptr, stream);
+}
+
+size_t mxm_workspace_size_plan(int mode, int64_t m, int64_t k, int64_t n, int slices,
+                               const mxm_plan* plan) {
+  const mxm_plan p = plan ? *plan : kNoPlan;
+  if (check_mode(mode, slices) != MXM_OK || !plan_ok(mode, p)) return 0;
+  return workspace_bytes(mode, m, k, n, slices, p);
 }
 
 mxm_status mxm_f64(const double* A, const double* B, double* C, int64_t m, int64_t k, int64_t n,
@@ -447,6 +509,8 @@ static mxm_status gemm_host_panels(DeviceState* ds, int mode, const double* hA, 
       double* blk = dC + r0 * n + j * w * hp;  // h x wj, row-major, contiguous
       OzakiDims dg = ozaki_dims(hp, k, wj, slices, beta, rn);
       dg.pair = dp.pair;
+      dg.raster = dg.pair ? kPairRaster : kDefaultRaster;
+      dg.kb_alt = 1;
       cudaEvent_t done = eC[i * Q + j];
       if (cudaStreamWaitEvent(c, eBs[j], 0) != cudaSuccess ||
           launch_ozaki_gemm(aplanes, bplanes, rowbits, colbits, blk, dg, sums, ds->status, c) !=

@@ -111,9 +111,10 @@ __device__ __forceinline__ void dmma_16x8x4(double (&d)[4], double a0, double a1
       : "d"(a0), "d"(a1), "d"(b0));
 }
 
-__device__ __forceinline__ void tile_coords(int64_t tile, int64_t Mt, int64_t Nt, int64_t& tm,
-                                            int64_t& tn) {
-  constexpr int64_t G = 8;
+__device__ __forceinline__ void tile_coords(int64_t tile, int64_t Mt, int64_t Nt, int64_t G,
+                                            int64_t& tm, int64_t& tn) {
+  // groups of G tile-rows, column-major inside a group (L2 reuse of the
+  // operand tiles of the CTAs working at the same time)
   const int64_t per_group = G * Nt;
   const int64_t grp = tile / per_group;
   const int64_t first = grp * G;
@@ -141,11 +142,12 @@ struct F64Single {
   double* C;
   double* partials;
   int64_t m, n, Mt, Nt, Kt, splits;
+  int64_t raster;
   __device__ __forceinline__ int64_t count() const { return Mt * Nt * splits; }
   __device__ __forceinline__ F64Tile tile(int64_t t) const {
     const int64_t tile = t / splits, sp = t - tile * splits;
     int64_t tm, tn;
-    tile_coords(tile, Mt, Nt, tm, tn);
+    tile_coords(tile, Mt, Nt, raster, tm, tn);
     const int64_t kb0 = Kt * sp / splits, kb1 = Kt * (sp + 1) / splits;
     const double* a = apack + (tm * Kt + kb0) * (BM * BK);
     const double* b = bpack + (tn * Kt + kb0) * (BN * BK);
@@ -350,7 +352,8 @@ cudaError_t launch_f64_gemm(uint8_t* ws, double* C, const F64Dims& d, int* statu
   const double* apack = reinterpret_cast<const double*>(ws);
   const double* bpack = apack + d.Mt * d.Kt * (BM * BK);
   double* partials = reinterpret_cast<double*>(ws + f64_partials_offset(d));
-  F64Single tiles{apack, bpack, C, partials, d.m, d.n, d.Mt, d.Nt, d.Kt, d.splits};
+  F64Single tiles{apack, bpack, C, partials, d.m, d.n, d.Mt, d.Nt, d.Kt, d.splits,
+                  d.raster > 0 ? d.raster : kDefaultRaster};
   const int64_t count = d.Mt * d.Nt * d.splits;
   const int64_t grid = count < sm_count() ? count : sm_count();
   cudaError_t e = launch_f64_gemm_t(tiles, grid, status, s);

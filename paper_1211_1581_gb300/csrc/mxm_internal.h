@@ -97,7 +97,16 @@ struct OzakiDims {
                        //    nearest (beta = 8, scale exponent + 1, |d| <= 128)
   int pair;            // 1: the slice GEMM runs on CTA pairs (cta_group::2) and
                        //    the B digit tiles are written in the halves layout
+  int raster;          // tile-rows (pair-rows on CTA pairs) per group of the
+                       //    persistent walk over C tiles
+  int kb_alt;          // 1: alternate the k-block direction from one diagonal
+                       //    (pair) to the next
 };
+
+// Default walk: groups of 8 tile-rows (4 pair-rows on CTA pairs); the
+// emulated modes alternate the k-block direction between diagonal pairs.
+constexpr int kDefaultRaster = 8;
+constexpr int kPairRaster = 4;
 
 inline OzakiDims ozaki_dims(int64_t m, int64_t k, int64_t n, int S, int beta, bool rn = false) {
   OzakiDims d;
@@ -110,6 +119,8 @@ inline OzakiDims ozaki_dims(int64_t m, int64_t k, int64_t n, int S, int beta, bo
   d.fp8 = 0;
   d.rn = rn ? 1 : 0;
   d.pair = d.Mt >= 2 ? 1 : 0;
+  d.raster = kDefaultRaster;
+  d.kb_alt = 0;
   return d;
 }
 
@@ -259,6 +270,7 @@ constexpr int kF64TileBytes = kF64BM * kF64BK * 8;  // 16 KiB (BM == BN)
 struct F64Dims {
   int64_t m, k, n, Mt, Nt, Kt;
   int64_t splits;  // k ranges per C tile (1: no split)
+  int raster;      // tile-rows per group of the persistent walk over C tiles
 };
 
 inline F64Dims f64_dims(int64_t m, int64_t k, int64_t n) {
@@ -268,6 +280,7 @@ inline F64Dims f64_dims(int64_t m, int64_t k, int64_t n) {
   d.Nt = (n + kF64BN - 1) / kF64BN;
   d.Kt = (k + kF64BK - 1) / kF64BK;
   d.splits = splitk_count(d.Mt * d.Nt, d.Kt, 8);
+  d.raster = kDefaultRaster;
   return d;
 }
 

@@ -593,11 +593,10 @@ struct __align__(1024) GemmSmem {
 
 constexpr size_t kGemmSmemBytes = sizeof(GemmSmem) + 1024;
 
-__device__ __forceinline__ void tile_coords(int64_t tile, int64_t Mt, int64_t Nt, int64_t& tm,
-                                            int64_t& tn) {
-  // groups of 8 tile-rows, column-major inside a group: CTAs working at the
+__device__ __forceinline__ void tile_coords(int64_t tile, int64_t Mt, int64_t Nt, int64_t G,
+                                            int64_t& tm, int64_t& tn) {
+  // groups of G tile-rows, column-major inside a group: CTAs working at the
   // same time share A tiles and B tiles in L2
-  constexpr int64_t G = 8;
   const int64_t per_group = G * Nt;
   const int64_t grp = tile / per_group;
   const int64_t first = grp * G;
@@ -638,12 +637,20 @@ struct OzSingle {
   long long* spill = nullptr;  // paired kernel: per-CTA int64 partials of the two diagonals
   int spill_every = 0;         // window drains after which a diagonal's int32 sum spills
   int eoff = 0;                // added to e_i + f_j in the final scaling (2: balanced digits)
+  int64_t raster = kDefaultRaster;  // tile-rows (pair-rows) per group of the tile walk
+  bool kb_alt = false;         // alternate the k-block direction between diagonal (pair)s
+  // Address k-block of the it-th k-block of diagonal (pair) q: every other
+  // one walks k backwards, so it starts on the tiles the previous one read
+  // last (still in L2).  The exact integer sums do not depend on the order.
+  __device__ __forceinline__ int64_t kblock(int q, int64_t it, int64_t Kt_) const {
+    return (kb_alt && (q & 1)) ? Kt_ - 1 - it : it;
+  }
   __device__ __forceinline__ int64_t count() const { return Mt * Nt * splits; }
   // Unit t: C tile t / splits, k range t % splits.
   __device__ __forceinline__ OzTile tile(int64_t t) const {
     const int64_t tt = t / splits, sp = t - tt * splits;
     int64_t tm, tn;
-    tile_coords(tt, Mt, Nt, tm, tn);
+    tile_coords(tt, Mt, Nt, raster, tm, tn);
     return tile_at(tm, tn, sp);
   }
   // CTA pairs (no split-k): unit t is the 256 x 128 C tile of tile-rows
@@ -653,7 +660,7 @@ struct OzSingle {
   __device__ __forceinline__ int64_t pair_count() const { return (Mt + 1) / 2 * Nt; }
   __device__ __forceinline__ OzTile pair_tile(int64_t t, uint32_t rank) const {
     int64_t tp, tn;
-    tile_coords(t, (Mt + 1) / 2, Nt, tp, tn);
+    tile_coords(t, (Mt + 1) / 2, Nt, raster, tp, tn);
     return tile_at(2 * tp + rank, tn, 0);
   }
   __device__ __forceinline__ OzTile tile_at(int64_t tm, int64_t tn, int64_t sp) const {
@@ -693,6 +700,7 @@ struct OzGrouped {
   const uint8_t* ws;
   int eoff;  // 2 for balanced 8-bit digits
   __device__ __forceinline__ int64_t count() const { return hdr->valid ? hdr->tiles : 0; }
+  __device__ __forceinline__ int64_t kblock(int, int64_t it, int64_t) const { return it; }
   __device__ __forceinline__ OzTile tile(int64_t t) const {
     const int64_t p = grouped_find(recs, hdr->count, t, &GroupedProblem::tile_begin);
     const GroupedProblem& r = recs[p];
@@ -856,9 +864,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
               }
               mbar_arrive_expect_tx(&sm.full[stage], 2 * kOzTileBytes);
-              bulk_g2s(sm.a[stage], j.a + (s - 1) * j.a_slice + kb * kOzTileBytes, kOzTileBytes,
+              const int64_t kbx = tiles.kblock(S + 1 - g, kb, j.Kt);
+              bulk_g2s(sm.a[stage], j.a + (s - 1) * j.a_slice + kbx * kOzTileBytes, kOzTileBytes,
                        &sm.full[stage]);
-              bulk_g2s(sm.b[stage], j.b + (g - s - 1) * j.b_slice + kb * kOzTileBytes,
+              bulk_g2s(sm.b[stage], j.b + (g - s - 1) * j.b_slice + kbx * kOzTileBytes,
                        kOzTileBytes, &sm.full[stage]);
               if (++stage == kStages) {
                 stage = 0;
@@ -1263,7 +1272,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
         for (int q = 0; q < ngroups && ok; ++q) {
           const int g = S + 1 - 2 * q;
           for (int64_t kb = 0; kb < j.Kt && ok; ++kb) {
-            const size_t koff = static_cast<size_t>(kb) * kTile;
+            const size_t koff = static_cast<size_t>(tiles.kblock(q, kb, j.Kt)) * kTile;
             ok = load(rb, sm.b, sm.b_full, sm.b_empty, j.b + (g - 2) * j.b_slice + koff + bhalf,
                       kBTile);
             for (int s = 1; s <= g - 1 && ok; ++s) {
@@ -1810,6 +1819,8 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
                  d.Mt,    d.Nt,    d.Kt,    sums,    splits, d.S,
                  static_cast<int64_t>(ozaki_tile_bytes(d))};
   tiles.eoff = d.rn ? 2 : 0;
+  tiles.raster = d.raster > 0 ? d.raster : kDefaultRaster;
+  tiles.kb_alt = d.kb_alt != 0;
   const int64_t count = d.Mt * d.Nt * splits;
   const int64_t grid = count < sm_count() ? count : sm_count();
   if (d.fp8) {

@@ -33,6 +33,18 @@ MODE_BF16_F32ACC = 4
 MODE_EMUL_FP8 = 5
 MODE_EMUL_RN8 = 6
 
+
+
+class Plan(ctypes.Structure):
+    """mxm_plan: how one product is laid out (see include/mxm.h); all zero
+    is the library's own rule."""
+    _fields_ = [("raster", ctypes.c_int32), ("kb_order", ctypes.c_int32),
+                ("cta", ctypes.c_int32), ("splitk", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
 # Every symbol include/mxm.h declares, with (restype, argtypes).
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
@@ -44,6 +56,8 @@ SIGNATURES = {
     "mxm_f64": (_I, [_P, _P, _P, _I64, _I64, _I64, _P]),
     "mxm_f64_emul": (_I, [_P, _P, _P, _I64, _I64, _I64, _I, _P]),
     "mxm_gemm": (_I, [_I, _P, _P, _P, _I64, _I64, _I64, _I, _P]),
+    "mxm_gemm_plan": (_I, [_I, _P, _P, _P, _I64, _I64, _I64, _I, ctypes.POINTER(Plan), _P]),
+    "mxm_workspace_size_plan": (_SZ, [_I, _I64, _I64, _I64, _I, ctypes.POINTER(Plan)]),
     "mxm_gemm_host": (_I, [_I, _P, _P, _P, _I64, _I64, _I64, _I, _P]),
     "mxm_workspace_size": (_SZ, [_I, _I64, _I64, _I64, _I]),
     "mxm_set_workspace": (_I, [_P, _SZ, _P]),
@@ -133,6 +147,22 @@ def mxm_gemm(mode: int, A, B, C, slices: int = 7, stream=None):
                          int(slices), _stream_ptr(stream))
     _check(st, "mxm_gemm")
     return C
+
+
+def mxm_gemm_plan(mode: int, A, B, C, slices: int = 7, plan: Plan | None = None, stream=None):
+    """mxm_gemm under an explicit plan (None: the library's rule)."""
+    m, k, n = _operands(A, B, C)
+    st = load().mxm_gemm_plan(int(mode), A.data_ptr(), B.data_ptr(), C.data_ptr(), m, k, n,
+                              int(slices), ctypes.byref(plan) if plan is not None else None,
+                              _stream_ptr(stream))
+    _check(st, "mxm_gemm_plan")
+    return C
+
+
+def mxm_workspace_size_plan(mode: int, m: int, k: int, n: int, slices: int = 7,
+                            plan: Plan | None = None) -> int:
+    return int(load().mxm_workspace_size_plan(int(mode), m, k, n, int(slices),
+                                              ctypes.byref(plan) if plan is not None else None))
 
 
 def mxm_f64(A, B, C, stream=None):
