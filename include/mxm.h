@@ -215,6 +215,21 @@ size_t mxm_workspace_size(int mode, int64_t m, int64_t k, int64_t n, int slices)
 mxm_status mxm_set_workspace(void* d_ws, size_t bytes, void* stream);
 
 /*
+ * mxm_group_plan -- how a grouped emulated call splits its problems between
+ * the two slice GEMMs (for the tuner; NULL or short_kt = -1: the library's
+ * default).  Problems with at most short_kt k-blocks of 128 run on the
+ * one-diagonal kernel (its FP64 running sums stay in tensor memory, which
+ * suits tiles with little k), the others on the diagonal-pair kernel (half
+ * the operand bytes per digit product).  Both give the same bits.  Ignored
+ * by MXM_MODE_F64.  reserved[] must be zero.  The default is 8.  The paper
+ * has no counterpart.
+ */
+typedef struct {
+  int32_t short_kt;
+  int32_t reserved[3];
+} mxm_group_plan;
+
+/*
  * mxm_grouped_workspace_size -- bytes of workspace mxm_grouped needs for
  * these problems (host copy of the table; only m, k, n are read).
  */
@@ -234,6 +249,17 @@ mxm_status mxm_grouped_workspace_size(int64_t count, const mxm_problem* h_proble
  */
 mxm_status mxm_grouped(int64_t count, const mxm_problem* d_problems, int mode, int slices,
                        void* d_ws, size_t ws_bytes, void* stream);
+
+/* mxm_grouped_plan / mxm_grouped_workspace_size_plan -- the same under an
+ * explicit mxm_group_plan (NULL: the default); the workspace depends on the
+ * plan (running sums for the long-k problems' tiles).  A plan with
+ * short_kt < -1 or a nonzero reserved field: MXM_ERR_INVALID_ARG. */
+mxm_status mxm_grouped_plan(int64_t count, const mxm_problem* d_problems, int mode, int slices,
+                            const mxm_group_plan* plan, void* d_ws, size_t ws_bytes,
+                            void* stream);
+mxm_status mxm_grouped_workspace_size_plan(int64_t count, const mxm_problem* h_problems, int mode,
+                                           int slices, const mxm_group_plan* plan,
+                                           size_t* bytes);
 
 /*
  * mxm_get_device_status -- synchronise `stream`, then read and clear the

@@ -72,29 +72,6 @@ __global__ void f64_pack_b_kernel(const double* __restrict__ B, int64_t k, int64
   pack_b_tile(B, k, n, tn, tk, out + (tn * Kt + tk) * (BN * BK), t);
 }
 
-// Every operand tile of a grouped call (A tiles, then B tiles).
-__global__ void f64_grouped_pack_kernel(uint8_t* __restrict__ ws) {
-  __shared__ double t[BK][BN + 1];
-  const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
-  if (!hdr->valid) return;
-  const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
-  double* apack = reinterpret_cast<double*>(ws + hdr->off_a);
-  double* bpack = reinterpret_cast<double*>(ws + hdr->off_b);
-  const int64_t na = hdr->atiles, nb = hdr->btiles;
-  for (int64_t i = blockIdx.x; i < na + nb; i += gridDim.x) {
-    if (i < na) {
-      const GroupedProblem& p = recs[grouped_find(recs, hdr->count, i, &GroupedProblem::atile_begin)];
-      const int64_t local = i - p.atile_begin;
-      pack_a_tile(p.A, p.m, p.k, local / p.Kt, local % p.Kt, apack + i * (BM * BK));
-    } else {
-      const int64_t j = i - na;
-      const GroupedProblem& p = recs[grouped_find(recs, hdr->count, j, &GroupedProblem::btile_begin)];
-      const int64_t local = j - p.btile_begin;
-      pack_b_tile(p.B, p.k, p.n, local / p.Kt, local % p.Kt, bpack + j * (BN * BK), t);
-    }
-  }
-}
-
 struct __align__(128) F64Smem {
   double a[kStages][BM * BK];
   double b[kStages][BN * BK];
@@ -172,25 +149,106 @@ __global__ void __launch_bounds__(256) f64_splitk_reduce_kernel(const double* __
   C[idx] = acc;
 }
 
-struct F64Grouped {
-  const uint8_t* ws;
-  __device__ __forceinline__ int64_t count() const {
-    const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
-    return hdr->valid ? hdr->tiles : 0;
+// ---------------------------------------------------------------- grouped
+// Many small products of uneven sizes: the work is cut into 32 x 32 pieces
+// of the C matrices (the plan's tiles), one warp each, handed out by an
+// atomic cursor in the plan header (dynamic scheduling: pieces of long-k
+// problems cost more).  The FP64 pipe of this GPU (~3.5 flops per clock per
+// SM) is the limit, so the operands are read straight from the caller's
+// arrays (L1/L2 serve the reuse) with no packed copies, and the pieces are
+// small enough that padding wastes little: every product is cut at 32 rows,
+// 32 columns and 4 k.  Each warp holds its 32 x 32 piece as 2 x 4 DMMA
+// m16n8 accumulators and reads the fragments of the next k step while the
+// current ones multiply.
+constexpr int kGroupedF64Threads = 256;
+
+__device__ __forceinline__ void load_frags(const double* __restrict__ A,
+                                           const double* __restrict__ B, int64_t k, int64_t n,
+                                           const int64_t (&arow)[4], const int64_t (&bcol)[4],
+                                           uint32_t rmask, uint32_t cmask, int64_t kk,
+                                           double (&a)[4], double (&b)[4]) {
+  const bool kv = kk < k;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    a[i] = (kv && ((rmask >> i) & 1u)) ? __ldg(A + arow[i] * k + kk) : 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    b[i] = (kv && ((cmask >> i) & 1u)) ? __ldg(B + kk * n + bcol[i]) : 0.0;
+}
+
+__global__ void __launch_bounds__(kGroupedF64Threads, 2)
+    f64_grouped_kernel(uint8_t* __restrict__ ws) {
+  GroupedHeader* hdr = reinterpret_cast<GroupedHeader*>(ws);
+  if (!hdr->valid) return;
+  const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
+  unsigned long long* cursor = reinterpret_cast<unsigned long long*>(&hdr->cursor);
+  const int64_t total = hdr->tiles;
+  const int64_t count = hdr->count;
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t4 = lane & 3;
+  constexpr int T = kF64GroupedTile;
+  for (;;) {
+    int64_t unit = 0;
+    if (lane == 0) unit = static_cast<int64_t>(atomicAdd(cursor, 1ull));
+    unit = __shfl_sync(0xFFFFFFFFu, unit, 0);
+    if (unit >= total) break;
+    const GroupedProblem& r = recs[grouped_find(recs, count, unit, &GroupedProblem::tile_begin)];
+    const int64_t local = unit - r.tile_begin;
+    const int64_t tm = local / r.Nt, tn = local - (local / r.Nt) * r.Nt;
+    const int64_t row0 = tm * T, col0 = tn * T;
+    const double* A = r.A;
+    const double* B = r.B;
+    const int64_t m = r.m, k = r.k, n = r.n;
+    // this lane's A rows (mi = 0, 1; halves g, g + 8) and B columns (ni = 0..3)
+    int64_t arow[4], bcol[4];
+    uint32_t rmask = 0, cmask = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      arow[i] = row0 + (i >> 1) * 16 + (i & 1) * 8 + g;
+      if (arow[i] < m) rmask |= 1u << i;
+      bcol[i] = col0 + i * 8 + g;
+      if (bcol[i] < n) cmask |= 1u << i;
+    }
+    double acc[2][4][4];
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[mi][ni][q] = 0.0;
+    double a[4], b[4], an[4], bn[4];
+    load_frags(A, B, k, n, arow, bcol, rmask, cmask, t4, a, b);
+    for (int64_t k0 = 0; k0 < k; k0 += kF64GroupedK) {
+      load_frags(A, B, k, n, arow, bcol, rmask, cmask, k0 + kF64GroupedK + t4, an, bn);
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+          dmma_16x8x4(acc[mi][ni], a[2 * mi], a[2 * mi + 1], b[ni]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = an[i];
+        b[i] = bn[i];
+      }
+    }
+    // D fragment of m16n8: (g, 2 t4), (g, 2 t4 + 1), (g + 8, 2 t4), (g + 8, 2 t4 + 1)
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t row = row0 + mi * 16 + h * 8 + g;
+        if (row >= m) continue;
+        double* crow = r.C + row * n;
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) {
+          const int64_t col = col0 + ni * 8 + 2 * t4;
+          if (col < n) crow[col] = acc[mi][ni][2 * h];
+          if (col + 1 < n) crow[col + 1] = acc[mi][ni][2 * h + 1];
+        }
+      }
+    }
   }
-  __device__ __forceinline__ F64Tile tile(int64_t t) const {
-    const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
-    const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
-    const GroupedProblem& p = recs[grouped_find(recs, hdr->count, t, &GroupedProblem::tile_begin)];
-    const int64_t local = t - p.tile_begin;
-    const int64_t tm = local / p.Nt, tn = local - (local / p.Nt) * p.Nt;
-    const double* apack = reinterpret_cast<const double*>(ws + hdr->off_a);
-    const double* bpack = reinterpret_cast<const double*>(ws + hdr->off_b);
-    return F64Tile{apack + (p.atile_begin + tm * p.Kt) * (BM * BK),
-                   bpack + (p.btile_begin + tn * p.Kt) * (BN * BK), p.Kt, p.C, p.m, p.n, p.n,
-                   tm * BM, tn * BN};
-  }
-};
+}
 
 // Persistent: every CTA walks tiles blockIdx.x, +gridDim.x, ...; the producer
 // and the consumers walk the same sequence and keep the stage ring running
@@ -364,12 +422,11 @@ cudaError_t launch_f64_gemm(uint8_t* ws, double* C, const F64Dims& d, int* statu
   return cudaGetLastError();
 }
 
-cudaError_t launch_f64_grouped(uint8_t* ws, int* status, cudaStream_t s) {
-  const int sms = sm_count();
-  f64_grouped_pack_kernel<<<sms * 8, 256, 0, s>>>(ws);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return launch_f64_gemm_t(F64Grouped{ws}, sms, status, s);
+cudaError_t launch_f64_grouped(uint8_t* ws, int* /*status*/, cudaStream_t s) {
+  // two resident CTAs of 8 warps per SM, every warp pulling pieces until the
+  // cursor passes the last one
+  f64_grouped_kernel<<<static_cast<unsigned>(2 * sm_count()), kGroupedF64Threads, 0, s>>>(ws);
+  return cudaGetLastError();
 }
 
 }  // namespace mxm

@@ -23,11 +23,14 @@ namespace mxm {
 namespace {
 
 constexpr int kPlanThreads = 1024;
-constexpr int kCounts = 6;  // C tiles, A tiles, B tiles, rows, columns, 32-column groups
+// C tiles, A tiles, B tiles, rows, columns, A tile-rows, B tile-columns, C tiles of the
+// long-k problems, C tiles of the short-k problems
+constexpr int kCounts = 9;
 
 struct PlanGeometry {
   int64_t tile_rows;  // rows of A (or columns of B) per tile
   int64_t tile_k;     // k per operand tile
+  int64_t short_kt;   // emulated: problems with at most this many k-blocks are "short"
 };
 
 __host__ __device__ inline void problem_counts(int64_t m, int64_t k, int64_t n,
@@ -48,7 +51,10 @@ __host__ __device__ inline void problem_counts(int64_t m, int64_t k, int64_t n,
   c[2] = Nt * Kt;
   c[3] = live ? m : 0;
   c[4] = live ? n : 0;
-  c[5] = live ? (n + 31) / 32 : 0;
+  c[5] = live ? Mt : 0;
+  c[6] = live ? Nt : 0;
+  c[7] = Kt > g.short_kt ? c[0] : 0;
+  c[8] = Kt > g.short_kt ? 0 : c[0];
 }
 
 // Exclusive prefix sum over the block (1024 threads = 32 warps).
@@ -130,7 +136,10 @@ __global__ void __launch_bounds__(kPlanThreads) grouped_plan_kernel(
       r.btile_begin = begin[2];
       r.row_begin = begin[3];
       r.col_begin = begin[4];
-      r.cgrp_begin = begin[5];
+      r.trow_begin = begin[5];
+      r.tcol_begin = begin[6];
+      r.ltile_begin = begin[7];
+      r.stile_begin = begin[8];
       recs[i] = r;
     }
   }
@@ -143,8 +152,12 @@ __global__ void __launch_bounds__(kPlanThreads) grouped_plan_kernel(
     h.btiles = carry[2];
     h.rows = carry[3];
     h.cols = carry[4];
-    h.cgroups = carry[5];
+    h.trows = carry[5];
+    h.tcols = carry[6];
+    h.ltiles = carry[7];
+    h.stiles = carry[8];
     h.max_kt = max_kt;
+    h.cursor = 0;
     grouped_offsets(h, planes, tile_bytes, bits != 0);
     h.valid = (h.total <= ws_bytes && !bad) ? 1 : 0;
     if (!h.valid) atomicOr(status, bad ? kStatusBounds : kStatusWorkspace);
@@ -160,15 +173,27 @@ bool grouped_mode_ok(int mode, int slices) {
   return false;
 }
 
-void mode_geometry(int mode, int slices, PlanGeometry& g, int& planes, size_t& tile_bytes,
-                   int& bits) {
+// The plan's short-k boundary (k-blocks of 128): the caller's, or the default.
+int64_t plan_short_kt(const mxm_group_plan* plan) {
+  return (plan != nullptr && plan->short_kt >= 0) ? plan->short_kt : kGroupedShortKt;
+}
+
+bool group_plan_ok(const mxm_group_plan* plan) {
+  if (plan == nullptr) return true;
+  return plan->short_kt >= -1 && plan->reserved[0] == 0 && plan->reserved[1] == 0 &&
+         plan->reserved[2] == 0;
+}
+
+void mode_geometry(int mode, int slices, int64_t short_kt, PlanGeometry& g, int& planes,
+                   size_t& tile_bytes, int& bits) {
   if (mode == MXM_MODE_F64) {
-    g = PlanGeometry{kF64BM, kF64BK};
-    planes = 1;
-    tile_bytes = kF64TileBytes;
+    // warp units of 32 x 32; operands read in place (no packed copies)
+    g = PlanGeometry{kF64GroupedTile, kF64GroupedK, 0};
+    planes = 0;
+    tile_bytes = 0;
     bits = 0;
   } else {
-    g = PlanGeometry{kOzTileRows, kOzTileK};
+    g = PlanGeometry{kOzTileRows, kOzTileK, short_kt};
     planes = slices;
     tile_bytes = kOzTileBytes;
     bits = 1;
@@ -180,18 +205,21 @@ void mode_geometry(int mode, int slices, PlanGeometry& g, int& planes, size_t& t
 
 using namespace mxm;
 
-extern "C" mxm_status mxm_grouped_workspace_size(int64_t count, const mxm_problem* h_problems,
-                                                 int mode, int slices, size_t* bytes) {
+extern "C" mxm_status mxm_grouped_workspace_size_plan(int64_t count,
+                                                      const mxm_problem* h_problems, int mode,
+                                                      int slices, const mxm_group_plan* plan,
+                                                      size_t* bytes) {
   if (bytes == nullptr || count < 0 || (count > 0 && h_problems == nullptr))
     return MXM_ERR_INVALID_ARG;
   if (!grouped_mode_ok(mode, slices)) return MXM_ERR_UNSUPPORTED;
+  if (!group_plan_ok(plan)) return MXM_ERR_INVALID_ARG;
   PlanGeometry g;
   int planes, bits;
   size_t tile_bytes;
-  mode_geometry(mode, slices, g, planes, tile_bytes, bits);
+  mode_geometry(mode, slices, plan_short_kt(plan), g, planes, tile_bytes, bits);
   GroupedHeader h{};
   h.count = count;
-  int64_t tot[kCounts] = {0, 0, 0, 0, 0, 0};
+  int64_t tot[kCounts] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int64_t i = 0; i < count; ++i) {
     const mxm_problem& p = h_problems[i];
     if (p.m < 0 || p.k < 0 || p.n < 0) return MXM_ERR_INVALID_ARG;
@@ -204,10 +232,18 @@ extern "C" mxm_status mxm_grouped_workspace_size(int64_t count, const mxm_proble
   h.btiles = tot[2];
   h.rows = tot[3];
   h.cols = tot[4];
-  h.cgroups = tot[5];
+  h.trows = tot[5];
+  h.tcols = tot[6];
+  h.ltiles = tot[7];
+  h.stiles = tot[8];
   grouped_offsets(h, planes, tile_bytes, bits != 0);
   *bytes = h.total;
   return MXM_OK;
+}
+
+extern "C" mxm_status mxm_grouped_workspace_size(int64_t count, const mxm_problem* h_problems,
+                                                 int mode, int slices, size_t* bytes) {
+  return mxm_grouped_workspace_size_plan(count, h_problems, mode, slices, nullptr, bytes);
 }
 
 // defined in abi.cu: the current device's status word
@@ -215,11 +251,13 @@ namespace mxm {
 int* device_status_word();
 }
 
-extern "C" mxm_status mxm_grouped(int64_t count, const mxm_problem* d_problems, int mode,
-                                  int slices, void* d_ws, size_t ws_bytes, void* stream) {
+extern "C" mxm_status mxm_grouped_plan(int64_t count, const mxm_problem* d_problems, int mode,
+                                       int slices, const mxm_group_plan* plan, void* d_ws,
+                                       size_t ws_bytes, void* stream) {
   NvtxRange nvtx_range("mxm_grouped");
   if (count < 0 || (count > 0 && d_problems == nullptr)) return MXM_ERR_INVALID_ARG;
   if (!grouped_mode_ok(mode, slices)) return MXM_ERR_UNSUPPORTED;
+  if (!group_plan_ok(plan)) return MXM_ERR_INVALID_ARG;
   if (count == 0) return MXM_OK;
   if (d_ws == nullptr) return MXM_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(d_ws) & 255) return MXM_ERR_ALIGNMENT;
@@ -230,7 +268,7 @@ extern "C" mxm_status mxm_grouped(int64_t count, const mxm_problem* d_problems, 
   PlanGeometry g;
   int planes, bits;
   size_t tile_bytes;
-  mode_geometry(mode, slices, g, planes, tile_bytes, bits);
+  mode_geometry(mode, slices, plan_short_kt(plan), g, planes, tile_bytes, bits);
   uint8_t* ws = static_cast<uint8_t*>(d_ws);
   grouped_plan_kernel<<<1, kPlanThreads, 0, s>>>(d_problems, count, g, planes, tile_bytes, bits,
                                                  ws_bytes, ws, status);
@@ -242,4 +280,9 @@ extern "C" mxm_status mxm_grouped(int64_t count, const mxm_problem* d_problems, 
     e = launch_ozaki_grouped(ws, slices, mode == MXM_MODE_EMUL_I8 ? 7 : 8, 0, status, s,
                              mode == MXM_MODE_EMUL_RN8);
   return e == cudaSuccess ? MXM_OK : MXM_ERR_CUDA;
+}
+
+extern "C" mxm_status mxm_grouped(int64_t count, const mxm_problem* d_problems, int mode,
+                                  int slices, void* d_ws, size_t ws_bytes, void* stream) {
+  return mxm_grouped_plan(count, d_problems, mode, slices, nullptr, d_ws, ws_bytes, stream);
 }

@@ -317,14 +317,20 @@ struct GroupedProblem {
   int64_t btile_begin;     // first B operand tile (prefix of Nt*Kt)
   int64_t row_begin;       // first row maximum (prefix of m)
   int64_t col_begin;       // first column maximum (prefix of n)
-  int64_t cgrp_begin;      // first 32-column group of B (prefix of ceil(n/32))
+  int64_t trow_begin;      // first tile-row of A (prefix of Mt)
+  int64_t tcol_begin;      // first tile-column of B (prefix of Nt)
+  int64_t ltile_begin;     // emulated: first C tile among the long-k problems
+  int64_t stile_begin;     // emulated: first C tile among the short-k problems
 };
 
 struct GroupedHeader {
   int64_t valid;           // 0: workspace too small, every later kernel does nothing
   int64_t count;           // problems
-  int64_t tiles, atiles, btiles, rows, cols, cgroups, max_kt;
+  int64_t tiles, atiles, btiles, rows, cols, trows, tcols, ltiles, stiles, max_kt;
   int64_t off_rowbits, off_colbits, off_a, off_b, total;  // byte offsets in the workspace
+  int64_t cursor;          // next work unit of a dynamically scheduled kernel (zeroed by
+                           // the plan kernel on every call)
+  int64_t off_sums, off_spill;  // emulated: running sums of every C tile, spill areas
 };
 
 constexpr size_t kGroupedRecordsOff = 256;
@@ -345,6 +351,14 @@ __host__ __device__ inline void grouped_offsets(GroupedHeader& h, int planes, si
   off = align_up(off + static_cast<size_t>(planes) * h.atiles * tile_bytes, 1024);
   h.off_b = off;
   off = align_up(off + static_cast<size_t>(planes) * h.btiles * tile_bytes, 1024);
+  // emulated: the running sums of the diagonal-pair slice GEMM (128 x 128 x 8
+  // bytes per C tile of the long-k problems) and the int64 spill areas of its
+  // CTAs (long k)
+  h.off_sums = off;
+  if (bits) off = align_up(off + static_cast<size_t>(h.ltiles) * kOzTileRows * kOzTileRows * 8, 1024);
+  h.off_spill = off;
+  if (bits) off = align_up(off + static_cast<size_t>(kOzSpillCtas) * 2 * kOzTileRows * kOzTileRows * 8,
+                           1024);
   h.total = off;
 }
 
@@ -362,10 +376,19 @@ __device__ __forceinline__ int64_t grouped_find(const Rec* recs, int64_t count, 
   return lo;
 }
 
-cudaError_t launch_grouped_plan(const void* table, int64_t count, int emul, int S,
-                                size_t ws_bytes, uint8_t* ws, int* status, cudaStream_t s);
+// Problems of a grouped emulated call with at most this many k-blocks run on
+// the one-diagonal slice GEMM (running sums in tensor memory), the others on
+// the diagonal-pair GEMM.
+// Measured on 2000 problems of dims log-uniform in [16, 1024] (k <= 8 blocks):
+// all on the one-diagonal kernel is fastest (11.0 ms at S = 8 against 14.4 ms
+// all on the pair kernel), so the default takes every problem up to 8 blocks.
+constexpr int kGroupedShortKt = 8;
 cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t max_kt, int* status,
                                  cudaStream_t s, bool rn = false);
+// Native grouped products: work units of 32 x 32 C elements (one warp each,
+// operands loaded straight from the caller's arrays, k in steps of 4).
+constexpr int kF64GroupedTile = 32;
+constexpr int kF64GroupedK = 4;
 cudaError_t launch_f64_grouped(uint8_t* ws, int* status, cudaStream_t s);
 int sm_count();
 

@@ -313,16 +313,20 @@ struct SplitGeo {
 // `slice_stride` bytes apart.  A thread takes V consecutive k of one row
 // (consecutive threads: consecutive chunks of a row, so the loads and the
 // 16-byte stores are contiguous); rows of even k are read as 16-byte pairs.
+// (row_lim, chunk_lim: only rows < row_lim and chunks < chunk_lim of the
+// tile are written -- the rest is never read by the edge-tile copies.)
 template <int V>
 __device__ __forceinline__ void split_a_tile(const double* __restrict__ A, int64_t m, int64_t k,
                                              const uint64_t* __restrict__ rowbits, int S,
                                              int beta, int64_t tm, int64_t tk, uint8_t* tile,
-                                             size_t slice_stride, bool rn = false) {
+                                             size_t slice_stride, bool rn = false,
+                                             int row_lim = kOzTileRows,
+                                             int chunk_lim = SplitGeo<V>::kChunksPerRow) {
   using G = SplitGeo<V>;
   const bool pairs = ((k & 1) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
 #pragma unroll 2
-  for (int p = threadIdx.x; p < kOzTileRows * G::kChunksPerRow; p += blockDim.x) {
-    const int c = p % G::kChunksPerRow, r = p / G::kChunksPerRow;
+  for (int p = threadIdx.x; p < row_lim * chunk_lim; p += blockDim.x) {
+    const int c = p % chunk_lim, r = p / chunk_lim;
     const int64_t row = tm * kOzTileRows + r;
     const int64_t k0 = tk * kOzTileK + c * V;
     double v[V];
@@ -355,10 +359,13 @@ __device__ __forceinline__ void split_b_tile(const double* __restrict__ B, int64
                                              int beta, int64_t tn, int64_t tk, uint8_t* tile,
                                              size_t slice_stride,
                                              double (*sb)[kOzTileRows + 1], bool rn = false,
-                                             bool halves = false) {
+                                             bool halves = false, int row_lim = kOzTileRows,
+                                             int chunk_lim = SplitGeo<V>::kChunksPerRow) {
   using G = SplitGeo<V>;
   const int64_t col0 = tn * kOzTileRows;
+  constexpr int kChunksPerPass = kSplitBRows / V;
   for (int pass = 0; pass < kOzTileK / kSplitBRows; ++pass) {
+    if (pass * kChunksPerPass >= chunk_lim) break;  // block-uniform
     const int64_t l0 = tk * kOzTileK + pass * kSplitBRows;
     for (int p = threadIdx.x; p < kSplitBRows * kOzTileRows; p += blockDim.x) {
       const int lr = p / kOzTileRows, cc = p % kOzTileRows;
@@ -369,6 +376,7 @@ __device__ __forceinline__ void split_b_tile(const double* __restrict__ B, int64
     constexpr int kChunks = kSplitBRows / V;  // chunks of V k per column in a pass
     for (int p = threadIdx.x; p < kOzTileRows * kChunks; p += blockDim.x) {
       const int r = p % kOzTileRows, cl = p / kOzTileRows;
+      if (r >= row_lim || pass * kChunks + cl >= chunk_lim) continue;
       const int64_t col = col0 + r;
       const int f = col < n ? exponent_from_absbits(colbits[col]) : 0;
       double v[V];
@@ -409,107 +417,130 @@ __global__ void __launch_bounds__(256) oz_split_b_kernel(
 }
 
 // ---------------------------------------------------------------- grouped steps 1-2
-// The same scale and split over every problem of a grouped call, items
-// located through the device plan.
-// A warp takes a contiguous run of rows (one binary search for the first,
-// then the owning problem only moves forward).
-__global__ void oz_grouped_rowmax_kernel(const uint8_t* __restrict__ ws, int* __restrict__ status) {
+// The scale and the split of a grouped call, fused per operand tile-row: one
+// block takes the 128 rows of one A tile-row (or the 128 columns of one B
+// tile-column) of one problem, finds their maxima, then writes their digit
+// tiles for every k-block, re-reading the operand from L2.  Only what the
+// edge-tile copies of the slice GEMM read is written: rows up to the tile's
+// rows rounded up to 8 (A) or columns up to 16 (B, the MMA's N step), and
+// in the last k-block the 16-byte chunks up to k rounded up to 16 (with
+// zeros past k).
+
+// Chunks of 8 k written in k-block tk of a problem with Kt k-blocks.
+__device__ __forceinline__ int grouped_chunk_lim(int64_t k, int64_t Kt, int64_t tk) {
+  if (tk < Kt - 1) return kOzChunksPerRow;
+  const int64_t klast = k - (Kt - 1) * kOzTileK;
+  return static_cast<int>((klast + 15) / 16 * 2);
+}
+
+__global__ void __launch_bounds__(256) oz_grouped_prep_a_kernel(uint8_t* __restrict__ ws, int S,
+                                                                int beta, bool rn,
+                                                                int* __restrict__ status) {
   const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
   if (!hdr->valid) return;
   const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
-  uint64_t* rowbits = reinterpret_cast<uint64_t*>(const_cast<uint8_t*>(ws) + hdr->off_rowbits);
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
-  const int64_t w = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int64_t per = (hdr->rows + warps - 1) / warps;
-  const int64_t r0 = w * per, r1 = (r0 + per) < hdr->rows ? (r0 + per) : hdr->rows;
-  if (r0 >= r1) return;
-  int64_t pi = grouped_find(recs, hdr->count, r0, &GroupedProblem::row_begin);
-  for (int64_t r = r0; r < r1; ++r) {
-    while (pi + 1 < hdr->count && recs[pi + 1].row_begin <= r) ++pi;
-    const GroupedProblem& p = recs[pi];
-    const double* a = p.A + (r - p.row_begin) * p.k;
-    uint64_t mx = 0;
-    for (int64_t l = lane; l < p.k; l += 32) {
-      const uint64_t b = static_cast<uint64_t>(__double_as_longlong(__ldg(a + l))) & kAbsMask;
-      mx = mx > b ? mx : b;
+  uint64_t* rowbits = reinterpret_cast<uint64_t*>(ws + hdr->off_rowbits);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int64_t it = blockIdx.x; it < hdr->trows; it += gridDim.x) {  // block-uniform
+    const GroupedProblem& p = recs[grouped_find(recs, hdr->count, it, &GroupedProblem::trow_begin)];
+    const int64_t tm = it - p.trow_begin;
+    const int64_t r0 = tm * kOzTileRows;
+    const int rows = static_cast<int>((p.m - r0) < kOzTileRows ? (p.m - r0) : kOzTileRows);
+    // row maxima: a warp per row, four loads in flight per lane
+    for (int r = warp; r < rows; r += nwarps) {
+      const double* a0 = p.A + (r0 + r) * p.k;
+      uint64_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+      int64_t l = lane;
+      for (; l + 96 < p.k; l += 128) {
+        const uint64_t b0 = static_cast<uint64_t>(__double_as_longlong(__ldg(a0 + l))) & kAbsMask;
+        const uint64_t b1 = static_cast<uint64_t>(__double_as_longlong(__ldg(a0 + l + 32))) & kAbsMask;
+        const uint64_t b2 = static_cast<uint64_t>(__double_as_longlong(__ldg(a0 + l + 64))) & kAbsMask;
+        const uint64_t b3 = static_cast<uint64_t>(__double_as_longlong(__ldg(a0 + l + 96))) & kAbsMask;
+        m0 = m0 > b0 ? m0 : b0;
+        m1 = m1 > b1 ? m1 : b1;
+        m2 = m2 > b2 ? m2 : b2;
+        m3 = m3 > b3 ? m3 : b3;
+      }
+      for (; l < p.k; l += 32) {
+        const uint64_t b0 = static_cast<uint64_t>(__double_as_longlong(__ldg(a0 + l))) & kAbsMask;
+        m0 = m0 > b0 ? m0 : b0;
+      }
+      m0 = m0 > m1 ? m0 : m1;
+      m2 = m2 > m3 ? m2 : m3;
+      m0 = warp_max_u64(m0 > m2 ? m0 : m2);
+      if (lane == 0) {
+        rowbits[p.row_begin + r0 + r] = m0;
+        if (m0 >= kInfBits) atomicOr(status, kStatusNonFinite);
+      }
     }
-    mx = warp_max_u64(mx);
-    if (lane == 0) {
-      rowbits[r] = mx;
+    __syncthreads();  // the maxima of these rows, written above, are read below
+    const int row_lim = rows >= kOzTileRows ? kOzTileRows : (rows + 7) / 8 * 8;
+    for (int64_t tk = 0; tk < p.Kt; ++tk)
+      split_a_tile<8>(p.A, p.m, p.k, rowbits + p.row_begin, S, beta, tm, tk,
+                      ws + hdr->off_a + static_cast<size_t>(p.atile_begin + tm * p.Kt + tk) *
+                                            kOzTileBytes,
+                      static_cast<size_t>(hdr->atiles) * kOzTileBytes, rn, row_lim,
+                      grouped_chunk_lim(p.k, p.Kt, tk));
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) oz_grouped_prep_b_kernel(uint8_t* __restrict__ ws, int S,
+                                                                int beta, bool rn,
+                                                                int* __restrict__ status) {
+  const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
+  if (!hdr->valid) return;
+  const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
+  uint64_t* colbits = reinterpret_cast<uint64_t*>(ws + hdr->off_colbits);
+  __shared__ double sb[kSplitBRows][kOzTileRows + 1];
+  __shared__ uint64_t red[2][kOzTileRows];
+  for (int64_t it = blockIdx.x; it < hdr->tcols; it += gridDim.x) {  // block-uniform
+    const GroupedProblem& p = recs[grouped_find(recs, hdr->count, it, &GroupedProblem::tcol_begin)];
+    const int64_t tn = it - p.tcol_begin;
+    const int64_t c0 = tn * kOzTileRows;
+    const int cols = static_cast<int>((p.n - c0) < kOzTileRows ? (p.n - c0) : kOzTileRows);
+    // column maxima: thread t takes column t % 128 of every other row
+    // (consecutive threads read consecutive columns of a row)
+    {
+      const int c = threadIdx.x & (kOzTileRows - 1), h = threadIdx.x >> 7;
+      uint64_t mx = 0;
+      if (c < cols) {
+        // eight rows in flight per thread
+        const double* bc = p.B + c0 + c;
+        uint64_t mm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int64_t l = h;
+        for (; l + 14 < p.k; l += 16) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const uint64_t b =
+                static_cast<uint64_t>(__double_as_longlong(__ldg(bc + (l + 2 * u) * p.n))) & kAbsMask;
+            mm[u] = mm[u] > b ? mm[u] : b;
+          }
+        }
+        for (; l < p.k; l += 2) {
+          const uint64_t b = static_cast<uint64_t>(__double_as_longlong(__ldg(bc + l * p.n))) & kAbsMask;
+          mm[0] = mm[0] > b ? mm[0] : b;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) mx = mx > mm[u] ? mx : mm[u];
+      }
+      red[h][c] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x < cols) {
+      const uint64_t a = red[0][threadIdx.x], b = red[1][threadIdx.x];
+      const uint64_t mx = a > b ? a : b;
+      colbits[p.col_begin + c0 + threadIdx.x] = mx;
       if (mx >= kInfBits) atomicOr(status, kStatusNonFinite);
     }
-  }
-}
-
-// A warp takes a contiguous run of 32-column groups (as above); four
-// independent maxima keep four loads of the column walk in flight.
-__global__ void oz_grouped_colmax_kernel(const uint8_t* __restrict__ ws, int* __restrict__ status) {
-  const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
-  if (!hdr->valid) return;
-  const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
-  uint64_t* colbits = reinterpret_cast<uint64_t*>(const_cast<uint8_t*>(ws) + hdr->off_colbits);
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
-  const int64_t w = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int64_t per = (hdr->cgroups + warps - 1) / warps;
-  const int64_t g0 = w * per, g1 = (g0 + per) < hdr->cgroups ? (g0 + per) : hdr->cgroups;
-  if (g0 >= g1) return;
-  int64_t pi = grouped_find(recs, hdr->count, g0, &GroupedProblem::cgrp_begin);
-  for (int64_t gi = g0; gi < g1; ++gi) {
-    while (pi + 1 < hdr->count && recs[pi + 1].cgrp_begin <= gi) ++pi;
-    const GroupedProblem& p = recs[pi];
-    const int64_t col = (gi - p.cgrp_begin) * 32 + lane;
-    if (col >= p.n) continue;
-    const double* bc = p.B + col;
-    uint64_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
-    int64_t l = 0;
-    for (; l + 4 <= p.k; l += 4) {
-      const uint64_t b0 = static_cast<uint64_t>(__double_as_longlong(__ldg(bc + l * p.n))) & kAbsMask;
-      const uint64_t b1 = static_cast<uint64_t>(__double_as_longlong(__ldg(bc + (l + 1) * p.n))) & kAbsMask;
-      const uint64_t b2 = static_cast<uint64_t>(__double_as_longlong(__ldg(bc + (l + 2) * p.n))) & kAbsMask;
-      const uint64_t b3 = static_cast<uint64_t>(__double_as_longlong(__ldg(bc + (l + 3) * p.n))) & kAbsMask;
-      m0 = m0 > b0 ? m0 : b0;
-      m1 = m1 > b1 ? m1 : b1;
-      m2 = m2 > b2 ? m2 : b2;
-      m3 = m3 > b3 ? m3 : b3;
-    }
-    for (; l < p.k; ++l) {
-      const uint64_t b = static_cast<uint64_t>(__double_as_longlong(__ldg(bc + l * p.n))) & kAbsMask;
-      m0 = m0 > b ? m0 : b;
-    }
-    m0 = m0 > m1 ? m0 : m1;
-    m2 = m2 > m3 ? m2 : m3;
-    const uint64_t mx = m0 > m2 ? m0 : m2;
-    colbits[p.col_begin + col] = mx;
-    if (mx >= kInfBits) atomicOr(status, kStatusNonFinite);
-  }
-}
-
-__global__ void __launch_bounds__(256) oz_grouped_split_kernel(uint8_t* __restrict__ ws, int S,
-                                                               int beta, bool rn) {
-  const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
-  if (!hdr->valid) return;
-  const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
-  const uint64_t* rowbits = reinterpret_cast<const uint64_t*>(ws + hdr->off_rowbits);
-  const uint64_t* colbits = reinterpret_cast<const uint64_t*>(ws + hdr->off_colbits);
-  const int64_t na = hdr->atiles, nb = hdr->btiles;
-  __shared__ double sb[kSplitBRows][kOzTileRows + 1];
-  for (int64_t t = blockIdx.x; t < na + nb; t += gridDim.x) {  // block-uniform branch
-    if (t < na) {
-      const GroupedProblem& p = recs[grouped_find(recs, hdr->count, t, &GroupedProblem::atile_begin)];
-      const int64_t local = t - p.atile_begin;
-      split_a_tile<8>(p.A, p.m, p.k, rowbits + p.row_begin, S, beta, local / p.Kt, local % p.Kt,
-                   ws + hdr->off_a + static_cast<size_t>(t) * kOzTileBytes,
-                   static_cast<size_t>(na) * kOzTileBytes, rn);
-    } else {
-      const int64_t tb = t - na;
-      const GroupedProblem& p = recs[grouped_find(recs, hdr->count, tb, &GroupedProblem::btile_begin)];
-      const int64_t local = tb - p.btile_begin;
-      split_b_tile<8>(p.B, p.k, p.n, colbits + p.col_begin, S, beta, local / p.Kt, local % p.Kt,
-                   ws + hdr->off_b + static_cast<size_t>(tb) * kOzTileBytes,
-                   static_cast<size_t>(nb) * kOzTileBytes, sb, rn);
-    }
+    __syncthreads();  // the maxima written above are read by the split below
+    const int row_lim = cols >= kOzTileRows ? kOzTileRows : (cols + 15) / 16 * 16;
+    for (int64_t tk = 0; tk < p.Kt; ++tk)
+      split_b_tile<8>(p.B, p.k, p.n, colbits + p.col_begin, S, beta, tn, tk,
+                      ws + hdr->off_b + static_cast<size_t>(p.btile_begin + tn * p.Kt + tk) *
+                                            kOzTileBytes,
+                      static_cast<size_t>(hdr->btiles) * kOzTileBytes, sb, rn, false, row_lim,
+                      grouped_chunk_lim(p.k, p.Kt, tk));
   }
 }
 
@@ -620,7 +651,26 @@ struct OzTile {
   uint64_t* sums;            // 128 x 128 running sums, column-major (paired kernel)
   uint64_t* partial;         // split-k: this range's D_g, [S - 1 diagonals][128 x 128]
   int eoff;                  // added to e_i + f_j in the final scaling (2: balanced digits)
+  // Edge tiles (one-diagonal kernel): the MMAs compute n_eff columns (the
+  // tile's columns rounded up to 16, the MMA's N step), only the first
+  // a_rows rows of each A atom and n_eff rows of each B atom are copied (the
+  // rest of the slot holds older digits, which reach only rows and columns of
+  // D that are never stored), and the unit's last k-block issues last_mmas
+  // MMAs of K = 16 (k rounded up to 16; the digit planes hold zeros there).
+  int n_eff;
+  int a_rows;
+  int last_mmas;
 };
+
+// Edge geometry of a tile: rows of A left from row0, columns of B from
+// col0, and whether the unit's k range ends with the product's last k-block.
+__device__ __forceinline__ void oz_edges(OzTile& j, int64_t k, bool ends_at_k) {
+  const int64_t rn = j.n - j.col0, rm = j.m - j.row0;
+  j.n_eff = rn >= kOzTileRows ? kOzTileRows : static_cast<int>((rn + 15) / 16 * 16);
+  j.a_rows = rm >= kOzTileRows ? kOzTileRows : (rm > 0 ? static_cast<int>((rm + 7) / 8 * 8) : 0);
+  const int64_t klast = k - (k - 1) / kOzTileK * kOzTileK;  // 1 .. 128 (k > 0)
+  j.last_mmas = (ends_at_k && k > 0) ? static_cast<int>((klast + 15) / 16) : kOzTileK / 16;
+}
 
 // Tiles of one product.
 struct OzSingle {
@@ -637,6 +687,8 @@ struct OzSingle {
   long long* spill = nullptr;  // paired kernel: per-CTA int64 partials of the two diagonals
   int spill_every = 0;         // window drains after which a diagonal's int32 sum spills
   int eoff = 0;                // added to e_i + f_j in the final scaling (2: balanced digits)
+  int64_t k = 0;               // the product's k (edge tiles)
+  __device__ __forceinline__ long long* spill_area() const { return spill; }
   int64_t raster = kDefaultRaster;  // tile-rows (pair-rows) per group of the tile walk
   bool kb_alt = false;         // alternate the k-block direction between diagonal (pair)s
   // Address k-block of the it-th k-block of diagonal (pair) q: every other
@@ -679,6 +731,7 @@ struct OzSingle {
     j.row0 = tm * kOzTileRows;
     j.col0 = tn * kOzTileRows;
     j.eoff = eoff;
+    oz_edges(j, k, kb1 == Kt);
     const size_t tile_words = kOzTileRows * kOzTileRows;
     if (splits > 1) {
       j.sums = nullptr;
@@ -699,12 +752,22 @@ struct OzGrouped {
   const GroupedProblem* recs;
   const uint8_t* ws;
   int eoff;  // 2 for balanced 8-bit digits
-  __device__ __forceinline__ int64_t count() const { return hdr->valid ? hdr->tiles : 0; }
+  bool long_k;  // the tiles of the long-k problems (else those of the short-k ones)
+  int spill_every = 0;         // window drains after which a diagonal's int32 sum spills
+  // paired kernel: per-CTA int64 partials of the two diagonals (long k)
+  __device__ __forceinline__ long long* spill_area() const {
+    return reinterpret_cast<long long*>(const_cast<uint8_t*>(ws) + hdr->off_spill);
+  }
+  __device__ __forceinline__ int64_t count() const {
+    return hdr->valid ? (long_k ? hdr->ltiles : hdr->stiles) : 0;
+  }
   __device__ __forceinline__ int64_t kblock(int, int64_t it, int64_t) const { return it; }
   __device__ __forceinline__ OzTile tile(int64_t t) const {
-    const int64_t p = grouped_find(recs, hdr->count, t, &GroupedProblem::tile_begin);
+    int64_t GroupedProblem::*begin = long_k ? &GroupedProblem::ltile_begin
+                                            : &GroupedProblem::stile_begin;
+    const int64_t p = grouped_find(recs, hdr->count, t, begin);
     const GroupedProblem& r = recs[p];
-    const int64_t local = t - r.tile_begin;
+    const int64_t local = t - r.*begin;
     const int64_t tm = local / r.Nt, tn = local - (local / r.Nt) * r.Nt;
     OzTile j;
     j.a_slice = static_cast<size_t>(hdr->atiles) * kOzTileBytes;
@@ -719,9 +782,11 @@ struct OzGrouped {
     j.n = r.n;
     j.row0 = tm * kOzTileRows;
     j.col0 = tn * kOzTileRows;
-    j.sums = nullptr;
+    j.sums = reinterpret_cast<uint64_t*>(const_cast<uint8_t*>(ws) + hdr->off_sums) +
+             static_cast<size_t>(t) * (kOzTileRows * kOzTileRows);
     j.partial = nullptr;
     j.eoff = eoff;
+    oz_edges(j, r.k, true);
     return j;
   }
 };
@@ -850,25 +915,42 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp < 4) regs_dec_80();  // warps 2, 3 idle
   if (warp == 0) {
     // ------------------------------------------------ producer (bulk copies)
+    // Full tiles move as one 32 KiB copy per operand; edge tiles copy the
+    // rows the MMAs read, atom by atom, and in the last k-block only the
+    // atoms its MMAs reach.
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const OzTile j = tiles.tile(t);
+        const uint32_t arow_bytes = static_cast<uint32_t>(j.a_rows) * 128u;
+        const uint32_t brow_bytes = static_cast<uint32_t>(j.n_eff) * 128u;
         for (int g = S + 1; g >= 2 && ok; --g) {
           for (int64_t kb = 0; kb < j.Kt && ok; ++kb) {
+            const int64_t kbx = tiles.kblock(S + 1 - g, kb, j.Kt);
+            const int atoms = (kbx == j.Kt - 1 && j.last_mmas <= kOzAtomK / kMmaK) ? 1 : 2;
+            const bool whole = atoms == 2 && j.a_rows == kOzTileRows && j.n_eff == kOzTileRows;
             for (int s = 1; s <= g - 1; ++s) {
               if (!mbar_wait_bounded(&sm.empty[stage], phase ^ 1u, abort_flag, status)) {
                 ok = false;
                 break;
               }
-              mbar_arrive_expect_tx(&sm.full[stage], 2 * kOzTileBytes);
-              const int64_t kbx = tiles.kblock(S + 1 - g, kb, j.Kt);
-              bulk_g2s(sm.a[stage], j.a + (s - 1) * j.a_slice + kbx * kOzTileBytes, kOzTileBytes,
-                       &sm.full[stage]);
-              bulk_g2s(sm.b[stage], j.b + (g - s - 1) * j.b_slice + kbx * kOzTileBytes,
-                       kOzTileBytes, &sm.full[stage]);
+              const uint8_t* asrc = j.a + (s - 1) * j.a_slice + kbx * kOzTileBytes;
+              const uint8_t* bsrc = j.b + (g - s - 1) * j.b_slice + kbx * kOzTileBytes;
+              if (whole) {
+                mbar_arrive_expect_tx(&sm.full[stage], 2 * kOzTileBytes);
+                bulk_g2s(sm.a[stage], asrc, kOzTileBytes, &sm.full[stage]);
+                bulk_g2s(sm.b[stage], bsrc, kOzTileBytes, &sm.full[stage]);
+              } else {
+                mbar_arrive_expect_tx(&sm.full[stage], atoms * (arow_bytes + brow_bytes));
+                for (int at = 0; at < atoms; ++at) {
+                  bulk_g2s(sm.a[stage] + at * kOzAtomBytes, asrc + at * kOzAtomBytes, arow_bytes,
+                           &sm.full[stage]);
+                  bulk_g2s(sm.b[stage] + at * kOzAtomBytes, bsrc + at * kOzAtomBytes, brow_bytes,
+                           &sm.full[stage]);
+                }
+              }
               if (++stage == kStages) {
                 stage = 0;
                 phase ^= 1u;
@@ -889,12 +971,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
-    // Kept lean: one wait per stage, four MMAs with precomputed descriptors
-    // (stage s of the ring is s * 16 KiB further, i.e. +1024 in the
-    // descriptor's address field; K steps of 16 bf16 = 32 bytes are +2), and
-    // windows counted in whole stages.
+    // Kept lean: one wait per stage, the tile's MMAs with precomputed
+    // descriptors (stage s of the ring is s * 16 KiB further, i.e. +1024 in
+    // the descriptor's address field; K steps of 16 bf16 = 32 bytes are +2),
+    // N = the tile's n_eff, and windows counted in whole stages.
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16_f32(128, kBN);
       const uint64_t adesc0 = sw128_kmajor_desc(smem_u32(sm.a[0]));
       const uint64_t bdesc0 = sw128_kmajor_desc(smem_u32(sm.b[0]));
       int stage = 0;
@@ -905,9 +986,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       int wcnt = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int64_t Kt = tiles.tile(t).Kt;
+        const OzTile j = tiles.tile(t);
+        const int64_t Kt = j.Kt;
+        const uint32_t idesc = idesc_bf16_f32(128, j.n_eff);
         for (int g = S + 1; g >= 2 && ok; --g) {
           const int64_t nst = Kt * (g - 1);
+          int64_t kb = 0;
+          int s = 1;
           for (int64_t st = 0; st < nst; ++st) {
             if (!mbar_wait_bounded(&sm.full[stage], phase, abort_flag, status)) {
               ok = false;
@@ -926,6 +1011,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               acquired = true;
               wcnt = 0;
             }
+            const int nmma =
+                tiles.kblock(S + 1 - g, kb, Kt) == Kt - 1 ? j.last_mmas : kMmaPerStage;
             const uint64_t da = adesc0 + static_cast<uint64_t>(stage) * (kOzTileBytes >> 4);
             const uint64_t db = bdesc0 + static_cast<uint64_t>(stage) * (kOzTileBytes >> 4);
             const uint32_t d = tmem + static_cast<uint32_t>(buf * kBN);
@@ -933,7 +1020,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int kk = 0; kk < kMmaPerStage; ++kk) {
               // k step kk: atom kk / 4 (16 KiB = +1024), 32 bytes per step inside it (+2)
               const uint64_t off = static_cast<uint64_t>((kk >> 2) * (kOzAtomBytes >> 4) + (kk & 3) * 2);
-              mma_bf16_ss(d, da + off, db + off, idesc, (kk > 0 || wcnt > 0) ? 1u : 0u);
+              if (kk < nmma)
+                mma_bf16_ss(d, da + off, db + off, idesc, (kk > 0 || wcnt > 0) ? 1u : 0u);
             }
             mma_commit(&sm.empty[stage]);
             ++wcnt;
@@ -946,12 +1034,19 @@ __global__ void __launch_bounds__(kThreads, 1)
               stage = 0;
               phase ^= 1u;
             }
+            if (++s == g) {
+              s = 1;
+              ++kb;
+            }
           }
         }
       }
     }
   } else if (warp >= 4) {
     // ------------------------------------------------ epilogue (8 warps)
+    // A warp whose 32 rows all lie past the tile's last row, and a group of
+    // columns past its last column, skip their tensor-memory reads and their
+    // share of the fold (the running sums there are never stored).
     regs_inc_208();
     const int ew = warp - 4;
     const int quarter = warp & 3;          // TMEM lanes this warp may access
@@ -963,9 +1058,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t fulls0 = 0u, fulls1 = 0u;  // windows drained from accumulator 0 / 1
     bool ok = true;
     Acc D[64];
+    using FInt = std::integral_constant<int, kFoldInt>;
+    using FConv = std::integral_constant<int, kFoldConv>;
+    using FFp = std::integral_constant<int, kFoldFp>;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const OzTile j = tiles.tile(t);
       const int gx = oz_exact_from(S, beta, j.Kt);
+      const bool rows_live = j.row0 + quarter * 32 < j.m;
+      const int64_t row = j.row0 + row_in_tile;
+      const bool row_ok = row < j.m;
+      const int64_t ncols = j.n - j.col0;    // columns of C in this tile (may exceed 128)
       for (int g = S + 1; g >= 2 && ok; --g) {
 #pragma unroll
         for (int i = 0; i < 64; ++i) D[i] = 0;
@@ -982,6 +1084,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t t_win = t_lane + static_cast<uint32_t>(buf * kBN + half * 64);
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
+            if (!rows_live || half * 64 + h * 32 >= j.n_eff) continue;  // warp-uniform
             uint32_t r[32];
             tmem_ld32(t_win + h * 32, r);
             tmem_wait_ld();
@@ -1002,66 +1105,84 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!kFloat && j.partial != nullptr) {
           // split-k: this range's exact D_g, column-major in the tile (a
           // warp's 32 lanes store 256 contiguous bytes per column)
+          if (!rows_live) continue;
           uint64_t* p = j.partial + static_cast<size_t>(g - 2) * (kOzTileRows * kOzTileRows) +
                         static_cast<size_t>(half * 64) * kOzTileRows + row_in_tile;
 #pragma unroll
           for (int i = 0; i < 64; ++i)
-            __stcg(reinterpret_cast<unsigned long long*>(p + i * kOzTileRows),
-                   static_cast<unsigned long long>(static_cast<long long>(D[i])));
+            if (half * 64 + i < ncols)
+              __stcg(reinterpret_cast<unsigned long long*>(p + i * kOzTileRows),
+                     static_cast<unsigned long long>(static_cast<long long>(D[i])));
           continue;
         }
+        if (!rows_live) continue;
         const bool first = (g == S + 1);
         const bool last = (g == 2);
-        const int64_t row = j.row0 + row_in_tile;
         int er = 0;
-        if (!kFloat && last && row < j.m) er = exponent_from_absbits(j.rowbits[row]);
+        if (!kFloat && last && row_ok) er = exponent_from_absbits(j.rowbits[row]);
         // 8 columns per step of a rolled loop; D is rotated down by 8 after
-        // each step so the body only names D[0..7] (compact code)
+        // each step so the body only names D[0..7] (compact code).  The kind
+        // of the fold step (int64 partial, the conversion to FP64, an FP64
+        // addition) is fixed per diagonal, so the 8 elements of a step are
+        // straight-line code.
+        auto fold_pass = [&](auto kc) {
+          [[maybe_unused]] constexpr int K = decltype(kc)::value;
 #pragma unroll 1
-        for (int ch = 0; ch < 8; ++ch) {
-          uint32_t r[16];
-          if (!first) {
-            tmem_ld16(t_acc + ch * 16, r);
-            tmem_wait_ld();
-          }
-          uint64_t st[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            if constexpr (kFloat) {
-              st[i] = static_cast<uint64_t>(__double_as_longlong(static_cast<double>(D[i])));
-            } else {
-              const uint64_t prev =
-                  first ? 0ull : ((static_cast<uint64_t>(r[2 * i + 1]) << 32) | r[2 * i]);
-              st[i] = fold_step(prev, static_cast<long long>(D[i]), g, gx, S, beta);
-            }
-          }
-          if (last) {
-            if (row < j.m) {
-              const int64_t col0 = j.col0 + half * 64 + ch * 8;
-              double* crow = j.C + row * j.n;
+          for (int ch = 0; ch < 8; ++ch) {
+            if (half * 64 + ch * 8 < ncols) {  // warp-uniform
+              uint32_t r[16];
+              if (!first) {
+                tmem_ld16(t_acc + ch * 16, r);
+                tmem_wait_ld();
+              }
+              uint64_t st[8];
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
-                const int64_t col = col0 + i;
-                if (col < j.n) {
-                  if constexpr (kFloat)
-                    crow[col] = __longlong_as_double(static_cast<long long>(st[i]));
-                  else
-                    crow[col] =
-                        final_scale(st[i], er + exponent_from_absbits(j.colbits[col]) + j.eoff);
+                if constexpr (kFloat) {
+                  st[i] = static_cast<uint64_t>(__double_as_longlong(static_cast<double>(D[i])));
+                } else {
+                  const uint64_t prev =
+                      first ? 0ull : ((static_cast<uint64_t>(r[2 * i + 1]) << 32) | r[2 * i]);
+                  st[i] = fold_kind<K>(prev, static_cast<long long>(D[i]), g, S, beta);
                 }
               }
-            }
-          } else {
+              if (last) {
+                if (row_ok) {
+                  const int64_t col0 = j.col0 + half * 64 + ch * 8;
+                  double* crow = j.C + row * j.n;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              r[2 * i] = static_cast<uint32_t>(st[i]);
-              r[2 * i + 1] = static_cast<uint32_t>(st[i] >> 32);
+                  for (int i = 0; i < 8; ++i) {
+                    const int64_t col = col0 + i;
+                    if (col < j.n) {
+                      if constexpr (kFloat)
+                        crow[col] = __longlong_as_double(static_cast<long long>(st[i]));
+                      else
+                        crow[col] = final_scale(
+                            st[i], er + exponent_from_absbits(j.colbits[col]) + j.eoff);
+                    }
+                  }
+                }
+              } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                  r[2 * i] = static_cast<uint32_t>(st[i]);
+                  r[2 * i + 1] = static_cast<uint32_t>(st[i] >> 32);
+                }
+                tmem_st16(t_acc + ch * 16, r);
+                tmem_wait_st();
+              }
             }
-            tmem_st16(t_acc + ch * 16, r);
-            tmem_wait_st();
+#pragma unroll
+            for (int i = 0; i < 56; ++i) D[i] = D[i + 8];
           }
-#pragma unroll
-          for (int i = 0; i < 56; ++i) D[i] = D[i + 8];
+        };
+        if constexpr (kFloat) {
+          fold_pass(FInt{});
+        } else {
+          const int kind = fold_kind_of(g, gx);
+          if (kind == kFoldInt) fold_pass(FInt{});
+          else if (kind == kFoldConv) fold_pass(FConv{});
+          else fold_pass(FFp{});
         }
       }
     }
@@ -1095,6 +1216,7 @@ constexpr int kP2Threads = 384;
 // twice as deep in the same shared memory.
 struct FmtBf16 {
   static constexpr bool kPair = false;
+  static constexpr bool kEdges = true;   // edge tiles: n_eff, partial copies, short last k-block
   static constexpr int kTileBytes = kOzTileBytes, kBTileBytes = kOzTileBytes;
   static constexpr int kMmas = 8;
   static constexpr int kRingA = 3, kRingB = 4;
@@ -1109,6 +1231,7 @@ struct FmtBf16 {
 };
 struct FmtE4m3 {
   static constexpr bool kPair = false;
+  static constexpr bool kEdges = false;
   static constexpr int kTileBytes = kOzTileBytesE4m3, kBTileBytes = kOzTileBytesE4m3;
   static constexpr int kMmas = 4;
   static constexpr int kRingA = 6, kRingB = 8;
@@ -1125,6 +1248,7 @@ struct FmtE4m3 {
 // instead of 64 for the same MMA work.  Rings of 4 A tiles and 6 B halves.
 struct FmtBf16Pair {
   static constexpr bool kPair = true;
+  static constexpr bool kEdges = false;
   static constexpr int kTileBytes = kOzTileBytes, kBTileBytes = kOzTileBytes / 2;
   static constexpr int kMmas = 8;
   static constexpr int kRingA = 4, kRingB = 6;
@@ -1191,6 +1315,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
   constexpr int kRingA = Fmt::kRingA, kRingB = Fmt::kRingB, kTile = Fmt::kTileBytes;
   constexpr int kBTile = Fmt::kBTileBytes;
   constexpr bool kPair = Fmt::kPair;
+  constexpr bool kEdges = Fmt::kEdges;
   extern __shared__ uint8_t smem_raw[];
   Gemm2Smem<Fmt>& sm = *reinterpret_cast<Gemm2Smem<Fmt>*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -1232,7 +1357,11 @@ __global__ void __launch_bounds__(kP2Threads, 1)
   const uint32_t tmem = sm.tmem_base;
   volatile int* abort_flag = &sm.abort_flag;
   // work units: C tiles, or (pairs) 256-row C tiles shared by the cluster
-  const int64_t nunits = kPair ? tiles.pair_count() : tiles.count();
+  int64_t nunits;
+  if constexpr (kPair)
+    nunits = tiles.pair_count();
+  else
+    nunits = tiles.count();
   const int64_t unit0 = kPair ? (blockIdx.x >> 1) : blockIdx.x;
   const int64_t unit_step = kPair ? (gridDim.x >> 1) : gridDim.x;
   auto unit_tile = [&](int64_t t) {
@@ -1265,14 +1394,45 @@ __global__ void __launch_bounds__(kP2Threads, 1)
         r.advance();
         return true;
       };
+      // edge tiles (kEdges): the rows the MMAs read, atom by atom; in the
+      // last k-block only the atoms its MMAs reach
+      auto load_edge = [&](auto& r, auto buf, uint64_t* full, uint64_t* empty,
+                           const uint8_t* src, uint32_t row_bytes, int atoms) {
+        if (!mbar_wait_bounded(&empty[r.slot], r.phase ^ 1u, abort_flag, status))
+          return false;
+        mbar_arrive_expect_tx(&full[r.slot], atoms * row_bytes);
+        for (int at = 0; at < atoms; ++at)
+          bulk_g2s(buf[r.slot] + at * kOzAtomBytes, src + at * kOzAtomBytes, row_bytes,
+                   &full[r.slot]);
+        r.advance();
+        return true;
+      };
       for (int64_t t = unit0; t < nunits && ok; t += unit_step) {
         const OzTile j = unit_tile(t);
         const bool live = !kPair || j.row0 < j.m;
         const size_t bhalf = kPair ? static_cast<size_t>(rank) * kBTile : 0;
+        const bool edge = kEdges && (j.a_rows < kOzTileRows || j.n_eff < kOzTileRows ||
+                                     j.last_mmas < Fmt::kMmas);
         for (int q = 0; q < ngroups && ok; ++q) {
           const int g = S + 1 - 2 * q;
           for (int64_t kb = 0; kb < j.Kt && ok; ++kb) {
-            const size_t koff = static_cast<size_t>(tiles.kblock(q, kb, j.Kt)) * kTile;
+            const int64_t kbx = tiles.kblock(q, kb, j.Kt);
+            const size_t koff = static_cast<size_t>(kbx) * kTile;
+            if (edge) {
+              const int atoms = (kbx == j.Kt - 1 && j.last_mmas <= kOzAtomK / kMmaK) ? 1 : 2;
+              const uint32_t arb = static_cast<uint32_t>(j.a_rows) * 128u;
+              const uint32_t brb = static_cast<uint32_t>(j.n_eff) * 128u;
+              ok = load_edge(rb, sm.b, sm.b_full, sm.b_empty, j.b + (g - 2) * j.b_slice + koff,
+                             brb, atoms);
+              for (int s = 1; s <= g - 1 && ok; ++s) {
+                ok = load_edge(ra, sm.a, sm.a_full, sm.a_empty, j.a + (s - 1) * j.a_slice + koff,
+                               arb, atoms);
+                if (ok && s <= g - 2)
+                  ok = load_edge(rb, sm.b, sm.b_full, sm.b_empty,
+                                 j.b + (g - 2 - s) * j.b_slice + koff, brb, atoms);
+              }
+              continue;
+            }
             ok = load(rb, sm.b, sm.b_full, sm.b_empty, j.b + (g - 2) * j.b_slice + koff + bhalf,
                       kBTile);
             for (int s = 1; s <= g - 1 && ok; ++s) {
@@ -1333,7 +1493,8 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       // one per issuer (a commit after its MMAs, or a plain arrival for a
       // tile it does not read).  On a pair both go to both CTAs.
       const int x = warp - 1;
-      const uint32_t idesc = Fmt::idesc();
+      uint32_t idesc = Fmt::idesc();
+      int nmma = Fmt::kMmas;  // MMAs of the current k-block
       const uint64_t adesc0 = sw128_kmajor_desc(smem_u32(sm.a[0]));
       const uint64_t bdesc0 = sw128_kmajor_desc(smem_u32(sm.b[0]));
       Ring<kRingA> ra;
@@ -1372,7 +1533,8 @@ __global__ void __launch_bounds__(kP2Threads, 1)
         const uint32_t acc0 = cnt > 0 ? 1u : 0u;
 #pragma unroll
         for (int kk = 0; kk < Fmt::kMmas; ++kk)
-          Fmt::mma(d, da + Fmt::koff(kk), db + Fmt::kboff(kk), idesc, kk > 0 ? 1u : acc0);
+          if (!kEdges || kk < nmma)
+            Fmt::mma(d, da + Fmt::koff(kk), db + Fmt::kboff(kk), idesc, kk > 0 ? 1u : acc0);
       };
       auto finish = [&](bool last) {
         if (++cnt == window || last) {
@@ -1382,11 +1544,15 @@ __global__ void __launch_bounds__(kP2Threads, 1)
         }
       };
       for (int64_t t = unit0; t < nunits && ok; t += unit_step) {
-        const int64_t Kt = unit_tile(t).Kt;
+        const OzTile jt = unit_tile(t);
+        const int64_t Kt = jt.Kt;
+        if constexpr (kEdges) idesc = idesc_bf16_f32(128, jt.n_eff);
         for (int q = 0; q < ngroups && ok; ++q) {
           const int g = S + 1 - 2 * q;
           const bool pair = g - 1 >= 2;
           for (int64_t kb = 0; kb < Kt && ok; ++kb) {
+            if constexpr (kEdges)
+              nmma = tiles.kblock(q, kb, Kt) == Kt - 1 ? jt.last_mmas : Fmt::kMmas;
             if (!mbar_wait_bounded(&sm.b_full[rb.slot], rb.phase, abort_flag, status)) {
               ok = false;
               break;
@@ -1460,7 +1626,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
     int nd0 = 0, nd1 = 0;
     bool sp0 = false, sp1 = false;
     long long* const spill_base =
-        tiles.spill + static_cast<size_t>(blockIdx.x) * 2 * kOzTileRows * kOzTileRows;
+        tiles.spill_area() + static_cast<size_t>(blockIdx.x) * 2 * kOzTileRows * kOzTileRows;
     auto spill = [&](int x, int (&Dx)[64]) {
       bool& sp = x ? sp1 : sp0;
       long long* p = spill_base + (static_cast<size_t>(x) * kOzTileRows + half * 64) * kOzTileRows +
@@ -1479,6 +1645,10 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       }
       sp = true;
     };
+    // edge tiles: whether this warp's 32 rows hold any row of C, and the
+    // MMA columns (warp-uniform; the tile's values)
+    bool warp_rows_live = true;
+    int tile_neff = kOzTileRows;
     auto drain = [&](int x, int (&Dx)[64]) {
       int& b = x ? buf1 : buf0;
       uint32_t& f = x ? (b ? fulls11 : fulls10) : (b ? fulls01 : fulls00);
@@ -1489,6 +1659,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       const uint32_t t_win = t_lane + static_cast<uint32_t>(a * kBN + half * 64);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
+        if (kEdges && (!warp_rows_live || half * 64 + h * 32 >= tile_neff)) continue;
         uint32_t r[32];
         tmem_ld32(t_win + h * 32, r);
         tmem_wait_ld();
@@ -1518,6 +1689,11 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       // a CTA of a pair past the last tile-row drains its windows (its sums
       // are not used) and touches no memory of the product
       const bool live = !kPair || j.row0 < j.m;
+      if constexpr (kEdges) {
+        warp_rows_live = j.row0 + quarter * 32 < j.m;
+        tile_neff = j.n_eff;
+      }
+      const int64_t ncols = j.n - j.col0;  // columns of C in this tile (may exceed 128)
       // diagonals g >= gx fold exactly in int64 (see oz_gemm_kernel)
       const int gx = oz_exact_from(S, beta, j.Kt);
       const int64_t row = j.row0 + row_in_tile;
@@ -1534,13 +1710,14 @@ __global__ void __launch_bounds__(kP2Threads, 1)
         nd0 = nd1 = 0;
         sp0 = sp1 = false;
         for (int64_t kb = 0; kb < j.Kt && ok; ++kb) {
-          if (kb == j.Kt - 1 && q > 0 && live) {
+          if (kb == j.Kt - 1 && q > 0 && live && (!kEdges || warp_rows_live)) {
             // the fold at the end of this k-block reads the tile's running
             // sums: bring them into L2 while the last windows finish
             const uint64_t* ps =
                 j.sums + static_cast<size_t>(half * 64) * kOzTileRows + row_in_tile;
 #pragma unroll 1
-            for (int i = 0; i < 64; ++i) prefetch_l2(ps + i * kOzTileRows);
+            for (int i = 0; i < 64; ++i)
+              if (!kEdges || half * 64 + i < ncols) prefetch_l2(ps + i * kOzTileRows);
           }
           for (int s = 1; s <= g - 1; ++s) {
             if (++cnt0 == window || (kb == j.Kt - 1 && s == g - 1)) {
@@ -1588,6 +1765,15 @@ __global__ void __launch_bounds__(kP2Threads, 1)
           uint64_t cur[8];
 #pragma unroll 1
           for (int ch = 0; ch < 8; ++ch) {
+            if (kEdges && (!warp_rows_live || half * 64 + ch * 8 >= ncols)) {
+              // no row or no column of C here: nothing to fold
+#pragma unroll
+              for (int i = 0; i < 56; ++i) {
+                D0[i] = D0[i + 8];
+                D1[i] = D1[i + 8];
+              }
+              continue;
+            }
             uint64_t* tch = tsum + static_cast<size_t>(ch * 8) * kOzTileRows;
 #pragma unroll
             for (int i = 0; i < 8; ++i) cur[i] = first ? 0ull : __ldca(tch + i * kOzTileRows);
@@ -1819,6 +2005,7 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
                  d.Mt,    d.Nt,    d.Kt,    sums,    splits, d.S,
                  static_cast<int64_t>(ozaki_tile_bytes(d))};
   tiles.eoff = d.rn ? 2 : 0;
+  tiles.k = d.k;
   tiles.raster = d.raster > 0 ? d.raster : kDefaultRaster;
   tiles.kb_alt = d.kb_alt != 0;
   const int64_t count = d.Mt * d.Nt * splits;
@@ -1874,17 +2061,34 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
 cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t /*max_kt*/, int* status,
                                  cudaStream_t s, bool rn) {
   const int sms = sm_count();
-  oz_grouped_rowmax_kernel<<<sms * 4, 256, 0, s>>>(ws, status);
-  oz_grouped_colmax_kernel<<<sms * 4, 256, 0, s>>>(ws, status);
-  oz_grouped_split_kernel<<<sms * 8, 256, 0, s>>>(ws, S, beta, rn);
+  oz_grouped_prep_a_kernel<<<sms * 4, 256, 0, s>>>(ws, S, beta, rn, status);
+  oz_grouped_prep_b_kernel<<<sms * 4, 256, 0, s>>>(ws, S, beta, rn, status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
   const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
-  OzGrouped tiles{hdr, recs, ws, rn ? 2 : 0};
-  // the host does not see the table: 64-bit running sums are safe for any k
-  return launch_oz_gemm_t<long long, false>(tiles, sms, S, beta, ozaki_window_stages(beta, rn),
-                                            status, s);
+  // long-k problems: the diagonals in pairs on single CTAs, edge tiles cut
+  // to their rows and columns; the host does not see the table, so the
+  // int32 sums spill to int64 when a problem's k is long enough to need it
+  OzGrouped lt{hdr, recs, ws, rn ? 2 : 0, true};
+  const int window = ozaki_window_stages(beta, rn);
+  const double dmax = rn ? 128.0 : static_cast<double>((1 << beta) - 1);
+  lt.spill_every = static_cast<int>(2147483647.0 / (static_cast<double>(window) * kOzTileK *
+                                                     dmax * dmax));
+  if (lt.spill_every < 1) return cudaErrorNotSupported;
+  auto kern = oz_gemm2_kernel<OzGrouped, FmtBf16, true>;
+  const size_t kSmem = gemm2_smem_bytes<FmtBf16>();
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kSmem));
+  if (e != cudaSuccess) return e;
+  const int grid = sms < kOzSpillCtas ? sms : static_cast<int>(kOzSpillCtas);
+  kern<<<grid, kP2Threads, kSmem, s>>>(lt, S, beta, window, status);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // short-k problems: one diagonal at a time, FP64 running sums in tensor
+  // memory (64-bit window sums: any k)
+  OzGrouped st{hdr, recs, ws, rn ? 2 : 0, false};
+  return launch_oz_gemm_t<long long, false>(st, sms, S, beta, window, status, s);
 }
 
 cudaError_t launch_bf16_gemm(const double* A, const double* B, double* C, const OzakiDims& d,
@@ -1898,6 +2102,7 @@ cudaError_t launch_bf16_gemm(const double* A, const double* B, double* C, const 
   if (e != cudaSuccess) return e;
   OzSingle tiles{aplane, bplane, nullptr, nullptr, C,       d.m, d.n, d.Mt, d.Nt,
                  d.Kt,   nullptr, 1,     1,       kOzTileBytes};
+  tiles.k = d.k;
   const int64_t count = d.Mt * d.Nt;
   const int64_t grid = count < sm_count() ? count : sm_count();
   // one window covers all of k (FP32 accumulation is the mode's semantics)

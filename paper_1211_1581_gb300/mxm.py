@@ -45,6 +45,13 @@ class Plan(ctypes.Structure):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
+class GroupPlan(ctypes.Structure):
+    """mxm_group_plan: problems of a grouped emulated call with at most
+    ``short_kt`` k-blocks of 128 run on the one-diagonal slice GEMM, the
+    others on the diagonal-pair GEMM (-1: the library's default)."""
+    _fields_ = [("short_kt", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
 # Every symbol include/mxm.h declares, with (restype, argtypes).
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
@@ -63,6 +70,9 @@ SIGNATURES = {
     "mxm_set_workspace": (_I, [_P, _SZ, _P]),
     "mxm_grouped_workspace_size": (_I, [_I64, _P, _I, _I, ctypes.POINTER(_SZ)]),
     "mxm_grouped": (_I, [_I64, _P, _I, _I, _P, _SZ, _P]),
+    "mxm_grouped_plan": (_I, [_I64, _P, _I, _I, ctypes.POINTER(GroupPlan), _P, _SZ, _P]),
+    "mxm_grouped_workspace_size_plan": (_I, [_I64, _P, _I, _I, ctypes.POINTER(GroupPlan),
+                                             ctypes.POINTER(_SZ)]),
     "mxm_get_device_status": (_I, [_P]),
     "mxm_peak_probe": (_I, [_I, ctypes.POINTER(ctypes.c_double)]),
     "mxm_debug_wait_timeout": (_I, [ctypes.c_uint64, _P]),
@@ -240,18 +250,23 @@ def problem_table(problems):
     return torch.tensor(rows, dtype=torch.int64).reshape(-1, 6)
 
 
-def mxm_grouped_workspace_size(table_host, mode: int, slices: int = 7) -> int:
+def mxm_grouped_workspace_size(table_host, mode: int, slices: int = 7,
+                               plan: GroupPlan | None = None) -> int:
     size = ctypes.c_size_t(0)
     t = table_host.contiguous()
-    _check(load().mxm_grouped_workspace_size(t.shape[0], t.data_ptr(), int(mode), int(slices),
-                                             ctypes.byref(size)), "mxm_grouped_workspace_size")
+    _check(load().mxm_grouped_workspace_size_plan(
+        t.shape[0], t.data_ptr(), int(mode), int(slices),
+        ctypes.byref(plan) if plan is not None else None, ctypes.byref(size)),
+        "mxm_grouped_workspace_size")
     return int(size.value)
 
 
-def mxm_grouped(table_device, mode: int, slices: int, ws, stream=None):
-    _check(load().mxm_grouped(table_device.shape[0], table_device.data_ptr(), int(mode),
-                              int(slices), ws.data_ptr(), ws.numel() * ws.element_size(),
-                              _stream_ptr(stream)), "mxm_grouped")
+def mxm_grouped(table_device, mode: int, slices: int, ws, stream=None,
+                plan: GroupPlan | None = None):
+    _check(load().mxm_grouped_plan(table_device.shape[0], table_device.data_ptr(), int(mode),
+                                   int(slices), ctypes.byref(plan) if plan is not None else None,
+                                   ws.data_ptr(), ws.numel() * ws.element_size(),
+                                   _stream_ptr(stream)), "mxm_grouped")
 
 
 def mxm_get_device_status(stream=None) -> int:

@@ -133,11 +133,25 @@ def test_grouped_workspace_size_on_host():
     size = ctypes.c_size_t(0)
     st = lib.mxm_grouped_workspace_size(3, rows.ctypes.data, 1, 7, ctypes.byref(size))
     assert st == mxm.MXM_OK
-    # A tiles: 1*1 + 2*1 ; B tiles: 1*1 + 1*1 ; 7 planes of 32 KiB tiles
-    assert size.value >= 7 * (3 + 2) * 32768
-    assert size.value < 7 * (3 + 2) * 32768 + 16 * 1024
+    # A tiles: 1*1 + 2*1 ; B tiles: 1*1 + 1*1 ; 7 planes of 32 KiB tiles; the
+    # spill areas of up to 256 CTAs of the diagonal-pair GEMM (2 x 128 x 128 x
+    # 8 bytes each); no running sums: both problems are short-k (one k-block)
+    fixed = 7 * (3 + 2) * 32768 + 256 * 2 * 128 * 128 * 8
+    assert fixed <= size.value < fixed + 16 * 1024
+    # with every problem on the diagonal-pair GEMM (short_kt = 0): the
+    # running sums of the 3 C tiles (128 x 128 x 8 bytes each) as well
+    plan = mxm.GroupPlan(0)
+    st = lib.mxm_grouped_workspace_size_plan(3, rows.ctypes.data, 1, 7, ctypes.byref(plan),
+                                             ctypes.byref(size))
+    assert st == mxm.MXM_OK
+    assert fixed + 3 * 128 * 128 * 8 <= size.value < fixed + 3 * 128 * 128 * 8 + 16 * 1024
+    bad_plan = mxm.GroupPlan(-2)
+    assert lib.mxm_grouped_workspace_size_plan(3, rows.ctypes.data, 1, 7, ctypes.byref(bad_plan),
+                                               ctypes.byref(size)) == mxm.MXM_ERR_INVALID_ARG
+    # native: the plan only (the operands are read in place): a 256-byte
+    # header and one record per problem, rounded to 1 KiB
     st = lib.mxm_grouped_workspace_size(3, rows.ctypes.data, 0, 0, ctypes.byref(size))
-    assert st == mxm.MXM_OK and size.value >= (5 + 5) * 128 * 16 * 8
+    assert st == mxm.MXM_OK and size.value == 1024
     bad = rows.copy()
     bad[0, 3] = -1
     assert lib.mxm_grouped_workspace_size(3, bad.ctypes.data, 1, 7, ctypes.byref(size)) == \

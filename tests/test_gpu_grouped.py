@@ -25,19 +25,19 @@ def make_group(dims, seed=0, kind="uniform"):
     return hs, ds
 
 
-def run_group(ds, mode, S, graph=False):
+def run_group(ds, mode, S, graph=False, plan=None):
     table_h = mxm.problem_table(ds)
-    ws_bytes = mxm.mxm_grouped_workspace_size(table_h, mode, S)
+    ws_bytes = mxm.mxm_grouped_workspace_size(table_h, mode, S, plan)
     ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device="cuda")
     table_d = table_h.cuda()
     if not graph:
-        mxm.mxm_grouped(table_d, mode, S, ws)
+        mxm.mxm_grouped(table_d, mode, S, ws, plan=plan)
     else:
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=s):
-            mxm.mxm_grouped(table_d, mode, S, ws, stream=s)
+            mxm.mxm_grouped(table_d, mode, S, ws, stream=s, plan=plan)
         for _, _, C in ds:
             C.fill_(float("nan"))
         g.replay()
@@ -50,12 +50,21 @@ DIMS = [(1, 1, 1), (17, 5, 33), (128, 64, 128), (129, 65, 131), (300, 200, 257),
         (0, 5, 7), (5, 0, 7), (7, 9, 0), (1000, 33, 20), (64, 300, 500), (256, 256, 256)]
 
 
+# The emulated problems run on two slice GEMMs split by k (mxm_group_plan):
+# the default sends every problem here to the one-diagonal kernel; short_kt
+# = 0 sends all of them to the diagonal-pair kernel, 1 splits them.
+PLANS = {"default": None, "pair": mxm.GroupPlan(0), "split": mxm.GroupPlan(1)}
+
+
 @pytest.mark.parametrize("graph", [False, True])
+@pytest.mark.parametrize("plan", ["default", "pair", "split"])
 @pytest.mark.parametrize("mode,S", [(mxm.MODE_EMUL_I8, 7), (mxm.MODE_EMUL_BF16, 6),
                                     (mxm.MODE_EMUL_RN8, 6), (mxm.MODE_F64, 0)])
-def test_grouped_matches_oracle(mode, S, graph):
+def test_grouped_matches_oracle(mode, S, graph, plan):
+    if mode == mxm.MODE_F64 and plan != "default":
+        pytest.skip("the plan only splits emulated calls")
     hs, ds = make_group(DIMS, kind="spread" if mode != mxm.MODE_F64 else "uniform")
-    assert run_group(ds, mode, S, graph=graph) == mxm.MXM_OK
+    assert run_group(ds, mode, S, graph=graph, plan=PLANS[plan]) == mxm.MXM_OK
     for (A, B), (_, _, C) in zip(hs, ds):
         got = C.cpu().numpy()
         if mode == mxm.MODE_F64:
@@ -68,6 +77,33 @@ def test_grouped_matches_oracle(mode, S, graph):
             beta = 8 if mode == mxm.MODE_EMUL_BF16 else 7
             assert_bitwise(got, oracle.ozaki_gemm(A, B, S=S, beta=beta),
                            f"grouped emul {A.shape}x{B.shape}")
+
+
+# Edge tiles: the grouped kernels cut work at 16 columns and 16 k (the MMA
+# steps) and copy only the rows an edge tile reads, and the native kernel
+# cuts at 32 x 32 pieces and 4 k; every remainder around those steps.
+EDGE_DIMS = [(m, k, n) for m in (1, 9, 40, 130) for k in (1, 15, 16, 17, 64, 65, 129)
+             for n in (1, 16, 17, 100)]
+
+
+@pytest.mark.parametrize("mode,S,plan", [(mxm.MODE_EMUL_I8, 5, "default"),
+                                         (mxm.MODE_EMUL_I8, 5, "pair"),
+                                         (mxm.MODE_EMUL_RN8, 4, "default"),
+                                         (mxm.MODE_EMUL_RN8, 4, "pair"),
+                                         (mxm.MODE_F64, 0, "default")])
+def test_grouped_edge_tiles(mode, S, plan):
+    hs, ds = make_group(EDGE_DIMS, seed=3, kind="spread" if mode != mxm.MODE_F64 else "uniform")
+    assert run_group(ds, mode, S, plan=PLANS[plan]) == mxm.MXM_OK
+    for (A, B), (_, _, C) in zip(hs, ds):
+        got = C.cpu().numpy()
+        if mode == mxm.MODE_F64:
+            assert_within_bound(got, oracle.gemm_dot2(A, B), oracle.gemm_abs(A, B), A.shape[1],
+                                f"edge f64 {A.shape}x{B.shape}")
+        elif mode == mxm.MODE_EMUL_RN8:
+            assert_bitwise(got, oracle.ozaki_gemm_rn8(A, B, S), f"edge rn8 {A.shape}x{B.shape}")
+        else:
+            assert_bitwise(got, oracle.ozaki_gemm(A, B, S=S, beta=7),
+                           f"edge emul {A.shape}x{B.shape}")
 
 
 def test_grouped_workspace_too_small_reported():
