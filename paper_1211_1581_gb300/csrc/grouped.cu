@@ -277,8 +277,8 @@ extern "C" mxm_status mxm_grouped_plan(int64_t count, const mxm_problem* d_probl
   if (mode == MXM_MODE_F64)
     e = launch_f64_grouped(ws, status, s);
   else
-    e = launch_ozaki_grouped(ws, slices, mode == MXM_MODE_EMUL_I8 ? 7 : 8, 0, status, s,
-                             mode == MXM_MODE_EMUL_RN8);
+    e = launch_ozaki_grouped(ws, slices, mode == MXM_MODE_EMUL_I8 ? 7 : 8, plan_short_kt(plan),
+                             status, s, mode == MXM_MODE_EMUL_RN8);
   return e == cudaSuccess ? MXM_OK : MXM_ERR_CUDA;
 }
 

@@ -383,7 +383,9 @@ __device__ __forceinline__ int64_t grouped_find(const Rec* recs, int64_t count, 
 // all on the one-diagonal kernel is fastest (11.0 ms at S = 8 against 14.4 ms
 // all on the pair kernel), so the default takes every problem up to 8 blocks.
 constexpr int kGroupedShortKt = 8;
-cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t max_kt, int* status,
+// short_kt: the plan's boundary (k-blocks) between the short-k problems (the
+// one-diagonal kernel) and the long-k ones (the diagonal-pair kernel).
+cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t short_kt, int* status,
                                  cudaStream_t s, bool rn = false);
 // Native grouped products: work units of 32 x 32 C elements (one warp each,
 // operands loaded straight from the caller's arrays, k in steps of 4).

@@ -1120,24 +1120,32 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool last = (g == 2);
         int er = 0;
         if (!kFloat && last && row_ok) er = exponent_from_absbits(j.rowbits[row]);
-        // 8 columns per step of a rolled loop; D is rotated down by 8 after
-        // each step so the body only names D[0..7] (compact code).  The kind
-        // of the fold step (int64 partial, the conversion to FP64, an FP64
-        // addition) is fixed per diagonal, so the 8 elements of a step are
-        // straight-line code.
+        // E columns per step of a rolled loop (8 with 64-bit digit sums, 32
+        // with 32-bit ones: one tensor-memory round trip per 32 running sums
+        // instead of four); D is rotated down by E after each step so the
+        // body only names D[0..E-1] (compact code).  The kind of the fold
+        // step (int64 partial, the conversion to FP64, an FP64 addition) is
+        // fixed per diagonal, so the E elements of a step are straight-line
+        // code.
         auto fold_pass = [&](auto kc) {
           [[maybe_unused]] constexpr int K = decltype(kc)::value;
+          constexpr int E = (sizeof(Acc) == 4 && !kFloat) ? 32 : 8;
 #pragma unroll 1
-          for (int ch = 0; ch < 8; ++ch) {
-            if (half * 64 + ch * 8 < ncols) {  // warp-uniform
-              uint32_t r[16];
+          for (int ch = 0; ch < 64 / E; ++ch) {
+            if (half * 64 + ch * E < ncols) {  // warp-uniform
+              uint32_t r[2 * E];
               if (!first) {
-                tmem_ld16(t_acc + ch * 16, r);
+                if constexpr (E == 32) {
+                  tmem_ld32(t_acc + ch * 64, *reinterpret_cast<uint32_t(*)[32]>(r));
+                  tmem_ld32(t_acc + ch * 64 + 32, *reinterpret_cast<uint32_t(*)[32]>(r + 32));
+                } else {
+                  tmem_ld16(t_acc + ch * 16, r);
+                }
                 tmem_wait_ld();
               }
-              uint64_t st[8];
+              uint64_t st[E];
 #pragma unroll
-              for (int i = 0; i < 8; ++i) {
+              for (int i = 0; i < E; ++i) {
                 if constexpr (kFloat) {
                   st[i] = static_cast<uint64_t>(__double_as_longlong(static_cast<double>(D[i])));
                 } else {
@@ -1148,10 +1156,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               if (last) {
                 if (row_ok) {
-                  const int64_t col0 = j.col0 + half * 64 + ch * 8;
+                  const int64_t col0 = j.col0 + half * 64 + ch * E;
                   double* crow = j.C + row * j.n;
 #pragma unroll
-                  for (int i = 0; i < 8; ++i) {
+                  for (int i = 0; i < E; ++i) {
                     const int64_t col = col0 + i;
                     if (col < j.n) {
                       if constexpr (kFloat)
@@ -1164,16 +1172,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
               } else {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < E; ++i) {
                   r[2 * i] = static_cast<uint32_t>(st[i]);
                   r[2 * i + 1] = static_cast<uint32_t>(st[i] >> 32);
                 }
-                tmem_st16(t_acc + ch * 16, r);
+                if constexpr (E == 32) {
+                  tmem_st32(t_acc + ch * 64, *reinterpret_cast<const uint32_t(*)[32]>(r));
+                  tmem_st32(t_acc + ch * 64 + 32,
+                            *reinterpret_cast<const uint32_t(*)[32]>(r + 32));
+                } else {
+                  tmem_st16(t_acc + ch * 16, r);
+                }
                 tmem_wait_st();
               }
             }
 #pragma unroll
-            for (int i = 0; i < 56; ++i) D[i] = D[i + 8];
+            for (int i = 0; i < 64 - E; ++i) D[i] = D[i + E];
           }
         };
         if constexpr (kFloat) {
@@ -2058,7 +2072,7 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
   return cudaGetLastError();
 }
 
-cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t /*max_kt*/, int* status,
+cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t short_kt, int* status,
                                  cudaStream_t s, bool rn) {
   const int sms = sm_count();
   oz_grouped_prep_a_kernel<<<sms * 4, 256, 0, s>>>(ws, S, beta, rn, status);
@@ -2088,6 +2102,9 @@ cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t /*max_kt*
   // short-k problems: one diagonal at a time, FP64 running sums in tensor
   // memory (64-bit window sums: any k)
   OzGrouped st{hdr, recs, ws, rn ? 2 : 0, false};
+  const double dsum = static_cast<double>(S) * dmax * dmax * kOzTileK;
+  if (dsum * static_cast<double>(short_kt) < 2147483647.0)  // every short tile's sums fit int32
+    return launch_oz_gemm_t<int, false>(st, sms, S, beta, window, status, s);
   return launch_oz_gemm_t<long long, false>(st, sms, S, beta, window, status, s);
 }
 
