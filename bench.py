@@ -560,7 +560,8 @@ def run_suite(args):
             with tempfile.TemporaryDirectory() as td:
                 c = tune.tune(A, B, tag=kind, cache=tune.TuneCache(os.path.join(td, "t.json")))
             emit(case=case, inputs=kind, m=m, k=k, n=n, tuner_choice=c.name,
-                 slices=c.slices or None, ms=round(c.ms, 4), err_over_ku_AB=c.err_ratio)
+                 slices=c.slices or None, plan=c.plan, ms=round(c.ms, 4),
+                 err_over_ku_AB=c.err_ratio)
         del A, B, C, ref, bnd
         torch.cuda.empty_cache()
 
@@ -600,18 +601,25 @@ def run_suite(args):
     check = np.random.default_rng(5).choice(len(dims), 24, replace=False)
     refs = [tune.accuracy_reference(ds[p][0], ds[p][1], stream) for p in check]
     for mode, S in ((mxm.MODE_F64, 0), (mxm.MODE_EMUL_I8, s_i8), (mxm.MODE_EMUL_RN8, s_rn8)):
-        ws = torch.empty(max(1, mxm.mxm_grouped_workspace_size(table_h, mode, S)),
+        # the size classes of the emulated call from the grouped tuner
+        plan = None
+        if mode != mxm.MODE_F64:
+            with tempfile.TemporaryDirectory() as td:
+                plan = tune.tune_grouped(table_h, table_d, mode, S,
+                                         cache=tune.TuneCache(os.path.join(td, "g.json")))
+        ws = torch.empty(max(1, mxm.mxm_grouped_workspace_size(table_h, mode, S, plan)),
                          dtype=torch.uint8, device="cuda")
         side = torch.cuda.Stream()
         side.wait_stream(stream)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=side):
-            mxm.mxm_grouped(table_d, mode, S, ws, stream=side)
+            mxm.mxm_grouped(table_d, mode, S, ws, stream=side, plan=plan)
         ms = _timed_ms(g.replay, 3, stream)
         st = mxm.mxm_get_device_status()
         err = max(tune.error_ratio(ds[p][2], r, b) for p, (r, b) in zip(check, refs))
         emit(case="grouped", inputs="uniform", problems=len(dims), mode=names[mode],
              slices=S or None, slices_from=f"tuner: largest need over {len(sample)} sampled problems" if S else None,
+             short_kt=plan.short_kt if plan is not None else None,
              ms=round(ms, 4), tflops=round(flops / (ms * 1e-3) / 1e12, 3),
              err_over_ku_AB_24_checked=err, status=st, graph=True)
         del ws, g

@@ -22,9 +22,19 @@ cost more).  Results are kept in a JSON cache keyed by device, a tag the
 caller gives for the kind of data, the power-of-two size class of (m, k, n)
 and ``tol``; ``gemm`` looks the choice up and tunes on a miss.
 
-The tile shapes are not tuned: they are fixed by the tensor instructions
-(128 x 128 output tiles, the MMA shape of tcgen05 and the TMEM column
-budget), and the persistent kernels size their grids to the SM count.
+After the engine and slice count, ``tune`` chooses the product's layout on
+the GPU (``mxm_plan``) by measuring it: the C-tile shape of the slice GEMM
+(256 x 128 tiles on CTA pairs, cta_group::2, or 128 x 128 on single CTAs),
+the raster group of the persistent tile walk (how many tile-rows the CTAs
+working at the same time share), the k-block order, and split-k (none, the
+library's rule, or other range counts) for products with few C tiles.  The
+search changes one field at a time from the library's rule and keeps a
+change only when it is more than 1 % faster and still accurate (for the
+emulated engines every plan gives the same bits; the native FP64 product's
+rounding depends on split-k, so its error is checked again).  The choice,
+plan included, is kept in the cache.  For grouped calls ``tune_grouped``
+chooses the size classes: the k (in blocks of 128) up to which problems run
+on the one-diagonal slice GEMM rather than the diagonal-pair one.
 """
 from __future__ import annotations
 
@@ -46,6 +56,9 @@ ENGINES = (mxm.MODE_F64, mxm.MODE_EMUL_I8, mxm.MODE_EMUL_BF16, mxm.MODE_EMUL_FP8
            mxm.MODE_EMUL_RN8)
 
 
+PLAN_FIELDS = ("raster", "kb_order", "cta", "splitk")
+
+
 @dataclass
 class Choice:
     mode: int
@@ -53,6 +66,8 @@ class Choice:
     ms: float
     err_ratio: float
     measured: list = field(default_factory=list)  # [mode, slices, err_ratio, ms] per candidate
+    plan: dict = field(default_factory=dict)      # mxm_plan fields ({}: the library's rule)
+    plan_measured: list = field(default_factory=list)  # [plan, err_ratio, ms] per plan tried
 
     @property
     def name(self) -> str:
@@ -86,6 +101,9 @@ class TuneCache:
 
     def put(self, key: str, choice: Choice):
         self.entries[key] = asdict(choice)
+        self.save()
+
+    def save(self):
         d = os.path.dirname(os.path.abspath(self.path))
         os.makedirs(d, exist_ok=True)
         fd, tmp = tempfile.mkstemp(dir=d, prefix=".mxm_tune.")
@@ -118,11 +136,69 @@ def select(measure, tol: float, modes=ENGINES, max_slices=None) -> Choice:
     return Choice(mode=best[0], slices=best[1], ms=best[3], err_ratio=best[2], measured=measured)
 
 
-def _run(mode, slices, A, B, C, stream):
-    if mode == mxm.MODE_F64:
+def make_plan(plan: dict | None):
+    """An mxm.Plan from a dict of its fields (missing fields: 0, the rule)."""
+    if not plan:
+        return None
+    return mxm.Plan(*(int(plan.get(f, 0)) for f in PLAN_FIELDS))
+
+
+def _run(mode, slices, A, B, C, stream, plan: dict | None = None):
+    if plan:
+        mxm.mxm_gemm_plan(mode, A, B, C, slices=slices, plan=make_plan(plan), stream=stream)
+    elif mode == mxm.MODE_F64:
         mxm.mxm_f64(A, B, C, stream=stream)
     else:
         mxm.mxm_gemm(mode, A, B, C, slices=slices, stream=stream)
+
+
+def plan_candidates(mode: int, m: int, k: int, n: int) -> dict:
+    """Per plan field, the values worth trying for this product (the rule,
+    0, first).  CTA pairs need two or more tile-rows of A and bf16 digits;
+    split-k is only considered for products with fewer C tiles than SMs."""
+    tiles = -(-m // 128) * -(-n // 128)
+    emul_bf16 = mode in (mxm.MODE_EMUL_I8, mxm.MODE_EMUL_BF16, mxm.MODE_EMUL_RN8)
+    c = {}
+    if mode == mxm.MODE_F64:
+        c["raster"] = [0, 4, 16]
+        kt = -(-k // 16)
+        if tiles < 152 and kt >= 16:
+            rule = max(1, min(304 // tiles, kt // 8))
+            c["splitk"] = [0] + sorted({1, max(2, rule // 2), min(kt, 2 * rule)} - {rule})
+        return c
+    if emul_bf16 or mode == mxm.MODE_EMUL_FP8:
+        c["raster"] = [0, 2, 8]
+        c["kb_order"] = [0, 1]
+    if emul_bf16:
+        if -(-m // 128) >= 2:
+            c["cta"] = [0, 1]
+        kt = -(-k // 128)
+        if tiles < 152 and kt >= 2:
+            rule = max(1, min(304 // tiles, kt // 4))
+            c["splitk"] = [0] + sorted({1, max(2, rule // 2), min(kt, 2 * rule)} - {rule})
+    return c
+
+
+def select_plan(measure, candidates: dict, tol: float, gain: float = 0.01):
+    """Coordinate search over the plan fields: from the rule (every field
+    0), try each alternative of one field at a time on top of the best plan
+    so far; keep it when it is accurate and more than ``gain`` faster.
+    ``measure(plan) -> (err_ratio, ms)``.  Returns (plan, err, ms, tried)."""
+    best = {}
+    err, ms = measure(best)
+    tried = [[dict(best), float(err), float(ms)]]
+    for f, values in candidates.items():
+        for v in values:
+            if v == best.get(f, 0):
+                continue
+            p = dict(best)
+            p[f] = v
+            e, t = measure(p)
+            tried.append([dict(p), float(e), float(t)])
+            if e <= tol and t < ms * (1.0 - gain):
+                best, err, ms = p, e, t
+    best = {f: v for f, v in best.items() if v != 0}
+    return best, float(err), float(ms), tried
 
 
 def accuracy_reference(A, B, stream=None):
@@ -159,14 +235,14 @@ def device_measure(A, B, reps: int = 3, stream=None):
     ref, bound = accuracy_reference(A, B, stream)
     C = torch.empty_like(ref)
 
-    def measure(mode, slices):
-        _run(mode, slices, A, B, C, stream)  # warm-up (and workspace growth)
+    def measure(mode, slices, plan=None):
+        _run(mode, slices, A, B, C, stream, plan)  # warm-up (and workspace growth)
         times = []
         for _ in range(reps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _run(mode, slices, A, B, C, stream)
+            _run(mode, slices, A, B, C, stream, plan)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -195,13 +271,21 @@ def grouped_slices(problems, mode: int = mxm.MODE_EMUL_I8, tol: float = 1.0,
 
 
 def tune(A, B, tag: str = "default", tol: float = 1.0, cache: TuneCache | None = None,
-         reps: int = 3, stream=None) -> Choice:
-    """Measure every candidate on A, B and store the choice under
-    (device, tag, size class, tol)."""
+         reps: int = 3, stream=None, plans: bool = True) -> Choice:
+    """Measure every candidate on A, B (engine and slice count, then the
+    plan of the chosen one) and store the choice under (device, tag, size
+    class, tol)."""
     import torch
     m, k = A.shape
     n = B.shape[1]
-    choice = select(device_measure(A, B, reps=reps, stream=stream), tol)
+    measure = device_measure(A, B, reps=reps, stream=stream)
+    choice = select(measure, tol)
+    if plans:
+        cands = plan_candidates(choice.mode, m, k, n)
+        if cands:
+            plan, err, ms, tried = select_plan(
+                lambda p: measure(choice.mode, choice.slices, p), cands, tol)
+            choice.plan, choice.err_ratio, choice.ms, choice.plan_measured = plan, err, ms, tried
     cache = cache if cache is not None else TuneCache()
     cache.put(cache_key(torch.cuda.get_device_name(A.device), tag, m, k, n, tol), choice)
     return choice
@@ -218,5 +302,50 @@ def gemm(A, B, C, tag: str = "default", tol: float = 1.0, cache: TuneCache | Non
     choice = cache.get(cache_key(torch.cuda.get_device_name(A.device), tag, m, k, n, tol))
     if choice is None:
         choice = tune(A, B, tag=tag, tol=tol, cache=cache, stream=stream)
-    _run(choice.mode, choice.slices, A, B, C, stream)
+    _run(choice.mode, choice.slices, A, B, C, stream, choice.plan)
     return choice
+
+
+def grouped_key(device: str, tag: str, count: int, mode: int, slices: int) -> str:
+    return f"{device}|grouped|{tag}|count={count}|{MODE_NAMES.get(mode, mode)}|S={slices}"
+
+
+def tune_grouped(table_h, table_d, mode: int, slices: int, tag: str = "default",
+                 cache: TuneCache | None = None, candidates=(0, 1, 2, 4, 8), reps: int = 2,
+                 stream=None):
+    """The size classes of a grouped emulated call: the largest k (in
+    blocks of 128) that still runs on the one-diagonal slice GEMM, chosen by
+    timing the whole call (every boundary gives the same bits) and cached
+    under (device, tag, count, mode, slices).  Returns an mxm.GroupPlan."""
+    import torch
+    cache = cache if cache is not None else TuneCache()
+    key = grouped_key(torch.cuda.get_device_name(table_d.device), tag, table_h.shape[0], mode,
+                      slices)
+    hit = cache.entries.get(key)
+    if hit is not None:
+        return mxm.GroupPlan(int(hit["short_kt"]))
+    stream = stream or torch.cuda.current_stream()
+    kmax = int(table_h[:, 4].max().item()) if table_h.shape[0] else 0
+    cands = sorted(set(int(c) for c in candidates) | {-(-kmax // 128)})
+    measured = []
+    for skt in cands:
+        plan = mxm.GroupPlan(skt)
+        ws = torch.empty(max(1, mxm.mxm_grouped_workspace_size(table_h, mode, slices, plan)),
+                         dtype=torch.uint8, device=table_d.device)
+        mxm.mxm_grouped(table_d, mode, slices, ws, stream=stream, plan=plan)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            mxm.mxm_grouped(table_d, mode, slices, ws, stream=stream, plan=plan)
+        e1.record(stream)
+        e1.synchronize()
+        st = mxm.mxm_get_device_status(stream)
+        if st != mxm.MXM_OK:
+            raise mxm.MxmError(st, "tune_grouped")
+        measured.append([skt, e0.elapsed_time(e1) / reps])
+        del ws
+    best = min(measured, key=lambda r: r[1])
+    cache.entries[key] = {"short_kt": best[0], "ms": best[1], "measured": measured}
+    cache.save()
+    return mxm.GroupPlan(best[0])

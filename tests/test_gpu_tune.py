@@ -59,3 +59,58 @@ def test_gemm_uses_the_cache(tmp_path, monkeypatch):
     torch.cuda.synchronize()
     assert second == first
     assert torch.equal(C1, C2)
+
+
+def test_tuned_plan_few_tiles(tmp_path):
+    """A product with few C tiles and long k: the plan search tries split-k
+    counts and CTA forms; the tuned product stays bit-identical to the
+    oracle's emulation when an emulated engine is chosen, and within the
+    FP64 bound in any case; the cache keeps the plan."""
+    m, k, n = 256, 4096, 256
+    A_h, B_h = inputs.gemm_operands("spread", m, k, n, seed=7, cfg=0)
+    A = torch.from_numpy(A_h).cuda()
+    B = torch.from_numpy(B_h).cuda()
+    cache = tune.TuneCache(str(tmp_path / "t.json"))
+    choice = tune.tune(A, B, tag="spread", cache=cache)
+    assert choice.plan_measured and choice.plan_measured[0][0] == {}
+    C = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    tune._run(choice.mode, choice.slices, A, B, C, torch.cuda.current_stream(), choice.plan)
+    torch.cuda.synchronize()
+    assert mxm.mxm_get_device_status() == mxm.MXM_OK
+    got = C.cpu().numpy()
+    assert_within_bound(got, oracle.gemm_dot2(A_h, B_h), oracle.gemm_abs(A_h, B_h), k,
+                        f"tuned {choice.name} S={choice.slices} plan={choice.plan}")
+    if choice.mode == mxm.MODE_EMUL_I8:
+        assert np.array_equal(got, oracle.ozaki_gemm(A_h, B_h, S=choice.slices, beta=7))
+    key = tune.cache_key(torch.cuda.get_device_name(0), "spread", m, k, n, 1.0)
+    assert tune.TuneCache(cache.path).get(key).plan == choice.plan
+
+
+def test_tune_grouped_size_classes(tmp_path):
+    """The grouped tuner times the size-class boundaries and caches the
+    fastest; the call under it gives the oracle's bits."""
+    dims = [(100, 40, 90), (300, 700, 200), (64, 1000, 500), (129, 129, 17), (20, 300, 40)]
+    hs, ds = [], []
+    for p, (m, k, n) in enumerate(dims):
+        A_h, B_h = inputs.gemm_operands("spread", m, k, n, seed=8, cfg=p)
+        hs.append((A_h, B_h))
+        ds.append((torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda(),
+                   torch.empty((m, n), dtype=torch.float64, device="cuda")))
+    table_h = mxm.problem_table(ds)
+    table_d = table_h.cuda()
+    cache = tune.TuneCache(str(tmp_path / "g.json"))
+    plan = tune.tune_grouped(table_h, table_d, mxm.MODE_EMUL_I8, 8, cache=cache)
+    key = tune.grouped_key(torch.cuda.get_device_name(0), "default", len(dims),
+                           mxm.MODE_EMUL_I8, 8)
+    entry = tune.TuneCache(cache.path).entries[key]
+    assert entry["short_kt"] == plan.short_kt and len(entry["measured"]) >= 5
+    ws = torch.empty(mxm.mxm_grouped_workspace_size(table_h, mxm.MODE_EMUL_I8, 8, plan),
+                     dtype=torch.uint8, device="cuda")
+    mxm.mxm_grouped(table_d, mxm.MODE_EMUL_I8, 8, ws, plan=plan)
+    torch.cuda.synchronize()
+    assert mxm.mxm_get_device_status() == mxm.MXM_OK
+    for (A_h, B_h), (_, _, C) in zip(hs, ds):
+        assert np.array_equal(C.cpu().numpy(), oracle.ozaki_gemm(A_h, B_h, S=8, beta=7))
+    # a second call is a cache hit
+    assert tune.tune_grouped(table_h, table_d, mxm.MODE_EMUL_I8, 8,
+                             cache=cache).short_kt == plan.short_kt

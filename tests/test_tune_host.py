@@ -105,3 +105,55 @@ def test_grouped_slices_takes_the_worst_problem():
     probs = [("long", None), ("short", None), ("mid", None)]
     assert tune.grouped_slices(probs, measure_for=measure_for) == 8
     assert tune.grouped_slices(probs[:1], measure_for=measure_for) == 6
+
+
+def test_select_plan_coordinate_search():
+    """From the rule (all fields 0), each alternative of one field is tried
+    on top of the best plan so far; a change is kept only when accurate and
+    more than 1 % faster."""
+    cost = {("raster", 2): 0.90, ("raster", 8): 1.05, ("kb_order", 1): 0.95,
+            ("cta", 1): 1.20, ("splitk", 1): 0.97}
+    tried = []
+
+    def measure(plan):
+        tried.append(dict(plan))
+        t = 100.0
+        for f, v in plan.items():
+            t *= cost.get((f, v), 1.0)
+        err = 5.0 if plan.get("splitk") == 1 else 0.5  # an inaccurate alternative
+        return err, t
+
+    cands = {"raster": [0, 2, 8], "kb_order": [0, 1], "cta": [0, 1], "splitk": [0, 1]}
+    plan, err, ms, rows = tune.select_plan(measure, cands, tol=1.0)
+    assert plan == {"raster": 2, "kb_order": 1}
+    assert abs(ms - 100.0 * 0.90 * 0.95) < 1e-9 and err == 0.5
+    assert tried[0] == {} and len(rows) == len(tried) == 1 + 2 + 1 + 1 + 1
+    # raster 8 was tried on top of nothing better than raster 2: it came
+    # after raster 2 was kept, with raster replaced
+    assert {"raster": 8} in tried
+
+
+def test_plan_candidates_follow_the_shape():
+    big = tune.plan_candidates(mxm.MODE_EMUL_I8, 8192, 8192, 8192)
+    assert "splitk" not in big and big["cta"] == [0, 1] and big["raster"][0] == 0
+    few = tune.plan_candidates(mxm.MODE_EMUL_I8, 128, 65536, 128)
+    assert "cta" not in few and few["splitk"][0] == 0 and 1 in few["splitk"]
+    native = tune.plan_candidates(mxm.MODE_F64, 128, 65536, 128)
+    assert native["splitk"][0] == 0 and "cta" not in native
+    assert "splitk" not in tune.plan_candidates(mxm.MODE_EMUL_FP8, 128, 65536, 128)
+
+
+def test_cache_keeps_the_plan(tmp_path):
+    path = str(tmp_path / "c.json")
+    c = tune.TuneCache(path)
+    ch = tune.Choice(mode=mxm.MODE_EMUL_I8, slices=7, ms=1.5, err_ratio=0.1,
+                     plan={"raster": 2, "splitk": 1}, plan_measured=[[{}, 0.1, 1.6]])
+    c.put("k", ch)
+    back = tune.TuneCache(path).get("k")
+    assert back == ch and back.plan == {"raster": 2, "splitk": 1}
+    p = tune.make_plan(back.plan)
+    assert (p.raster, p.kb_order, p.cta, p.splitk) == (2, 0, 0, 1)
+    assert tune.make_plan({}) is None
+    # entries written before plans existed still load
+    c.entries["old"] = {"mode": 1, "slices": 7, "ms": 1.0, "err_ratio": 0.2, "measured": []}
+    assert tune.TuneCache.get(c, "old").plan == {}
