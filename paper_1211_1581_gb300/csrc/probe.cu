@@ -2,8 +2,9 @@
 // denominators the driver does not measure: FP64 DFMA, FP64 DMMA, legacy
 // IMMA) plus tcgen05 BF16 for comparison with the driver's cuBLAS figure.
 // Each probe keeps its operands in registers (or zeroed shared memory), runs
-// a fixed number of independent operations per warp and is timed with CUDA
-// events; the rate is operations / time over the whole GPU.
+// a fixed number of independent operations per warp (tens of milliseconds of
+// work, so that launch overhead and the clock's ramp do not count) and is
+// timed with CUDA events; the rate is operations / time over the whole GPU.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -147,19 +148,19 @@ extern "C" mxm_status mxm_peak_probe(int kind, double* tflops) {
     const int blocks = sms * 4, threads = 256;
     switch (kind) {
       case 0: {
-        const int iters = timed ? 512 : 8;
+        const int iters = timed ? 16384 : 8;
         probe_dfma_kernel<<<blocks, threads>>>(iters, 1.0, static_cast<double*>(sink));
         ops = 2.0 * 8 * iters * double(blocks) * threads;
         break;
       }
       case 1: {
-        const int iters = timed ? 32 : 2;
+        const int iters = timed ? 1024 : 2;
         probe_dmma_kernel<<<blocks, threads>>>(iters, 1.0, static_cast<double*>(sink));
         ops = 2.0 * 16 * 8 * 4 * 8.0 * iters * blocks * (threads / 32);
         break;
       }
       case 4: {
-        const int iters = timed ? 512 : 8;
+        const int iters = timed ? 4096 : 8;
         probe_imma_kernel<<<blocks, threads>>>(iters, 1, static_cast<int*>(sink));
         ops = 2.0 * 16 * 8 * 32 * 8.0 * iters * blocks * (threads / 32);
         break;
