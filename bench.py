@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--no-check", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--suite", nargs="?", const="all",
-                   choices=("all", "gemm", "spmv", "cg", "fft"),
+                   choices=("all", "gemm", "spmv", "cg", "fft", "probes"),
                    help="instead of the benchmark line: one JSON line per case of the "
                         "workload suite (FP64 sweep, slice counts and modes, rectangular "
                         "shapes, grouped batch under a CUDA graph; mod2as sparse products; "
@@ -529,6 +529,10 @@ def run_suite(args):
     def emit(**d):
         print(json.dumps(dict(suite=True, **d)), flush=True)
 
+    if args.suite in ("all", "probes"):
+        run_probe_suite(emit)
+    if args.suite == "probes":
+        return
     if args.suite in ("all", "spmv"):
         run_spmv_suite(emit, stream, peaks, args.only)
     if args.suite in ("all", "cg"):
@@ -623,6 +627,27 @@ def run_suite(args):
              ms=round(ms, 4), tflops=round(flops / (ms * 1e-3) / 1e12, 3),
              err_over_ku_AB_24_checked=err, status=st, graph=True)
         del ws, g
+
+
+def run_probe_suite(emit, repeats=12, rounds=2):
+    """The unit probes behind the roofline denominators the driver does not
+    measure (FP64 DFMA and DMMA, legacy IMMA) and tcgen05 BF16 beside them:
+    each repeated back to back with SM clocks sampled around the repeats;
+    median TFLOP/s and TFLOP/s per GHz."""
+    from paper_1211_1581_gb300 import mxm
+    names = {0: "fp64_dfma", 1: "fp64_dmma", 4: "imma_s8", 2: "tcgen05_bf16_128x128"}
+    for rnd in range(rounds):
+        for kind, name in names.items():
+            clk = ClockSampler(0)
+            clk.start()
+            vals = [mxm.mxm_peak_probe(kind) for _ in range(repeats)]
+            c = clk.stop()
+            v = statistics.median(vals)
+            mhz = c.get("sm_mhz")
+            emit(case="probe", probe=name, kind=kind, round=rnd, tflops=round(v, 4),
+                 spread=[round(min(vals), 4), round(max(vals), 4)], sm_mhz=mhz,
+                 reasons=c.get("reasons"),
+                 tflops_per_ghz=round(v / (mhz / 1000.0), 4) if mhz else None)
 
 
 def _selected(key, only):
