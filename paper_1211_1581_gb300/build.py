@@ -50,43 +50,63 @@ def _inputs():
             + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+# The bounds-checked build (-DMXM_DEBUG_BOUNDS): the kernels check their tile
+# coordinates, copy sources and tensor-memory columns and record a violation
+# as MXM_ERR_INVALID_ARG in the device status word (never a trap).
+LIB_DEBUG = os.path.join(BUILD, "libmxm_debug.so")
+FLAVORS = {LIB: [], LIB_DEBUG: ["-DMXM_DEBUG_BOUNDS"]}
+
+
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Compile every CUDA source and link libmxm.so; returns its path."""
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra_flags=None, debug: bool = True) -> str:
+    """Compile every CUDA source and link libmxm.so (and, with debug, the
+    bounds-checked libmxm_debug.so, compiled in the same pool of parallel
+    nvcc processes); returns the path of libmxm.so."""
+    libs = [LIB] + ([LIB_DEBUG] if debug else [])
+    todo = [lib for lib in libs if force or not up_to_date(lib)]
+    if not todo:
         return LIB
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
-    flags = NVCC_FLAGS + ARCH + ["-I", CSRC, "-I", INCLUDE] + list(extra_flags or [])
-    objs = []
+    srcs = sources()
+    jobs = []
+    for lib in todo:
+        odir = os.path.join(BUILD, "debug") if lib == LIB_DEBUG else BUILD
+        os.makedirs(odir, exist_ok=True)
+        flags = (NVCC_FLAGS + ARCH + ["-I", CSRC, "-I", INCLUDE] + FLAVORS[lib] +
+                 list(extra_flags or []))
+        for src in srcs:
+            jobs.append((lib, src, os.path.join(odir, os.path.basename(src)[:-3] + ".o"), flags))
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+    def compile_one(job):
+        lib, src, obj, flags = job
         cmd = [nvcc, "-c", src, "-o", obj] + flags
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")
         if verbose and (r.stdout or r.stderr):
             print(r.stdout, r.stderr)
-        return obj
+        return lib, obj
 
-    srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-        objs = list(ex.map(compile_one, srcs))
+    # the slowest translation units first, so that they start at once
+    jobs.sort(key=lambda j: -os.path.getsize(j[1]))
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
+        done = list(ex.map(compile_one, jobs))
     libdir = _cuda_lib_dir(nvcc)
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + [
-        "-cudart", "shared", "-L", libdir, "-Xlinker", "-rpath," + libdir]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link of libmxm.so failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    for lib in todo:
+        objs = [o for (l, o) in done if l == lib]
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + [
+            "-cudart", "shared", "-L", libdir, "-Xlinker", "-rpath," + libdir]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link of {os.path.basename(lib)} failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -121,6 +121,11 @@ struct F64Single {
   int64_t m, n, Mt, Nt, Kt, splits;
   int64_t raster;
   __device__ __forceinline__ int64_t count() const { return Mt * Nt * splits; }
+  // the packed operand tiles (bounds checks of the debug build)
+  __device__ __forceinline__ const double* a_begin() const { return apack; }
+  __device__ __forceinline__ const double* a_end() const { return apack + Mt * Kt * (BM * BK); }
+  __device__ __forceinline__ const double* b_begin() const { return bpack; }
+  __device__ __forceinline__ const double* b_end() const { return bpack + Nt * Kt * (BN * BK); }
   __device__ __forceinline__ F64Tile tile(int64_t t) const {
     const int64_t tile = t / splits, sp = t - tile * splits;
     int64_t tm, tn;
@@ -177,7 +182,7 @@ __device__ __forceinline__ void load_frags(const double* __restrict__ A,
 }
 
 __global__ void __launch_bounds__(kGroupedF64Threads, 2)
-    f64_grouped_kernel(uint8_t* __restrict__ ws) {
+    f64_grouped_kernel(uint8_t* __restrict__ ws, int* __restrict__ status) {
   GroupedHeader* hdr = reinterpret_cast<GroupedHeader*>(ws);
   if (!hdr->valid) return;
   const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
@@ -196,6 +201,7 @@ __global__ void __launch_bounds__(kGroupedF64Threads, 2)
     const int64_t local = unit - r.tile_begin;
     const int64_t tm = local / r.Nt, tn = local - (local / r.Nt) * r.Nt;
     const int64_t row0 = tm * T, col0 = tn * T;
+    MXM_BOUNDS(row0 < r.m && col0 < r.n && local < r.Mt * r.Nt, status);
     const double* A = r.A;
     const double* B = r.B;
     const int64_t m = r.m, k = r.k, n = r.n;
@@ -285,6 +291,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
+          MXM_BOUNDS(in_range(j.a + kb * (BM * BK), kF64TileBytes, tiles.a_begin(),
+                              tiles.a_end()) &&
+                         in_range(j.b + kb * (BN * BK), kF64TileBytes, tiles.b_begin(),
+                                  tiles.b_end()),
+                     status);
           mbar_arrive_expect_tx(&sm.full[stage], 2 * kF64TileBytes);
           bulk_g2s(sm.a[stage], j.a + kb * (BM * BK), kF64TileBytes, &sm.full[stage]);
           bulk_g2s(sm.b[stage], j.b + kb * (BN * BK), kF64TileBytes, &sm.full[stage]);
@@ -422,10 +433,11 @@ cudaError_t launch_f64_gemm(uint8_t* ws, double* C, const F64Dims& d, int* statu
   return cudaGetLastError();
 }
 
-cudaError_t launch_f64_grouped(uint8_t* ws, int* /*status*/, cudaStream_t s) {
+cudaError_t launch_f64_grouped(uint8_t* ws, int* status, cudaStream_t s) {
   // two resident CTAs of 8 warps per SM, every warp pulling pieces until the
   // cursor passes the last one
-  f64_grouped_kernel<<<static_cast<unsigned>(2 * sm_count()), kGroupedF64Threads, 0, s>>>(ws);
+  f64_grouped_kernel<<<static_cast<unsigned>(2 * sm_count()), kGroupedF64Threads, 0, s>>>(ws,
+                                                                                          status);
   return cudaGetLastError();
 }
 

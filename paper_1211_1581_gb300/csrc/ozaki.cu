@@ -689,6 +689,20 @@ struct OzSingle {
   int eoff = 0;                // added to e_i + f_j in the final scaling (2: balanced digits)
   int64_t k = 0;               // the product's k (edge tiles)
   __device__ __forceinline__ long long* spill_area() const { return spill; }
+  // the digit planes and the running sums (bounds checks of the debug build)
+  __device__ __forceinline__ const uint8_t* a_end() const {
+    return aslices + static_cast<size_t>(S) * Mt * Kt * tile_bytes;
+  }
+  __device__ __forceinline__ const uint8_t* b_end() const {
+    return bslices + static_cast<size_t>(S) * Nt * Kt * tile_bytes;
+  }
+  __device__ __forceinline__ const uint8_t* a_begin() const { return aslices; }
+  __device__ __forceinline__ const uint8_t* b_begin() const { return bslices; }
+  __device__ __forceinline__ const uint64_t* sums_begin() const { return sums; }
+  __device__ __forceinline__ const uint64_t* sums_end() const {
+    return sums + (splits > 1 ? static_cast<size_t>(splits) * Mt * Nt * S
+                              : static_cast<size_t>(Mt) * Nt) * (kOzTileRows * kOzTileRows);
+  }
   int64_t raster = kDefaultRaster;  // tile-rows (pair-rows) per group of the tile walk
   bool kb_alt = false;         // alternate the k-block direction between diagonal (pair)s
   // Address k-block of the it-th k-block of diagonal (pair) q: every other
@@ -760,6 +774,17 @@ struct OzGrouped {
   }
   __device__ __forceinline__ int64_t count() const {
     return hdr->valid ? (long_k ? hdr->ltiles : hdr->stiles) : 0;
+  }
+  // the digit planes and the running sums (bounds checks of the debug build)
+  __device__ __forceinline__ const uint8_t* a_begin() const { return ws + hdr->off_a; }
+  __device__ __forceinline__ const uint8_t* a_end() const { return ws + hdr->off_b; }
+  __device__ __forceinline__ const uint8_t* b_begin() const { return ws + hdr->off_b; }
+  __device__ __forceinline__ const uint8_t* b_end() const { return ws + hdr->off_sums; }
+  __device__ __forceinline__ const uint64_t* sums_begin() const {
+    return reinterpret_cast<const uint64_t*>(ws + hdr->off_sums);
+  }
+  __device__ __forceinline__ const uint64_t* sums_end() const {
+    return reinterpret_cast<const uint64_t*>(ws + hdr->off_spill);
   }
   __device__ __forceinline__ int64_t kblock(int, int64_t it, int64_t) const { return it; }
   __device__ __forceinline__ OzTile tile(int64_t t) const {
@@ -938,6 +963,9 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               const uint8_t* asrc = j.a + (s - 1) * j.a_slice + kbx * kOzTileBytes;
               const uint8_t* bsrc = j.b + (g - s - 1) * j.b_slice + kbx * kOzTileBytes;
+              MXM_BOUNDS(in_range(asrc, kOzTileBytes, tiles.a_begin(), tiles.a_end()), status);
+              MXM_BOUNDS(in_range(bsrc, kOzTileBytes, tiles.b_begin(), tiles.b_end()), status);
+              MXM_BOUNDS(j.row0 < j.m && j.col0 < j.n && kbx >= 0 && kbx < j.Kt, status);
               if (whole) {
                 mbar_arrive_expect_tx(&sm.full[stage], 2 * kOzTileBytes);
                 bulk_g2s(sm.a[stage], asrc, kOzTileBytes, &sm.full[stage]);
@@ -1016,6 +1044,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t da = adesc0 + static_cast<uint64_t>(stage) * (kOzTileBytes >> 4);
             const uint64_t db = bdesc0 + static_cast<uint64_t>(stage) * (kOzTileBytes >> 4);
             const uint32_t d = tmem + static_cast<uint32_t>(buf * kBN);
+            MXM_BOUNDS(buf * kBN + j.n_eff <= static_cast<int>(kAccCol) && nmma >= 1 &&
+                           nmma <= kMmaPerStage, status);
 #pragma unroll
             for (int kk = 0; kk < kMmaPerStage; ++kk) {
               // k step kk: atom kk / 4 (16 KiB = +1024), 32 bytes per step inside it (+2)
@@ -1397,6 +1427,10 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       // slot is marked full all the same
       auto load = [&](auto& r, auto buf, uint64_t* full, uint64_t* empty, const uint8_t* src,
                       uint32_t bytes) {
+        MXM_BOUNDS(src == nullptr || (full == sm.a_full
+                                          ? in_range(src, bytes, tiles.a_begin(), tiles.a_end())
+                                          : in_range(src, bytes, tiles.b_begin(), tiles.b_end())),
+                   status);
         if (!mbar_wait_bounded(&empty[r.slot], r.phase ^ 1u, abort_flag, status))
           return false;
         if (src != nullptr) {
@@ -1412,6 +1446,10 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       // last k-block only the atoms its MMAs reach
       auto load_edge = [&](auto& r, auto buf, uint64_t* full, uint64_t* empty,
                            const uint8_t* src, uint32_t row_bytes, int atoms) {
+        MXM_BOUNDS(full == sm.a_full
+                       ? in_range(src, kOzTileBytes, tiles.a_begin(), tiles.a_end())
+                       : in_range(src, kOzTileBytes, tiles.b_begin(), tiles.b_end()),
+                   status);
         if (!mbar_wait_bounded(&empty[r.slot], r.phase ^ 1u, abort_flag, status))
           return false;
         mbar_arrive_expect_tx(&full[r.slot], atoms * row_bytes);
@@ -1544,6 +1582,9 @@ __global__ void __launch_bounds__(kP2Threads, 1)
         const uint64_t da = adesc0 + static_cast<uint64_t>(aslot) * (kTile >> 4);
         const uint64_t db = bdesc0 + static_cast<uint64_t>(bslot) * (kBTile >> 4);
         const uint32_t d = tmem + static_cast<uint32_t>((2 * x + buf) * kBN);
+        MXM_BOUNDS((2 * x + buf) * kBN + kBN <= static_cast<int>(kTmemCols) && aslot < kRingA &&
+                       bslot < kRingB && nmma >= 1 && nmma <= Fmt::kMmas,
+                   status);
         const uint32_t acc0 = cnt > 0 ? 1u : 0u;
 #pragma unroll
         for (int kk = 0; kk < Fmt::kMmas; ++kk)
@@ -1771,6 +1812,9 @@ __global__ void __launch_bounds__(kP2Threads, 1)
         // step are independent straight-line code.  Each thread reads only
         // the sums it wrote itself.
         uint64_t* tsum = j.sums + static_cast<size_t>(half * 64) * kOzTileRows + row_in_tile;
+        MXM_BOUNDS(j.sums >= tiles.sums_begin() &&
+                       j.sums + kOzTileRows * kOzTileRows <= tiles.sums_end(),
+                   status);
         auto fold_pass = [&](auto k0c, auto k1c) {
           constexpr int K0 = decltype(k0c)::value, K1 = decltype(k1c)::value;
           // diagonal 2 (the last) is never in the int64-only phase

@@ -12,6 +12,31 @@
 
 namespace mxm {
 
+// ------------------------------------------------------------ bounds checks
+// The MXM_DEBUG_BOUNDS build (libmxm_debug.so) checks tile coordinates, the
+// sources of bulk copies and tensor-memory column ranges in the kernels; a
+// failed check records kStatusBounds in the device status word (reported by
+// mxm_get_device_status as MXM_ERR_INVALID_ARG) and the kernel goes on.  It
+// never traps.  The release build compiles the checks away.
+#ifdef MXM_DEBUG_BOUNDS
+#define MXM_BOUNDS(cond, status)                          \
+  do {                                                    \
+    if (!(cond)) atomicOr((status), ::mxm::kStatusBounds); \
+  } while (0)
+#else
+#define MXM_BOUNDS(cond, status) \
+  do {                           \
+  } while (0)
+#endif
+
+// Whether [p, p + bytes) lies inside [lo, hi).
+__device__ __forceinline__ bool in_range(const void* p, size_t bytes, const void* lo,
+                                         const void* hi) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p), l = reinterpret_cast<uintptr_t>(lo),
+                  h = reinterpret_cast<uintptr_t>(hi);
+  return a >= l && a + bytes <= h;
+}
+
 // ------------------------------------------------------------ misc
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -99,7 +99,9 @@ class MxmError(RuntimeError):
 
 
 def library_path() -> str:
-    return _build.LIB
+    """libmxm.so, or the bounds-checked build when MXM_DEBUG_BOUNDS=1 is set
+    in the environment (the process loads one or the other)."""
+    return _build.LIB_DEBUG if os.environ.get("MXM_DEBUG_BOUNDS") == "1" else _build.LIB
 
 
 def load(build_if_missing: bool = True):
@@ -107,11 +109,12 @@ def load(build_if_missing: bool = True):
     global _lib
     if _lib is not None:
         return _lib
+    path = library_path()
     if build_if_missing:
         _build.build()
-    if not os.path.exists(_build.LIB):
-        raise RuntimeError(f"libmxm.so not found at {_build.LIB}; run build() first")
-    lib = ctypes.CDLL(_build.LIB)
+    if not os.path.exists(path):
+        raise RuntimeError(f"{os.path.basename(path)} not found at {path}; run build() first")
+    lib = ctypes.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         f = getattr(lib, name)
         f.restype = res
