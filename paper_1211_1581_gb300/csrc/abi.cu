@@ -226,7 +226,8 @@ mxm_status run_gemm(int mode, const double* A, const double* B, double* C, int64
     e = launch_ozaki_scale(A, B, d, rowbits, colbits, status, s);
     profile_mark(ce, 1, s);
     if (e == cudaSuccess)
-      e = launch_ozaki_split(A, B, d, rowbits, colbits, ws + L.aslices, ws + L.bslices, s);
+      e = launch_ozaki_split(A, B, d, rowbits, colbits, ws + L.aslices, ws + L.bslices,
+                             status, s);
     profile_mark(ce, 2, s);
     if (e == cudaSuccess)
       e = launch_ozaki_gemm(ws + L.aslices, ws + L.bslices, rowbits, colbits, C, d,
@@ -242,7 +243,8 @@ mxm_status run_gemm(int mode, const double* A, const double* B, double* C, int64
     e = launch_ozaki_scale(A, B, d, rowbits, colbits, status, s);
     profile_mark(ce, 1, s);
     if (e == cudaSuccess)
-      e = launch_ozaki_split(A, B, d, rowbits, colbits, ws + L.aslices, ws + L.bslices, s);
+      e = launch_ozaki_split(A, B, d, rowbits, colbits, ws + L.aslices, ws + L.bslices,
+                             status, s);
     profile_mark(ce, 2, s);
     if (e == cudaSuccess)
       e = launch_ozaki_gemm(ws + L.aslices, ws + L.bslices, rowbits, colbits, C, d,
@@ -482,7 +484,7 @@ static mxm_status gemm_host_panels(DeviceState* ds, int mode, const double* hA, 
         launch_ozaki_scale(nullptr, dB + j * w * k, db, nullptr, colbits, ds->status, ds->c2) !=
             cudaSuccess ||
         launch_ozaki_split(nullptr, dB + j * w * k, db, nullptr, colbits, nullptr, bplanes,
-                           ds->c2) != cudaSuccess ||
+                           ds->status, ds->c2) != cudaSuccess ||
         cudaEventRecord(eBs[j], ds->c2) != cudaSuccess)
       fail();
   }
@@ -498,7 +500,8 @@ static mxm_status gemm_host_panels(DeviceState* ds, int mode, const double* hA, 
     if (cudaStreamWaitEvent(c, eA[i], 0) != cudaSuccess ||
         launch_ozaki_scale(dA + r0 * k, nullptr, da, rowbits, nullptr, ds->status, c) !=
             cudaSuccess ||
-        launch_ozaki_split(dA + r0 * k, nullptr, da, rowbits, nullptr, aplanes, nullptr, c) !=
+        launch_ozaki_split(dA + r0 * k, nullptr, da, rowbits, nullptr, aplanes, nullptr,
+                           ds->status, c) !=
             cudaSuccess)
       fail();
     for (int64_t j = 0; j < Q && rc == MXM_OK; ++j) {

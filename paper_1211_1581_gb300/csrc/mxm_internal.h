@@ -256,9 +256,12 @@ inline int ozaki_window_stages(int beta, bool rn = false) {
 cudaError_t launch_ozaki_scale(const double* A, const double* B, const OzakiDims& d,
                                uint64_t* rowbits, uint64_t* colbits, int* status,
                                cudaStream_t s);
+// Splits A and B into digit planes.  For bf16 digits with k up to 24576 the
+// row maxima of A are found here too (one pass over A: launch_ozaki_scale then
+// does B only), so rowbits is written and status takes a non-finite A.
 cudaError_t launch_ozaki_split(const double* A, const double* B, const OzakiDims& d,
-                               const uint64_t* rowbits, const uint64_t* colbits,
-                               uint8_t* aslices, uint8_t* bslices, cudaStream_t s);
+                               uint64_t* rowbits, const uint64_t* colbits,
+                               uint8_t* aslices, uint8_t* bslices, int* status, cudaStream_t s);
 cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
                               const uint64_t* rowbits, const uint64_t* colbits, double* C,
                               const OzakiDims& d, uint64_t* sums, int* status, cudaStream_t s);

@@ -113,7 +113,8 @@ extern "C" mxm_status mxm_f64_emul_noalloc(const double* A, const double* B, dou
   // sums and the split-k partials are written before they are read.
   cudaError_t e = launch_ozaki_scale(A, B, d, rowbits, colbits, status, s);
   if (e == cudaSuccess)
-    e = launch_ozaki_split(A, B, d, rowbits, colbits, ws + L.aslices, ws + L.bslices, s);
+    e = launch_ozaki_split(A, B, d, rowbits, colbits, ws + L.aslices, ws + L.bslices,
+                             status, s);
   if (e == cudaSuccess)
     e = launch_ozaki_gemm(ws + L.aslices, ws + L.bslices, rowbits, colbits, C, d,
                             reinterpret_cast<uint64_t*>(ws + L.sums), status, s);

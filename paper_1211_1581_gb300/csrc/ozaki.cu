@@ -402,6 +402,69 @@ __global__ void __launch_bounds__(256) oz_split_a_kernel(
                   static_cast<size_t>(Mt) * Kt * kTile, rn);
 }
 
+// Steps 1 and 2 for A in one pass: one block per row of A (and per padding
+// row of the last tile-row) holds the row in shared memory, zero-padded to
+// whole k-blocks, takes its maximum and writes its digits into every k-block
+// tile from there -- A is read from memory once.  The row's 16-byte chunks of
+// a tile atom fill one 128-byte line (the swizzle permutes chunks inside the
+// row), so the stores stay whole lines.  Padding rows (i >= m) get zero
+// digits and no maximum.
+constexpr int64_t kFusedRowMaxK = 24576;  // k doubles held in shared memory (192 KiB)
+
+__global__ void __launch_bounds__(256) oz_scale_split_a_kernel(
+    const double* __restrict__ A, int64_t m, int64_t k, uint64_t* __restrict__ rowbits, int S,
+    int beta, int64_t Mt, int64_t Kt, uint8_t* __restrict__ aslices, bool rn,
+    int* __restrict__ status) {
+  extern __shared__ double row[];
+  __shared__ uint64_t wmax[32];
+  const int64_t i = blockIdx.x;
+  const int64_t kp = Kt * kOzTileK;
+  const bool real = i < m;
+  const double* a = A + (real ? i : 0) * k;
+  uint64_t mx = 0;
+  for (int64_t l = threadIdx.x; l < kp; l += blockDim.x) {
+    const double v = (real && l < k) ? __ldg(a + l) : 0.0;
+    row[l] = v;
+    const uint64_t b = static_cast<uint64_t>(__double_as_longlong(v)) & kAbsMask;
+    mx = mx > b ? mx : b;
+  }
+  mx = warp_max_u64(mx);
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint64_t w = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0;
+    w = warp_max_u64(w);
+    if (threadIdx.x == 0) {
+      wmax[0] = w;
+      if (real) {
+        rowbits[i] = w;
+        if (w >= kInfBits) atomicOr(status, kStatusNonFinite);
+      }
+    }
+  }
+  __syncthreads();
+  const int e = exponent_from_absbits(wmax[0] < kInfBits ? wmax[0] : 0);
+  const int64_t tm = i / kOzTileRows;
+  const int r = static_cast<int>(i - tm * kOzTileRows);
+  const size_t slice_stride = static_cast<size_t>(Mt) * Kt * kOzTileBytes;
+  uint8_t* base = aslices + static_cast<size_t>(tm) * Kt * kOzTileBytes;
+  for (int64_t p = threadIdx.x; p < Kt * kOzChunksPerRow; p += blockDim.x) {
+    const int64_t tk = p / kOzChunksPerRow;
+    const int c = static_cast<int>(p - tk * kOzChunksPerRow);
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = row[tk * kOzTileK + c * 8 + j];
+    split_chunk(v, e, S, beta, base + tk * kOzTileBytes + oz_chunk_offset(r, c), slice_stride,
+                rn);
+  }
+}
+
+// Whether A's scale and split run fused (bf16 digits, k short enough for a
+// row in shared memory).
+__host__ __device__ inline bool oz_fused_a(const OzakiDims& d) {
+  return !d.fp8 && d.Kt * kOzTileK <= kFusedRowMaxK;
+}
+
 // B -> B_t tiles [S][Nt][Kt]; halves: the CTA-pair layout of each tile.
 template <int V>
 __global__ void __launch_bounds__(256) oz_split_b_kernel(
@@ -1918,7 +1981,8 @@ __global__ void zero_fill_kernel(double* __restrict__ C, int64_t count) {
 cudaError_t launch_ozaki_scale(const double* A, const double* B, const OzakiDims& d,
                                uint64_t* rowbits, uint64_t* colbits, int* status,
                                cudaStream_t s) {
-  if (d.m > 0) {
+  // A's row maxima come with its split (launch_ozaki_split) when fused
+  if (d.m > 0 && !(oz_fused_a(d) && d.Kt > 0)) {
     const int warps = 8;
     const int64_t blocks = (d.m + warps - 1) / warps;
     oz_rowmax_kernel<<<static_cast<unsigned>(blocks), warps * 32, 0, s>>>(A, d.m, d.k, rowbits,
@@ -1938,10 +2002,19 @@ cudaError_t launch_ozaki_scale(const double* A, const double* B, const OzakiDims
 }
 
 cudaError_t launch_ozaki_split(const double* A, const double* B, const OzakiDims& d,
-                               const uint64_t* rowbits, const uint64_t* colbits,
-                               uint8_t* aslices, uint8_t* bslices, cudaStream_t s) {
+                               uint64_t* rowbits, const uint64_t* colbits,
+                               uint8_t* aslices, uint8_t* bslices, int* status,
+                               cudaStream_t s) {
   if (d.Kt == 0) return cudaSuccess;
-  if (d.Mt > 0) {
+  if (d.Mt > 0 && oz_fused_a(d)) {
+    const size_t smem = static_cast<size_t>(d.Kt) * kOzTileK * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(oz_scale_split_a_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    oz_scale_split_a_kernel<<<static_cast<unsigned>(d.Mt * kOzTileRows), 256, smem, s>>>(
+        A, d.m, d.k, rowbits, d.S, d.beta, d.Mt, d.Kt, aslices, d.rn != 0, status);
+  } else if (d.Mt > 0) {
     dim3 grid(static_cast<unsigned>(d.Kt), static_cast<unsigned>(d.Mt));
     if (d.fp8)
       oz_split_a_kernel<16><<<grid, 256, 0, s>>>(A, d.m, d.k, rowbits, d.S, d.beta, d.Mt, d.Kt,
