@@ -1581,7 +1581,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       bool ok = true;
       auto relay = [&](auto& r, uint64_t* full) {
         if (!mbar_wait_bounded(&full[r.slot], r.phase, abort_flag, status)) return false;
-        mbar_arrive_cluster(smem_in_cta(&full[r.slot], 0));
+        mbar_arrive_remote_release(smem_in_cta(&full[r.slot], 0));
         r.advance();
         return true;
       };
@@ -1633,7 +1633,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
         const uint32_t u = buf ? uses1 : uses0;
         const int a = 2 * x + buf;
         if (u > 0 &&
-            !mbar_wait_bounded(&sm.accempty[a], (u - 1u) & 1u, abort_flag, status))
+            !mbar_wait_bounded<false, kPair>(&sm.accempty[a], (u - 1u) & 1u, abort_flag, status))
           return false;
         tc_fence_after();
         if (buf) ++uses1; else ++uses0;
@@ -1671,7 +1671,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
           for (int64_t kb = 0; kb < Kt && ok; ++kb) {
             if constexpr (kEdges)
               nmma = tiles.kblock(q, kb, Kt) == Kt - 1 ? jt.last_mmas : Fmt::kMmas;
-            if (!mbar_wait_bounded(&sm.b_full[rb.slot], rb.phase, abort_flag, status)) {
+            if (!mbar_wait_bounded<false, kPair>(&sm.b_full[rb.slot], rb.phase, abort_flag, status)) {
               ok = false;
               break;
             }
@@ -1679,7 +1679,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
             rb.advance();
             if (x == 1) release(&sm.b_empty[bprev]);
             for (int s = 1; s <= g - 1; ++s) {
-              if (!mbar_wait_bounded(&sm.a_full[ra.slot], ra.phase, abort_flag, status)) {
+              if (!mbar_wait_bounded<false, kPair>(&sm.a_full[ra.slot], ra.phase, abort_flag, status)) {
                 ok = false;
                 break;
               }
@@ -1687,7 +1687,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
               ra.advance();
               int bnew = -1;
               if (s <= g - 2) {
-                if (!mbar_wait_bounded(&sm.b_full[rb.slot], rb.phase, abort_flag,
+                if (!mbar_wait_bounded<false, kPair>(&sm.b_full[rb.slot], rb.phase, abort_flag,
                                               status)) {
                   ok = false;
                   break;
@@ -1788,7 +1788,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       __syncwarp();
       if (lane == 0) {
         if (kPair && !leader)
-          mbar_arrive_cluster(smem_in_cta(&sm.accempty[a], 0));  // the issuers are in rank 0
+          mbar_arrive_remote_release(smem_in_cta(&sm.accempty[a], 0));  // the issuers are in rank 0
         else
           mbar_arrive(&sm.accempty[a]);
       }

@@ -110,15 +110,47 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t pa
   return ok != 0;
 }
 
+// Cluster-scope handshake on an mbarrier the peer CTA arrives on: the peer
+// orders what it has observed with a release fence restricted to its shared
+// memory, then arrives relaxed at cluster scope; the waiter polls relaxed at
+// cluster scope and, once the phase has completed, takes an acquire fence
+// restricted to the cluster's shared memory.
+__device__ __forceinline__ void mbar_arrive_remote_release(uint32_t cluster_addr) {
+  asm volatile("fence.release.sync_restrict::shared::cta.cluster;" ::: "memory");
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait_relaxed_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.relaxed.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void fence_acquire_cluster_shared() {
+  asm volatile("fence.acquire.sync_restrict::shared::cluster.cluster;" ::: "memory");
+}
+
 // Wait until the phase with the given parity has completed.  Returns false
 // (and raises the abort flag and the status bit) after `limit_ns`, or at once
 // if another role of the block has already aborted.  kCluster: cluster-scope
 // acquire (arrivals from the peer CTA of a pair).
-template <bool kCluster = false>
+template <bool kCluster = false, bool kRemote = false>
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   volatile int* abort_flag, int* status,
                                                   uint64_t limit_ns = kWaitLimitNs) {
   auto try_once = [&]() {
+    if (kRemote) {
+      if (!mbar_try_wait_relaxed_cluster(bar, parity)) return false;
+      fence_acquire_cluster_shared();
+      return true;
+    }
     return kCluster ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity);
   };
   if (try_once()) return true;
@@ -162,9 +194,10 @@ __device__ __forceinline__ uint32_t smem_in_cta(const void* p, uint32_t rank) {
 }
 
 // Arrive on an mbarrier given by its shared::cluster address, possibly in
-// the peer CTA (default semantics: release at CTA scope; what the arrival
-// announces is the completion of copies and tensor-memory reads, ordered by
-// the waits and tcgen05 fences around it).
+// the peer CTA, with the default semantics (release at CTA scope).  Used
+// where the arrival carries no data dependency (an issuer giving back a slot
+// it did not read); arrivals that announce data the peer will use go through
+// mbar_arrive_remote_release.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
   asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
