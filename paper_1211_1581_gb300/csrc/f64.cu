@@ -121,11 +121,13 @@ struct F64Single {
   int64_t m, n, Mt, Nt, Kt, splits;
   int64_t raster;
   __device__ __forceinline__ int64_t count() const { return Mt * Nt * splits; }
+#ifdef MXM_DEBUG_BOUNDS
   // the packed operand tiles (bounds checks of the debug build)
   __device__ __forceinline__ const double* a_begin() const { return apack; }
   __device__ __forceinline__ const double* a_end() const { return apack + Mt * Kt * (BM * BK); }
   __device__ __forceinline__ const double* b_begin() const { return bpack; }
   __device__ __forceinline__ const double* b_end() const { return bpack + Nt * Kt * (BN * BK); }
+#endif
   __device__ __forceinline__ F64Tile tile(int64_t t) const {
     const int64_t tile = t / splits, sp = t - tile * splits;
     int64_t tm, tn;

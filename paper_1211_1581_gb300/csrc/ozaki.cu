@@ -752,6 +752,7 @@ struct OzSingle {
   int eoff = 0;                // added to e_i + f_j in the final scaling (2: balanced digits)
   int64_t k = 0;               // the product's k (edge tiles)
   __device__ __forceinline__ long long* spill_area() const { return spill; }
+#ifdef MXM_DEBUG_BOUNDS
   // the digit planes and the running sums (bounds checks of the debug build)
   __device__ __forceinline__ const uint8_t* a_end() const {
     return aslices + static_cast<size_t>(S) * Mt * Kt * tile_bytes;
@@ -766,6 +767,7 @@ struct OzSingle {
     return sums + (splits > 1 ? static_cast<size_t>(splits) * Mt * Nt * S
                               : static_cast<size_t>(Mt) * Nt) * (kOzTileRows * kOzTileRows);
   }
+#endif
   int64_t raster = kDefaultRaster;  // tile-rows (pair-rows) per group of the tile walk
   bool kb_alt = false;         // alternate the k-block direction between diagonal (pair)s
   // Address k-block of the it-th k-block of diagonal (pair) q: every other
@@ -838,6 +840,7 @@ struct OzGrouped {
   __device__ __forceinline__ int64_t count() const {
     return hdr->valid ? (long_k ? hdr->ltiles : hdr->stiles) : 0;
   }
+#ifdef MXM_DEBUG_BOUNDS
   // the digit planes and the running sums (bounds checks of the debug build)
   __device__ __forceinline__ const uint8_t* a_begin() const { return ws + hdr->off_a; }
   __device__ __forceinline__ const uint8_t* a_end() const { return ws + hdr->off_b; }
@@ -849,6 +852,7 @@ struct OzGrouped {
   __device__ __forceinline__ const uint64_t* sums_end() const {
     return reinterpret_cast<const uint64_t*>(ws + hdr->off_spill);
   }
+#endif
   __device__ __forceinline__ int64_t kblock(int, int64_t it, int64_t) const { return it; }
   __device__ __forceinline__ OzTile tile(int64_t t) const {
     int64_t GroupedProblem::*begin = long_k ? &GroupedProblem::ltile_begin
