@@ -671,6 +671,11 @@ constexpr int kEpiWarps = 8;
 constexpr int kBN = 128;            // MMA N (columns of the C tile)
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccCol = 256;   // FP64 running sums: 2 columns per value
+// The window accumulators of the one-diagonal kernel: four slots of 64
+// columns below kAccCol; a window of a tile with more than 64 MMA columns
+// takes two neighbouring slots (0-1 or 2-3), a narrower one a single slot,
+// so narrow tiles get four windows in flight instead of two.
+constexpr int kAccSlotCols = 64;
 constexpr int kMmaK = 16;           // K per tcgen05.mma kind::f16
 constexpr int kMmaPerStage = kOzTileK / kMmaK;
 
@@ -679,8 +684,8 @@ struct __align__(1024) GemmSmem {
   uint8_t b[kStages][kOzTileBytes];
   uint64_t full[kStages];
   uint64_t empty[kStages];
-  uint64_t accfull[2];
-  uint64_t accempty[2];
+  uint64_t accfull[4];   // per 64-column accumulator slot
+  uint64_t accempty[4];
   uint32_t tmem_base;
   int abort_flag;
 };
@@ -986,7 +991,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&sm.full[s], 1);
       mbar_init(&sm.empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < 4; ++b) {
       mbar_init(&sm.accfull[b], 1);
       mbar_init(&sm.accempty[b], kEpiWarps);
     }
@@ -1075,8 +1080,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint64_t bdesc0 = sw128_kmajor_desc(smem_u32(sm.b[0]));
       int stage = 0;
       uint32_t phase = 0;
-      int buf = 0;
-      uint32_t uses0 = 0u, uses1 = 0u;  // windows started in accumulator 0 / 1
+      int sc = 0;            // next accumulator slot (of four of 64 columns)
+      int first = 0;         // the current window's first slot
+      uint32_t uses[4] = {0u, 0u, 0u, 0u};  // windows started in each slot
       bool acquired = false;
       int wcnt = 0;
       bool ok = true;
@@ -1084,6 +1090,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const OzTile j = tiles.tile(t);
         const int64_t Kt = j.Kt;
         const uint32_t idesc = idesc_bf16_f32(128, j.n_eff);
+        const int wslots = j.n_eff > kAccSlotCols ? 2 : 1;  // slots per window
         for (int g = S + 1; g >= 2 && ok; --g) {
           const int64_t nst = Kt * (g - 1);
           int64_t kb = 0;
@@ -1095,14 +1102,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_after();
             if (!acquired) {
-              const uint32_t u = buf ? uses1 : uses0;
-              if (u > 0 &&
-                  !mbar_wait_bounded(&sm.accempty[buf], (u - 1u) & 1u, abort_flag, status)) {
-                ok = false;
-                break;
+              // a window of two slots starts on an even slot
+              if (wslots == 2 && (sc & 1)) sc = (sc + 1) & 3;
+              first = sc;
+              for (int i = 0; i < wslots && ok; ++i) {
+                const uint32_t u = uses[first + i];
+                if (u > 0 && !mbar_wait_bounded(&sm.accempty[first + i], (u - 1u) & 1u,
+                                                 abort_flag, status))
+                  ok = false;
+                ++uses[first + i];
               }
+              if (!ok) break;
+              sc = (sc + wslots) & 3;
               tc_fence_after();
-              if (buf) ++uses1; else ++uses0;
               acquired = true;
               wcnt = 0;
             }
@@ -1110,8 +1122,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tiles.kblock(S + 1 - g, kb, Kt) == Kt - 1 ? j.last_mmas : kMmaPerStage;
             const uint64_t da = adesc0 + static_cast<uint64_t>(stage) * (kOzTileBytes >> 4);
             const uint64_t db = bdesc0 + static_cast<uint64_t>(stage) * (kOzTileBytes >> 4);
-            const uint32_t d = tmem + static_cast<uint32_t>(buf * kBN);
-            MXM_BOUNDS(buf * kBN + j.n_eff <= static_cast<int>(kAccCol) && nmma >= 1 &&
+            const uint32_t d = tmem + static_cast<uint32_t>(first * kAccSlotCols);
+            MXM_BOUNDS(first * kAccSlotCols + j.n_eff <= static_cast<int>(kAccCol) && nmma >= 1 &&
                            nmma <= kMmaPerStage, status);
 #pragma unroll
             for (int kk = 0; kk < kMmaPerStage; ++kk) {
@@ -1123,8 +1135,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_commit(&sm.empty[stage]);
             ++wcnt;
             if (wcnt == window || st + 1 == nst) {
-              mma_commit(&sm.accfull[buf]);
-              buf ^= 1;
+              mma_commit(&sm.accfull[first]);
               acquired = false;
             }
             if (++stage == kStages) {
@@ -1151,8 +1162,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row_in_tile = quarter * 32 + lane;
     const uint32_t t_lane = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
     const uint32_t t_acc = t_lane + kAccCol + static_cast<uint32_t>(half * 128);
-    int buf = 0;
-    uint32_t fulls0 = 0u, fulls1 = 0u;  // windows drained from accumulator 0 / 1
+    int sc = 0;                             // next accumulator slot, as the issuer
+    uint32_t fulls[4] = {0u, 0u, 0u, 0u};   // windows drained that started in each slot
     bool ok = true;
     Acc D[64];
     using FInt = std::integral_constant<int, kFoldInt>;
@@ -1165,20 +1176,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t row = j.row0 + row_in_tile;
       const bool row_ok = row < j.m;
       const int64_t ncols = j.n - j.col0;    // columns of C in this tile (may exceed 128)
+      const int wslots = j.n_eff > kAccSlotCols ? 2 : 1;  // slots per window
       for (int g = S + 1; g >= 2 && ok; --g) {
 #pragma unroll
         for (int i = 0; i < 64; ++i) D[i] = 0;
         const int64_t nst = j.Kt * (g - 1);
         const int64_t nwin = (nst + window - 1) / window;
         for (int64_t w = 0; w < nwin; ++w) {
-          if (!mbar_wait_bounded(&sm.accfull[buf], (buf ? fulls1 : fulls0) & 1u, abort_flag,
-                                 status)) {
+          if (wslots == 2 && (sc & 1)) sc = (sc + 1) & 3;
+          const int first = sc;
+          sc = (sc + wslots) & 3;
+          if (!mbar_wait_bounded(&sm.accfull[first], fulls[first] & 1u, abort_flag, status)) {
             ok = false;
             break;
           }
-          if (buf) ++fulls1; else ++fulls0;
+          ++fulls[first];
           tc_fence_after();
-          const uint32_t t_win = t_lane + static_cast<uint32_t>(buf * kBN + half * 64);
+          const uint32_t t_win =
+              t_lane + static_cast<uint32_t>(first * kAccSlotCols + half * 64);
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             if (!rows_live || half * 64 + h * 32 >= j.n_eff) continue;  // warp-uniform
@@ -1195,8 +1210,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&sm.accempty[buf]);
-          buf ^= 1;
+          if (lane == 0)
+            for (int i = 0; i < wslots; ++i) mbar_arrive(&sm.accempty[first + i]);
         }
         if (!ok) break;
         if (!kFloat && j.partial != nullptr) {
@@ -2196,8 +2211,10 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
 cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t short_kt, int* status,
                                  cudaStream_t s, bool rn) {
   const int sms = sm_count();
-  oz_grouped_prep_a_kernel<<<sms * 4, 256, 0, s>>>(ws, S, beta, rn, status);
-  oz_grouped_prep_b_kernel<<<sms * 4, 256, 0, s>>>(ws, S, beta, rn, status);
+  // many blocks per SM: the passes are latency-bound (a block reads its rows
+  // or columns, then splits tile by tile between block barriers)
+  oz_grouped_prep_a_kernel<<<sms * 16, 256, 0, s>>>(ws, S, beta, rn, status);
+  oz_grouped_prep_b_kernel<<<sms * 16, 256, 0, s>>>(ws, S, beta, rn, status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
