@@ -666,8 +666,8 @@ __global__ void __launch_bounds__(256) bf16_tiles_kernel(const double* __restric
 
 // ---------------------------------------------------------------- steps 3-4
 constexpr int kStages = 3;
-constexpr int kThreads = 384;       // warp 0 copies, warp 1 MMA, warps 4..11 epilogue
-constexpr int kEpiWarps = 8;
+// The slice GEMMs: warp 0 copies, warp 1 issues MMAs, warps 2-3 idle, warps
+// 4.. run the epilogue (8, or 16 in the short-k grouped GEMM).
 constexpr int kBN = 128;            // MMA N (columns of the C tile)
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccCol = 256;   // FP64 running sums: 2 columns per value
@@ -678,19 +678,6 @@ constexpr uint32_t kAccCol = 256;   // FP64 running sums: 2 columns per value
 constexpr int kAccSlotCols = 64;
 constexpr int kMmaK = 16;           // K per tcgen05.mma kind::f16
 constexpr int kMmaPerStage = kOzTileK / kMmaK;
-
-struct __align__(1024) GemmSmem {
-  uint8_t a[kStages][kOzTileBytes];
-  uint8_t b[kStages][kOzTileBytes];
-  uint64_t full[kStages];
-  uint64_t empty[kStages];
-  uint64_t accfull[4];   // per 64-column accumulator slot
-  uint64_t accempty[4];
-  uint32_t tmem_base;
-  int abort_flag;
-};
-
-constexpr size_t kGemmSmemBytes = sizeof(GemmSmem) + 1024;
 
 __device__ __forceinline__ void tile_coords(int64_t tile, int64_t Mt, int64_t Nt, int64_t G,
                                             int64_t& tm, int64_t& tn) {
@@ -729,6 +716,30 @@ struct OzTile {
   int a_rows;
   int last_mmas;
 };
+
+// The one-diagonal kernel's shared memory.  The producer resolves every
+// tile it takes (its place in the digit planes, its edges) once and hands it
+// to the MMA issuer and the epilogue warps through a ring of kTileRing
+// entries: tfull completes when an entry is written, tempty when the issuer
+// and every epilogue warp have copied it.  An entry with tile_live == 0 ends
+// the CTA's work.
+constexpr int kTileRing = 4;
+struct __align__(1024) GemmSmem {
+  uint8_t a[kStages][kOzTileBytes];
+  uint8_t b[kStages][kOzTileBytes];
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t accfull[4];   // per 64-column accumulator slot
+  uint64_t accempty[4];
+  uint64_t tfull[kTileRing];
+  uint64_t tempty[kTileRing];
+  OzTile tiles[kTileRing];
+  int tile_live[kTileRing];
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+constexpr size_t kGemmSmemBytes = sizeof(GemmSmem) + 1024;
 
 // Edge geometry of a tile: rows of A left from row0, columns of B from
 // col0, and whether the unit's k range ends with the product's last k-block.
@@ -782,6 +793,11 @@ struct OzSingle {
     return (kb_alt && (q & 1)) ? Kt_ - 1 - it : it;
   }
   __device__ __forceinline__ int64_t count() const { return Mt * Nt * splits; }
+  // The it-th unit a CTA of the one-diagonal kernel takes: a fixed stride
+  // over the grid (equal units; neighbouring CTAs share operand tiles in L2).
+  __device__ __forceinline__ int64_t claim(int64_t it) const {
+    return static_cast<int64_t>(blockIdx.x) + it * gridDim.x;
+  }
   // Unit t: C tile t / splits, k range t % splits.
   __device__ __forceinline__ OzTile tile(int64_t t) const {
     const int64_t tt = t / splits, sp = t - tt * splits;
@@ -844,6 +860,14 @@ struct OzGrouped {
   }
   __device__ __forceinline__ int64_t count() const {
     return hdr->valid ? (long_k ? hdr->ltiles : hdr->stiles) : 0;
+  }
+  // The next tile for the one-diagonal kernel, from the header's cursor
+  // (zeroed by the plan kernel on every call): tiles differ in k and in their
+  // edges, so CTAs take them as they finish the previous one.
+  __device__ __forceinline__ int64_t claim(int64_t) const {
+    GroupedHeader* h = const_cast<GroupedHeader*>(hdr);
+    return static_cast<int64_t>(
+        atomicAdd(reinterpret_cast<unsigned long long*>(&h->cursor), 1ull));
   }
 #ifdef MXM_DEBUG_BOUNDS
   // the digit planes and the running sums (bounds checks of the debug build)
@@ -964,6 +988,14 @@ __device__ __forceinline__ void regs_dec_80() {
 __device__ __forceinline__ void regs_inc_208() {
   asm volatile("setmaxnreg.inc.sync.aligned.u32 208;" ::: "memory");
 }
+// The 640-thread form (16 epilogue warps): 640 threads x 96 registers at
+// launch = 128 x 64 (warpgroup 0) + 512 x 104 = 61,440, all of them.
+__device__ __forceinline__ void regs_dec_64() {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 64;" ::: "memory");
+}
+__device__ __forceinline__ void regs_inc_104() {
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 104;" ::: "memory");
+}
 
 // Persistent slice GEMM: every CTA walks tiles blockIdx.x, +gridDim.x, ...;
 // the three roles walk the same sequence and keep their pipeline state
@@ -977,9 +1009,16 @@ __device__ __forceinline__ void regs_inc_208() {
 // kFloat (BF16 comparison mode only): one slice of bf16-rounded values, the
 // FP32 accumulator covers all of k in one window and is converted to FP64
 // without scaling.
-template <typename Acc, bool kFloat, typename Tiles>
-__global__ void __launch_bounds__(kThreads, 1)
+//
+// kEpiW: epilogue warps, 8 (each of 64 columns of the tile) or 16 (each of 32
+// columns; 32-bit digit sums only): with 16 the folds, which wait on tensor
+// memory round trips, run on twice as many warps.
+template <typename Acc, bool kFloat, typename Tiles, int kEpiW = 8>
+__global__ void __launch_bounds__(128 + 32 * kEpiW, 1)
     oz_gemm_kernel(const Tiles tiles, int S, int beta, int window, int* __restrict__ status) {
+  static_assert(kEpiW == 8 || (kEpiW == 16 && sizeof(Acc) == 4 && !kFloat),
+                "16 epilogue warps need 32-bit digit sums");
+  constexpr int kCPW = kOzTileRows / (kEpiW / 4);  // tile columns per epilogue warp
   extern __shared__ uint8_t smem_raw[];
   GemmSmem& sm = *reinterpret_cast<GemmSmem*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -993,7 +1032,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 4; ++b) {
       mbar_init(&sm.accfull[b], 1);
-      mbar_init(&sm.accempty[b], kEpiWarps);
+      mbar_init(&sm.accempty[b], kEpiW);
+    }
+    for (int b = 0; b < kTileRing; ++b) {
+      mbar_init(&sm.tfull[b], 1);
+      mbar_init(&sm.tempty[b], 1 + kEpiW);
     }
     sm.abort_flag = 0;
     fence_mbar_init();
@@ -1009,7 +1052,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = &sm.abort_flag;
   const int64_t ntiles = tiles.count();
 
-  if (warp < 4) regs_dec_80();  // warps 2, 3 idle
+  if (warp < 4) {  // warps 2, 3 idle
+    if constexpr (kEpiW == 8) regs_dec_80(); else regs_dec_64();
+  }
   if (warp == 0) {
     // ------------------------------------------------ producer (bulk copies)
     // Full tiles move as one 32 KiB copy per operand; edge tiles copy the
@@ -1019,8 +1064,29 @@ __global__ void __launch_bounds__(kThreads, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const OzTile j = tiles.tile(t);
+      // Publish the it-th tile of this CTA in the ring: 1 a tile, 0 the end
+      // of the work, -1 a wait that gave up.  Tile it + 1 is published
+      // before the copies of tile it are issued, so that its lookup (a
+      // search of the problem table in a grouped call) is off the MMA
+      // issuer's path.
+      auto publish = [&](int64_t it) -> int {
+        const int64_t t = tiles.claim(it);
+        const int ts = static_cast<int>(it % kTileRing);
+        if (!mbar_wait_bounded(&sm.tempty[ts], (static_cast<uint32_t>(it / kTileRing) & 1u) ^ 1u,
+                               abort_flag, status))
+          return -1;
+        const bool live = t < ntiles;
+        if (live) sm.tiles[ts] = tiles.tile(t);
+        sm.tile_live[ts] = live ? 1 : 0;
+        mbar_arrive(&sm.tfull[ts]);  // release: the entry is visible to its waiters
+        return live ? 1 : 0;
+      };
+      int next = publish(0);
+      for (int64_t it = 0; ok && next == 1; ++it) {
+        next = publish(it + 1);
+        if (next < 0) break;
+        // the entry stays in place until tile it + kTileRing is published
+        const OzTile& j = sm.tiles[it % kTileRing];
         const uint32_t arow_bytes = static_cast<uint32_t>(j.a_rows) * 128u;
         const uint32_t brow_bytes = static_cast<uint32_t>(j.n_eff) * 128u;
         for (int g = S + 1; g >= 2 && ok; --g) {
@@ -1086,8 +1152,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool acquired = false;
       int wcnt = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const OzTile j = tiles.tile(t);
+      for (int64_t it = 0; ok; ++it) {
+        const int ts = static_cast<int>(it % kTileRing);
+        if (!mbar_wait_bounded(&sm.tfull[ts], static_cast<uint32_t>(it / kTileRing) & 1u,
+                               abort_flag, status))
+          break;
+        if (!sm.tile_live[ts]) break;
+        const OzTile j = sm.tiles[ts];
+        mbar_arrive(&sm.tempty[ts]);
         const int64_t Kt = j.Kt;
         const uint32_t idesc = idesc_bf16_f32(128, j.n_eff);
         const int wslots = j.n_eff > kAccSlotCols ? 2 : 1;  // slots per window
@@ -1151,26 +1223,33 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (warp >= 4) {
-    // ------------------------------------------------ epilogue (8 warps)
+    // ------------------------------------------------ epilogue (kEpiW warps)
     // A warp whose 32 rows all lie past the tile's last row, and a group of
     // columns past its last column, skip their tensor-memory reads and their
     // share of the fold (the running sums there are never stored).
-    regs_inc_208();
+    if constexpr (kEpiW == 8) regs_inc_208(); else regs_inc_104();
     const int ew = warp - 4;
     const int quarter = warp & 3;          // TMEM lanes this warp may access
-    const int half = ew >> 2;              // which 64 columns of the tile
+    const int cg = ew >> 2;                // which kCPW columns of the tile
     const int row_in_tile = quarter * 32 + lane;
     const uint32_t t_lane = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
-    const uint32_t t_acc = t_lane + kAccCol + static_cast<uint32_t>(half * 128);
+    const uint32_t t_acc = t_lane + kAccCol + static_cast<uint32_t>(cg * 2 * kCPW);
     int sc = 0;                             // next accumulator slot, as the issuer
     uint32_t fulls[4] = {0u, 0u, 0u, 0u};   // windows drained that started in each slot
     bool ok = true;
-    Acc D[64];
+    Acc D[kCPW];
     using FInt = std::integral_constant<int, kFoldInt>;
     using FConv = std::integral_constant<int, kFoldConv>;
     using FFp = std::integral_constant<int, kFoldFp>;
-    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const OzTile j = tiles.tile(t);
+    for (int64_t it = 0; ok; ++it) {
+      const int ts = static_cast<int>(it % kTileRing);
+      if (!mbar_wait_bounded(&sm.tfull[ts], static_cast<uint32_t>(it / kTileRing) & 1u,
+                             abort_flag, status))
+        break;
+      if (!sm.tile_live[ts]) break;
+      const OzTile j = sm.tiles[ts];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.tempty[ts]);
       const int gx = oz_exact_from(S, beta, j.Kt);
       const bool rows_live = j.row0 + quarter * 32 < j.m;
       const int64_t row = j.row0 + row_in_tile;
@@ -1179,7 +1258,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int wslots = j.n_eff > kAccSlotCols ? 2 : 1;  // slots per window
       for (int g = S + 1; g >= 2 && ok; --g) {
 #pragma unroll
-        for (int i = 0; i < 64; ++i) D[i] = 0;
+        for (int i = 0; i < kCPW; ++i) D[i] = 0;
         const int64_t nst = j.Kt * (g - 1);
         const int64_t nwin = (nst + window - 1) / window;
         for (int64_t w = 0; w < nwin; ++w) {
@@ -1193,10 +1272,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++fulls[first];
           tc_fence_after();
           const uint32_t t_win =
-              t_lane + static_cast<uint32_t>(first * kAccSlotCols + half * 64);
+              t_lane + static_cast<uint32_t>(first * kAccSlotCols + cg * kCPW);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            if (!rows_live || half * 64 + h * 32 >= j.n_eff) continue;  // warp-uniform
+          for (int h = 0; h < kCPW / 32; ++h) {
+            if (!rows_live || cg * kCPW + h * 32 >= j.n_eff) continue;  // warp-uniform
             uint32_t r[32];
             tmem_ld32(t_win + h * 32, r);
             tmem_wait_ld();
@@ -1219,10 +1298,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           // warp's 32 lanes store 256 contiguous bytes per column)
           if (!rows_live) continue;
           uint64_t* p = j.partial + static_cast<size_t>(g - 2) * (kOzTileRows * kOzTileRows) +
-                        static_cast<size_t>(half * 64) * kOzTileRows + row_in_tile;
+                        static_cast<size_t>(cg * kCPW) * kOzTileRows + row_in_tile;
 #pragma unroll
-          for (int i = 0; i < 64; ++i)
-            if (half * 64 + i < ncols)
+          for (int i = 0; i < kCPW; ++i)
+            if (cg * kCPW + i < ncols)
               __stcg(reinterpret_cast<unsigned long long*>(p + i * kOzTileRows),
                      static_cast<unsigned long long>(static_cast<long long>(D[i])));
           continue;
@@ -1232,19 +1311,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool last = (g == 2);
         int er = 0;
         if (!kFloat && last && row_ok) er = exponent_from_absbits(j.rowbits[row]);
-        // E columns per step of a rolled loop (8 with 64-bit digit sums, 32
-        // with 32-bit ones: one tensor-memory round trip per 32 running sums
-        // instead of four); D is rotated down by E after each step so the
+        // E columns per step of a rolled loop (8 with 64-bit digit sums or
+        // with 16 epilogue warps, 32 with 32-bit ones and 8 warps: one
+        // tensor-memory round trip per 32 running sums instead of four); D is
+        // rotated down by E after each step so the
         // body only names D[0..E-1] (compact code).  The kind of the fold
         // step (int64 partial, the conversion to FP64, an FP64 addition) is
         // fixed per diagonal, so the E elements of a step are straight-line
         // code.
         auto fold_pass = [&](auto kc) {
           [[maybe_unused]] constexpr int K = decltype(kc)::value;
-          constexpr int E = (sizeof(Acc) == 4 && !kFloat) ? 32 : 8;
+          constexpr int E = (sizeof(Acc) == 4 && !kFloat && kEpiW == 8) ? 32 : 8;
 #pragma unroll 1
-          for (int ch = 0; ch < 64 / E; ++ch) {
-            if (half * 64 + ch * E < ncols) {  // warp-uniform
+          for (int ch = 0; ch < kCPW / E; ++ch) {
+            if (cg * kCPW + ch * E < ncols) {  // warp-uniform
               uint32_t r[2 * E];
               if (!first) {
                 if constexpr (E == 32) {
@@ -1268,7 +1348,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               if (last) {
                 if (row_ok) {
-                  const int64_t col0 = j.col0 + half * 64 + ch * E;
+                  const int64_t col0 = j.col0 + cg * kCPW + ch * E;
                   double* crow = j.C + row * j.n;
 #pragma unroll
                   for (int i = 0; i < E; ++i) {
@@ -1299,7 +1379,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             }
 #pragma unroll
-            for (int i = 0; i < 64 - E; ++i) D[i] = D[i + E];
+            for (int i = 0; i < kCPW - E; ++i) D[i] = D[i + E];
           }
         };
         if constexpr (kFloat) {
@@ -2066,16 +2146,16 @@ int sm_count() {
   return g_sm_count;
 }
 
-template <typename Acc, bool kFloat, typename Tiles>
+template <typename Acc, bool kFloat, typename Tiles, int kEpiW = 8>
 static cudaError_t launch_oz_gemm_t(const Tiles& tiles, int64_t grid, int S, int beta,
                                     int window, int* status, cudaStream_t s) {
   if (grid <= 0) return cudaSuccess;
-  auto kern = oz_gemm_kernel<Acc, kFloat, Tiles>;
+  auto kern = oz_gemm_kernel<Acc, kFloat, Tiles, kEpiW>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(kGemmSmemBytes));
   if (e != cudaSuccess) return e;
-  kern<<<static_cast<unsigned>(grid), kThreads, kGemmSmemBytes, s>>>(tiles, S, beta, window,
-                                                                      status);
+  kern<<<static_cast<unsigned>(grid), 128 + 32 * kEpiW, kGemmSmemBytes, s>>>(tiles, S, beta,
+                                                                              window, status);
   return cudaGetLastError();
 }
 
@@ -2242,7 +2322,7 @@ cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t short_kt,
   OzGrouped st{hdr, recs, ws, rn ? 2 : 0, false};
   const double dsum = static_cast<double>(S) * dmax * dmax * kOzTileK;
   if (dsum * static_cast<double>(short_kt) < 2147483647.0)  // every short tile's sums fit int32
-    return launch_oz_gemm_t<int, false>(st, sms, S, beta, window, status, s);
+    return launch_oz_gemm_t<int, false, OzGrouped, 16>(st, sms, S, beta, window, status, s);
   return launch_oz_gemm_t<long long, false>(st, sms, S, beta, window, status, s);
 }
 
