@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kPlanThreads) grouped_plan_kernel(
   if (threadIdx.x < kCounts) carry[threadIdx.x] = 0;
   if (threadIdx.x == 0) {
     max_kt = 0;
-    bad = 0;
+    bad = (bits && count > 2147483647) ? 1 : 0;  // the owner map holds int32 problem indices
   }
   __syncthreads();
   for (int64_t base = 0; base < count; base += kPlanThreads) {
@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(kPlanThreads) grouped_plan_kernel(
     h.stiles = carry[8];
     h.max_kt = max_kt;
     h.cursor = 0;
+    h.cursor_max = 0;
     grouped_offsets(h, planes, tile_bytes, bits != 0);
     h.valid = (h.total <= ws_bytes && !bad) ? 1 : 0;
     if (!h.valid) atomicOr(status, bad ? kStatusBounds : kStatusWorkspace);

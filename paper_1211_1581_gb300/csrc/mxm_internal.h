@@ -334,9 +334,13 @@ struct GroupedHeader {
   int64_t cursor;          // next work unit of a dynamically scheduled kernel (zeroed by
                            // the plan kernel on every call)
   int64_t off_sums, off_spill;  // emulated: running sums of every C tile, spill areas
+  int64_t cursor_max;      // next unit of the emulated maxima pass (zeroed like cursor)
+  int64_t off_owner;       // emulated: the problem (int32) owning each A tile, B tile,
+                           // short-k C tile and long-k C tile, in that order
 };
 
 constexpr size_t kGroupedRecordsOff = 256;
+static_assert(sizeof(GroupedHeader) <= kGroupedRecordsOff, "the header precedes the records");
 
 __host__ __device__ inline size_t grouped_data_begin(int64_t count) {
   return align_up(kGroupedRecordsOff + sizeof(GroupedProblem) * static_cast<size_t>(count), 1024);
@@ -362,6 +366,10 @@ __host__ __device__ inline void grouped_offsets(GroupedHeader& h, int planes, si
   h.off_spill = off;
   if (bits) off = align_up(off + static_cast<size_t>(kOzSpillCtas) * 2 * kOzTileRows * kOzTileRows * 8,
                            1024);
+  h.off_owner = off;
+  if (bits)
+    off = align_up(off + 4 * static_cast<size_t>(h.atiles + h.btiles + h.stiles + h.ltiles + 1),
+                   1024);
   h.total = off;
 }
 

@@ -43,41 +43,59 @@ namespace {
 constexpr uint64_t kAbsMask = 0x7FFFFFFFFFFFFFFFull;
 constexpr uint64_t kInfBits = 0x7FF0000000000000ull;
 
-__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    uint64_t w = __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    v = w > v ? w : v;
-  }
-  return v;
+// ---------------------------------------------------------------- step 1
+// The maxima keep what the split and the final scaling read of max |x|: its
+// exponent (exponent_from_absbits) and whether it is inf or NaN.  Ordering
+// non-negative doubles equals ordering their bit patterns (NaN patterns sort
+// above +inf), and the high word of |x| (exponent field, top 20 mantissa
+// bits) fixes both properties unless every high word is zero (all
+// |x| < 2^-1042), when the low words give the exponent.  So the maxima run
+// on 32-bit high words (an integer max; the 64-bit form runs on the FP64
+// pipe, the slowest of this GPU), a second pass over the low words covers
+// the rows or columns whose high words are all zero, and the stored pattern
+// is max_bits(hi, lo): hi 2^32, or lo when hi = 0 -- the exponent of the true
+// maximum, and >= kInfBits exactly when the true maximum is.
+__device__ __forceinline__ uint32_t abs_hi(double x) {
+  return static_cast<uint32_t>(__double2hiint(x)) & 0x7FFFFFFFu;
+}
+__device__ __forceinline__ uint32_t lo_word(double x) {
+  return static_cast<uint32_t>(__double2loint(x));
+}
+__device__ __forceinline__ uint64_t max_bits(uint32_t hi, uint32_t lo) {
+  return hi ? (static_cast<uint64_t>(hi) << 32) : static_cast<uint64_t>(lo);
+}
+__device__ __forceinline__ uint32_t warp_max_u32(uint32_t v) {
+  return __reduce_max_sync(0xFFFFFFFFu, v);
 }
 
-// ---------------------------------------------------------------- step 1
-// max_l |a_il| as a bit pattern (ordering of non-negative doubles equals the
-// ordering of their bit patterns; NaN patterns sort above +inf).
+// Maximum of one row of k values (a warp; lanes stride the row): max_bits.
+__device__ __forceinline__ uint64_t warp_row_max(const double* __restrict__ a, int64_t k,
+                                                 int lane) {
+  uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+  int64_t l = lane;
+  for (; l + 96 < k; l += 128) {
+    m0 = max(m0, abs_hi(__ldg(a + l)));
+    m1 = max(m1, abs_hi(__ldg(a + l + 32)));
+    m2 = max(m2, abs_hi(__ldg(a + l + 64)));
+    m3 = max(m3, abs_hi(__ldg(a + l + 96)));
+  }
+  for (; l < k; l += 32) m0 = max(m0, abs_hi(__ldg(a + l)));
+  const uint32_t hi = warp_max_u32(max(max(m0, m1), max(m2, m3)));
+  uint32_t lo = 0;
+  if (hi == 0) {  // warp-uniform
+    for (l = lane; l < k; l += 32) lo = max(lo, lo_word(__ldg(a + l)));
+    lo = warp_max_u32(lo);
+  }
+  return max_bits(hi, lo);
+}
+
+// max_l |a_il| per row, a warp per row.
 __global__ void oz_rowmax_kernel(const double* __restrict__ A, int64_t m, int64_t k,
                                  uint64_t* __restrict__ rowbits, int* __restrict__ status) {
   const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= m) return;
   const int lane = threadIdx.x & 31;
-  const double* a = A + row * k;
-  uint64_t mx = 0;
-  int64_t l = lane;
-  for (; l + 96 < k; l += 128) {
-    uint64_t b0 = static_cast<uint64_t>(__double_as_longlong(__ldg(a + l))) & kAbsMask;
-    uint64_t b1 = static_cast<uint64_t>(__double_as_longlong(__ldg(a + l + 32))) & kAbsMask;
-    uint64_t b2 = static_cast<uint64_t>(__double_as_longlong(__ldg(a + l + 64))) & kAbsMask;
-    uint64_t b3 = static_cast<uint64_t>(__double_as_longlong(__ldg(a + l + 96))) & kAbsMask;
-    b0 = b0 > b1 ? b0 : b1;
-    b2 = b2 > b3 ? b2 : b3;
-    b0 = b0 > b2 ? b0 : b2;
-    mx = mx > b0 ? mx : b0;
-  }
-  for (; l < k; l += 32) {
-    uint64_t b = static_cast<uint64_t>(__double_as_longlong(__ldg(a + l))) & kAbsMask;
-    mx = mx > b ? mx : b;
-  }
-  mx = warp_max_u64(mx);
+  const uint64_t mx = warp_row_max(A + row * k, k, lane);
   if (lane == 0) {
     rowbits[row] = mx;
     if (mx >= kInfBits) atomicOr(status, kStatusNonFinite);
@@ -90,23 +108,24 @@ constexpr int kColRowsPerBlock = 256;
 __global__ void oz_colmax_kernel(const double* __restrict__ B, int64_t k, int64_t n,
                                  unsigned long long* __restrict__ colbits,
                                  int* __restrict__ status) {
-  __shared__ uint64_t red[8][32];
+  __shared__ uint32_t red[8][32];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t col = static_cast<int64_t>(blockIdx.x) * 32 + tx;
   const int64_t l0 = static_cast<int64_t>(blockIdx.y) * kColRowsPerBlock;
   const int64_t l1 = l0 + kColRowsPerBlock < k ? l0 + kColRowsPerBlock : k;
-  uint64_t mx = 0;
-  if (col < n) {
-    for (int64_t l = l0 + ty; l < l1; l += 8) {
-      uint64_t b = static_cast<uint64_t>(__double_as_longlong(__ldg(B + l * n + col))) & kAbsMask;
-      mx = mx > b ? mx : b;
-    }
-  }
-  red[ty][tx] = mx;
+  uint32_t mh = 0;
+  if (col < n)
+    for (int64_t l = l0 + ty; l < l1; l += 8) mh = max(mh, abs_hi(__ldg(B + l * n + col)));
+  red[ty][tx] = mh;
   __syncthreads();
   if (ty == 0 && col < n) {
 #pragma unroll
-    for (int y = 1; y < 8; ++y) mx = mx > red[y][tx] ? mx : red[y][tx];
+    for (int y = 1; y < 8; ++y) mh = max(mh, red[y][tx]);
+    uint32_t lo = 0;
+    if (mh == 0)  // every high word of this block's rows is zero
+      for (int64_t l = l0; l < l1; ++l) lo = max(lo, lo_word(__ldg(B + l * n + col)));
+    // the block maxima of a column meet in the same form: hi 2^32 beats any lo
+    const uint64_t mx = max_bits(mh, lo);
     atomicMax(colbits + col, static_cast<unsigned long long>(mx));
     if (mx >= kInfBits) atomicOr(status, kStatusNonFinite);
   }
@@ -173,17 +192,28 @@ __device__ __forceinline__ void split_chunk_store(const double (&x)[8], int e, i
 
 // The same for beta * S <= 64: the fraction |x| 2^-e is first put in one
 // 64-bit fixed-point word F = floor(|x| 2^{beta S - e}) (one shift), then
-// digit s is the field F >> beta (S - s) (a shift uniform over the warp).
-// V values per 16-byte chunk: V = 8 bf16 digits (the bf16 pattern is the
-// upper half of the FP32 pattern of the integer, exact: at most 8
-// significant bits), or V = 16 E4M3 digits (|d| <= 15, from a 16-entry
-// table of the E4M3 codes of 0..15).
+// digit s is the field F >> beta (S - s) (a shift uniform over the warp, of
+// the high word or a funnel shift of both).  V values per 16-byte chunk:
+// V = 8 bf16 digits, or V = 16 E4M3 digits (|d| <= 15, from a 16-entry table
+// of the E4M3 codes of 0..15).
+//
+// A bf16 digit is the upper half of the FP32 pattern of the integer +-mag
+// (exact: at most 8 significant bits), made without a conversion
+// instruction: the pattern of 2^23 + mag (mag in the low mantissa bits of
+// 2^23, with the sign of x) plus -+2^23 is exactly +-mag, and +0 for mag = 0
+// (x + (-x) rounds to +0).
+__device__ __forceinline__ uint32_t bf16_pair(uint32_t q0, uint32_t q1, uint32_t a0,
+                                              uint32_t a1) {
+  const float f0 = __uint_as_float(q0) + __uint_as_float(a0);
+  const float f1 = __uint_as_float(q1) + __uint_as_float(a1);
+  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);  // the upper halves
+}
+
 template <int V>
 __device__ __forceinline__ void split_chunk_store_w64(const double (&x)[V], int e, int S,
                                                       int beta, uint8_t* dst,
                                                       size_t slice_stride) {
-  uint64_t F[V];
-  uint32_t sg[V];
+  uint32_t Fh[V], Fl[V], mg[V];
 #pragma unroll
   for (int j = 0; j < V; ++j) {
     const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x[j]));
@@ -191,25 +221,24 @@ __device__ __forceinline__ void split_chunk_store_w64(const double (&x)[V], int 
     const uint64_t mant = b & 0x000FFFFFFFFFFFFFull;
     const uint64_t M = be ? (mant | 0x0010000000000000ull) : mant;
     const int sh = (be ? be - 1075 : -1074) - e + beta * S;
-    F[j] = sh >= 0 ? (sh < 64 ? M << sh : 0ull) : (-sh < 64 ? M >> -sh : 0ull);
-    sg[j] = static_cast<uint32_t>(b >> 63);
+    const uint64_t F = sh >= 0 ? (sh < 64 ? M << sh : 0ull) : (-sh < 64 ? M >> -sh : 0ull);
+    Fh[j] = static_cast<uint32_t>(F >> 32);
+    Fl[j] = static_cast<uint32_t>(F);
+    mg[j] = V == 8 ? (0x4B000000u | (static_cast<uint32_t>(b >> 63) << 31))  // +-2^23
+                   : static_cast<uint32_t>(b >> 63);
   }
   const uint32_t mask = (1u << beta) - 1u;
   for (int s = 1; s <= S; ++s) {
     const int p = beta * (S - s);
+    auto field = [&](int j) -> uint32_t {
+      return (p >= 32 ? (Fh[j] >> (p - 32)) : __funnelshift_r(Fl[j], Fh[j], p)) & mask;
+    };
     uint32_t packed[4];
     if constexpr (V == 8) {
 #pragma unroll
-      for (int j = 0; j < 8; j += 2) {
-        uint32_t bits2[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t mag = static_cast<uint32_t>(F[j + h] >> p) & mask;
-          const uint32_t hi = __float_as_uint(__uint2float_rn(mag)) >> 16;
-          bits2[h] = mag ? (hi | (sg[j + h] << 15)) : 0u;
-        }
-        packed[j >> 1] = bits2[0] | (bits2[1] << 16);
-      }
+      for (int j = 0; j < 8; j += 2)
+        packed[j >> 1] = bf16_pair(field(j) | mg[j], field(j + 1) | mg[j + 1],
+                                   mg[j] ^ 0x80000000u, mg[j + 1] ^ 0x80000000u);
     } else {
       // E4M3 codes of 0..7 and 8..15, one byte each
       constexpr uint64_t kLo = 0x4E4C4A4844403800ull, kHi = 0x5756555453525150ull;
@@ -219,10 +248,10 @@ __device__ __forceinline__ void split_chunk_store_w64(const double (&x)[V], int 
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
           const int j = 4 * w + h;
-          const uint32_t mag = static_cast<uint32_t>(F[j] >> p) & mask;
+          const uint32_t mag = field(j);
           const uint64_t tbl = mag < 8 ? kLo : kHi;
           uint32_t code = static_cast<uint32_t>(tbl >> (8 * (mag & 7))) & 0xFFu;
-          if (mag) code |= sg[j] << 7;
+          if (mag) code |= mg[j] << 7;
           word |= code << (8 * h);
         }
         packed[w] = word;
@@ -266,19 +295,23 @@ __device__ __forceinline__ void split_chunk_store_rn8(const double (&x)[8], int 
     const long long V = (b >> 63) ? -static_cast<long long>(q) : static_cast<long long>(q);
     W[j] = V + Boff;
   }
+  // digit dg (|dg| <= 128) as an exact float without a conversion
+  // instruction: the pattern of 1.5 2^23 + dg minus 1.5 2^23 (+0 for dg = 0)
+  constexpr uint32_t kMagic = 0x4B400000u;  // 1.5 2^23 = 12582912
+  const uint32_t kNegMagic = 0xCB400000u;
   for (int s = 1; s <= S; ++s) {
     const int p = 8 * (S - s);
     uint32_t packed[4];
 #pragma unroll
     for (int j = 0; j < 8; j += 2) {
-      uint32_t bits2[2];
+      uint32_t q[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int dg = s == 1 ? static_cast<int>(W[j + h] >> p)
                               : static_cast<int>((W[j + h] >> p) & 255) - 128;
-        bits2[h] = dg ? (__float_as_uint(__int2float_rn(dg)) >> 16) : 0u;
+        q[h] = kMagic + static_cast<uint32_t>(dg);
       }
-      packed[j >> 1] = bits2[0] | (bits2[1] << 16);
+      packed[j >> 1] = bf16_pair(q[0], q[1], kNegMagic, kNegMagic);
     }
     *reinterpret_cast<uint4*>(dst + static_cast<size_t>(s - 1) * slice_stride) =
         make_uint4(packed[0], packed[1], packed[2], packed[3]);
@@ -416,34 +449,40 @@ __global__ void __launch_bounds__(256) oz_scale_split_a_kernel(
     int beta, int64_t Mt, int64_t Kt, uint8_t* __restrict__ aslices, bool rn,
     int* __restrict__ status) {
   extern __shared__ double row[];
-  __shared__ uint64_t wmax[32];
+  __shared__ uint32_t wmax[32];
+  __shared__ uint64_t rmax;
   const int64_t i = blockIdx.x;
   const int64_t kp = Kt * kOzTileK;
   const bool real = i < m;
   const double* a = A + (real ? i : 0) * k;
-  uint64_t mx = 0;
+  uint32_t mh = 0;
   for (int64_t l = threadIdx.x; l < kp; l += blockDim.x) {
     const double v = (real && l < k) ? __ldg(a + l) : 0.0;
     row[l] = v;
-    const uint64_t b = static_cast<uint64_t>(__double_as_longlong(v)) & kAbsMask;
-    mx = mx > b ? mx : b;
+    mh = max(mh, abs_hi(v));
   }
-  mx = warp_max_u64(mx);
-  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+  mh = warp_max_u32(mh);
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mh;
   __syncthreads();
   if (threadIdx.x < 32) {
-    uint64_t w = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0;
-    w = warp_max_u64(w);
+    uint32_t w = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0;
+    w = warp_max_u32(w);
+    uint32_t lo = 0;
+    if (w == 0) {  // every high word is zero: the low words (row in shared memory)
+      for (int64_t l = threadIdx.x; l < kp; l += 32) lo = max(lo, lo_word(row[l]));
+      lo = warp_max_u32(lo);
+    }
     if (threadIdx.x == 0) {
-      wmax[0] = w;
+      const uint64_t mx = max_bits(w, lo);
+      rmax = mx;
       if (real) {
-        rowbits[i] = w;
-        if (w >= kInfBits) atomicOr(status, kStatusNonFinite);
+        rowbits[i] = mx;
+        if (mx >= kInfBits) atomicOr(status, kStatusNonFinite);
       }
     }
   }
   __syncthreads();
-  const int e = exponent_from_absbits(wmax[0] < kInfBits ? wmax[0] : 0);
+  const int e = exponent_from_absbits(rmax < kInfBits ? rmax : 0);
   const int64_t tm = i / kOzTileRows;
   const int r = static_cast<int>(i - tm * kOzTileRows);
   const size_t slice_stride = static_cast<size_t>(Mt) * Kt * kOzTileBytes;
@@ -480,14 +519,15 @@ __global__ void __launch_bounds__(256) oz_split_b_kernel(
 }
 
 // ---------------------------------------------------------------- grouped steps 1-2
-// The scale and the split of a grouped call, fused per operand tile-row: one
-// block takes the 128 rows of one A tile-row (or the 128 columns of one B
-// tile-column) of one problem, finds their maxima, then writes their digit
-// tiles for every k-block, re-reading the operand from L2.  Only what the
-// edge-tile copies of the slice GEMM read is written: rows up to the tile's
-// rows rounded up to 8 (A) or columns up to 16 (B, the MMA's N step), and
-// in the last k-block the 16-byte chunks up to k rounded up to 16 (with
-// zeros past k).
+// The scale and the split of a grouped call, in two passes over the operands.
+// oz_grouped_max_kernel (step 1) takes units of 32 rows of A or 32 columns
+// of B of one problem, their cost following k, from a cursor in the plan's
+// header (zeroed by the plan kernel on every call).  oz_grouped_split_kernel
+// (step 2) takes the 128 x 128 operand tiles, A's then B's, in equal
+// contiguous runs per block.  Only what the edge-tile copies of the slice
+// GEMM read is written: rows up to the tile's rows rounded up to 8 (A) or
+// columns up to 16 (B, the MMA's N step), and in the last k-block the
+// 16-byte chunks up to k rounded up to 16 (with zeros past k).
 
 // Chunks of 8 k written in k-block tk of a problem with Kt k-blocks.
 __device__ __forceinline__ int grouped_chunk_lim(int64_t k, int64_t Kt, int64_t tk) {
@@ -496,114 +536,135 @@ __device__ __forceinline__ int grouped_chunk_lim(int64_t k, int64_t Kt, int64_t 
   return static_cast<int>((klast + 15) / 16 * 2);
 }
 
-__global__ void __launch_bounds__(256) oz_grouped_prep_a_kernel(uint8_t* __restrict__ ws, int S,
-                                                                int beta, bool rn,
-                                                                int* __restrict__ status) {
-  const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
+constexpr int kMaxUnit = 32;  // rows of A or columns of B per unit of the maxima pass
+
+__global__ void __launch_bounds__(256) oz_grouped_max_kernel(uint8_t* __restrict__ ws,
+                                                             int* __restrict__ status) {
+  GroupedHeader* hdr = reinterpret_cast<GroupedHeader*>(ws);
   if (!hdr->valid) return;
   const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
   uint64_t* rowbits = reinterpret_cast<uint64_t*>(ws + hdr->off_rowbits);
+  uint64_t* colbits = reinterpret_cast<uint64_t*>(ws + hdr->off_colbits);
+  unsigned long long* cursor = reinterpret_cast<unsigned long long*>(&hdr->cursor_max);
+  constexpr int kPer = kOzTileRows / kMaxUnit;  // units per tile-row (tile-column)
+  const int64_t aunits = hdr->trows * kPer, total = aunits + hdr->tcols * kPer;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (int64_t it = blockIdx.x; it < hdr->trows; it += gridDim.x) {  // block-uniform
-    const GroupedProblem& p = recs[grouped_find(recs, hdr->count, it, &GroupedProblem::trow_begin)];
-    const int64_t tm = it - p.trow_begin;
-    const int64_t r0 = tm * kOzTileRows;
-    const int rows = static_cast<int>((p.m - r0) < kOzTileRows ? (p.m - r0) : kOzTileRows);
-    // row maxima: a warp per row, four loads in flight per lane
-    for (int r = warp; r < rows; r += nwarps) {
-      const double* a0 = p.A + (r0 + r) * p.k;
-      uint64_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
-      int64_t l = lane;
-      for (; l + 96 < p.k; l += 128) {
-        const uint64_t b0 = static_cast<uint64_t>(__double_as_longlong(__ldg(a0 + l))) & kAbsMask;
-        const uint64_t b1 = static_cast<uint64_t>(__double_as_longlong(__ldg(a0 + l + 32))) & kAbsMask;
-        const uint64_t b2 = static_cast<uint64_t>(__double_as_longlong(__ldg(a0 + l + 64))) & kAbsMask;
-        const uint64_t b3 = static_cast<uint64_t>(__double_as_longlong(__ldg(a0 + l + 96))) & kAbsMask;
-        m0 = m0 > b0 ? m0 : b0;
-        m1 = m1 > b1 ? m1 : b1;
-        m2 = m2 > b2 ? m2 : b2;
-        m3 = m3 > b3 ? m3 : b3;
+  {
+    // the owner map, read by the later kernels of the call: a warp per problem
+    int32_t* owner = reinterpret_cast<int32_t*>(ws + hdr->off_owner);
+    const int64_t count = hdr->count, at = hdr->atiles, bt = hdr->btiles, stl = hdr->stiles;
+    for (int64_t q = static_cast<int64_t>(blockIdx.x) * nwarps + warp; q < count;
+         q += static_cast<int64_t>(gridDim.x) * nwarps) {
+      const GroupedProblem& r = recs[q];
+      const GroupedProblem* nx = q + 1 < count ? &recs[q + 1] : nullptr;
+      const int64_t b0[4] = {r.atile_begin, r.btile_begin, r.stile_begin, r.ltile_begin};
+      const int64_t b1[4] = {nx ? nx->atile_begin : at, nx ? nx->btile_begin : bt,
+                             nx ? nx->stile_begin : stl, nx ? nx->ltile_begin : hdr->ltiles};
+      const int64_t base[4] = {0, at, at + bt, at + bt + stl};
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        for (int64_t t = b0[f] + lane; t < b1[f]; t += 32)
+          owner[base[f] + t] = static_cast<int32_t>(q);
+    }
+  }
+  __shared__ int64_t unit;
+  __shared__ uint32_t red[8][kMaxUnit];
+  for (;;) {
+    if (threadIdx.x == 0) unit = static_cast<int64_t>(atomicAdd(cursor, 1ull));
+    __syncthreads();
+    const int64_t u = unit;
+    __syncthreads();  // every thread has read the unit before thread 0 takes the next
+    if (u >= total) break;  // block-uniform
+    if (u < aunits) {
+      // 32 rows of A: a warp per row, eight loads in flight per lane
+      const int64_t it = u / kPer;
+      const GroupedProblem& p =
+          recs[grouped_find(recs, hdr->count, it, &GroupedProblem::trow_begin)];
+      const int64_t r0 = (it - p.trow_begin) * kOzTileRows + (u - it * kPer) * kMaxUnit;
+      for (int r = warp; r < kMaxUnit && r0 + r < p.m; r += nwarps) {
+        const uint64_t mx = warp_row_max(p.A + (r0 + r) * p.k, p.k, lane);
+        if (lane == 0) {
+          rowbits[p.row_begin + r0 + r] = mx;
+          if (mx >= kInfBits) atomicOr(status, kStatusNonFinite);
+        }
       }
-      for (; l < p.k; l += 32) {
-        const uint64_t b0 = static_cast<uint64_t>(__double_as_longlong(__ldg(a0 + l))) & kAbsMask;
-        m0 = m0 > b0 ? m0 : b0;
+    } else {
+      // 32 columns of B: thread (h, c) takes column c of the rows l = h mod 8
+      // (a warp reads 256 contiguous bytes of a row), four rows in flight
+      const int64_t ic = (u - aunits) / kPer;
+      const GroupedProblem& p =
+          recs[grouped_find(recs, hdr->count, ic, &GroupedProblem::tcol_begin)];
+      const int64_t c0 =
+          (ic - p.tcol_begin) * kOzTileRows + (u - aunits - ic * kPer) * kMaxUnit;
+      const int c = threadIdx.x & (kMaxUnit - 1), h = threadIdx.x >> 5;
+      uint32_t mh = 0;
+      if (c0 + c < p.n) {
+        const double* bc = p.B + c0 + c;
+        uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+        int64_t l = h;
+        for (; l + 3 * 8 < p.k; l += 4 * 8) {
+          m0 = max(m0, abs_hi(__ldg(bc + l * p.n)));
+          m1 = max(m1, abs_hi(__ldg(bc + (l + 8) * p.n)));
+          m2 = max(m2, abs_hi(__ldg(bc + (l + 16) * p.n)));
+          m3 = max(m3, abs_hi(__ldg(bc + (l + 24) * p.n)));
+        }
+        for (; l < p.k; l += 8) m0 = max(m0, abs_hi(__ldg(bc + l * p.n)));
+        mh = max(max(m0, m1), max(m2, m3));
       }
-      m0 = m0 > m1 ? m0 : m1;
-      m2 = m2 > m3 ? m2 : m3;
-      m0 = warp_max_u64(m0 > m2 ? m0 : m2);
-      if (lane == 0) {
-        rowbits[p.row_begin + r0 + r] = m0;
-        if (m0 >= kInfBits) atomicOr(status, kStatusNonFinite);
+      red[h][c] = mh;
+      __syncthreads();
+      if (threadIdx.x < kMaxUnit && c0 + threadIdx.x < p.n) {
+        uint32_t hi = red[0][threadIdx.x];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) hi = max(hi, red[q][threadIdx.x]);
+        uint32_t lo = 0;
+        if (hi == 0)  // every high word of the column is zero
+          for (int64_t l = 0; l < p.k; ++l)
+            lo = max(lo, lo_word(__ldg(p.B + l * p.n + c0 + threadIdx.x)));
+        const uint64_t m = max_bits(hi, lo);
+        colbits[p.col_begin + c0 + threadIdx.x] = m;
+        if (m >= kInfBits) atomicOr(status, kStatusNonFinite);
       }
     }
-    __syncthreads();  // the maxima of these rows, written above, are read below
-    const int row_lim = rows >= kOzTileRows ? kOzTileRows : (rows + 7) / 8 * 8;
-    for (int64_t tk = 0; tk < p.Kt; ++tk)
-      split_a_tile<8>(p.A, p.m, p.k, rowbits + p.row_begin, S, beta, tm, tk,
-                      ws + hdr->off_a + static_cast<size_t>(p.atile_begin + tm * p.Kt + tk) *
-                                            kOzTileBytes,
-                      static_cast<size_t>(hdr->atiles) * kOzTileBytes, rn, row_lim,
-                      grouped_chunk_lim(p.k, p.Kt, tk));
-    __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(256) oz_grouped_prep_b_kernel(uint8_t* __restrict__ ws, int S,
-                                                                int beta, bool rn,
-                                                                int* __restrict__ status) {
+// Step 2: tile u of A's (u < atiles) or of B's operand tiles, dealt round
+// robin over the blocks (tiles of one problem go to neighbouring blocks, so
+// every block gets a like mix of large and small tiles); the owner map gives
+// each tile's problem.
+__global__ void __launch_bounds__(256, 4) oz_grouped_split_kernel(uint8_t* __restrict__ ws,
+                                                                  int S, int beta, bool rn) {
   const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
   if (!hdr->valid) return;
   const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
-  uint64_t* colbits = reinterpret_cast<uint64_t*>(ws + hdr->off_colbits);
+  const uint64_t* rowbits = reinterpret_cast<const uint64_t*>(ws + hdr->off_rowbits);
+  const uint64_t* colbits = reinterpret_cast<const uint64_t*>(ws + hdr->off_colbits);
+  const int32_t* owner = reinterpret_cast<const int32_t*>(ws + hdr->off_owner);
   __shared__ double sb[kSplitBRows][kOzTileRows + 1];
-  __shared__ uint64_t red[2][kOzTileRows];
-  for (int64_t it = blockIdx.x; it < hdr->tcols; it += gridDim.x) {  // block-uniform
-    const GroupedProblem& p = recs[grouped_find(recs, hdr->count, it, &GroupedProblem::tcol_begin)];
-    const int64_t tn = it - p.tcol_begin;
-    const int64_t c0 = tn * kOzTileRows;
-    const int cols = static_cast<int>((p.n - c0) < kOzTileRows ? (p.n - c0) : kOzTileRows);
-    // column maxima: thread t takes column t % 128 of every other row
-    // (consecutive threads read consecutive columns of a row)
-    {
-      const int c = threadIdx.x & (kOzTileRows - 1), h = threadIdx.x >> 7;
-      uint64_t mx = 0;
-      if (c < cols) {
-        // eight rows in flight per thread
-        const double* bc = p.B + c0 + c;
-        uint64_t mm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        int64_t l = h;
-        for (; l + 14 < p.k; l += 16) {
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const uint64_t b =
-                static_cast<uint64_t>(__double_as_longlong(__ldg(bc + (l + 2 * u) * p.n))) & kAbsMask;
-            mm[u] = mm[u] > b ? mm[u] : b;
-          }
-        }
-        for (; l < p.k; l += 2) {
-          const uint64_t b = static_cast<uint64_t>(__double_as_longlong(__ldg(bc + l * p.n))) & kAbsMask;
-          mm[0] = mm[0] > b ? mm[0] : b;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) mx = mx > mm[u] ? mx : mm[u];
-      }
-      red[h][c] = mx;
-    }
-    __syncthreads();
-    if (threadIdx.x < cols) {
-      const uint64_t a = red[0][threadIdx.x], b = red[1][threadIdx.x];
-      const uint64_t mx = a > b ? a : b;
-      colbits[p.col_begin + c0 + threadIdx.x] = mx;
-      if (mx >= kInfBits) atomicOr(status, kStatusNonFinite);
-    }
-    __syncthreads();  // the maxima written above are read by the split below
-    const int row_lim = cols >= kOzTileRows ? kOzTileRows : (cols + 15) / 16 * 16;
-    for (int64_t tk = 0; tk < p.Kt; ++tk)
-      split_b_tile<8>(p.B, p.k, p.n, colbits + p.col_begin, S, beta, tn, tk,
-                      ws + hdr->off_b + static_cast<size_t>(p.btile_begin + tn * p.Kt + tk) *
-                                            kOzTileBytes,
+  const int64_t atiles = hdr->atiles, total = atiles + hdr->btiles;
+  for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {  // block-uniform
+    const bool in_b = u >= atiles;
+    const int64_t t = in_b ? u - atiles : u;
+    const GroupedProblem& r = recs[owner[u]];
+    const int64_t local = t - (in_b ? r.btile_begin : r.atile_begin);
+    const int64_t tr = local / r.Kt, tk = local - tr * r.Kt;
+    const int lim = grouped_chunk_lim(r.k, r.Kt, tk);
+    if (!in_b) {
+      const int64_t rows = r.m - tr * kOzTileRows;
+      const int row_lim = rows >= kOzTileRows ? kOzTileRows : static_cast<int>((rows + 7) / 8 * 8);
+      split_a_tile<8>(r.A, r.m, r.k, rowbits + r.row_begin, S, beta, tr, tk,
+                      ws + hdr->off_a + static_cast<size_t>(t) * kOzTileBytes,
+                      static_cast<size_t>(atiles) * kOzTileBytes, rn, row_lim, lim);
+    } else {
+      const int64_t cols = r.n - tr * kOzTileRows;
+      const int row_lim =
+          cols >= kOzTileRows ? kOzTileRows : static_cast<int>((cols + 15) / 16 * 16);
+      split_b_tile<8>(r.B, r.k, r.n, colbits + r.col_begin, S, beta, tr, tk,
+                      ws + hdr->off_b + static_cast<size_t>(t) * kOzTileBytes,
                       static_cast<size_t>(hdr->btiles) * kOzTileBytes, sb, rn, false, row_lim,
-                      grouped_chunk_lim(p.k, p.Kt, tk));
+                      lim);
+    }
   }
 }
 
@@ -845,8 +906,8 @@ struct OzSingle {
 };
 
 // Tiles of a grouped call: the device plan (grouped_plan_kernel) lists every
-// problem with prefix sums of its tile counts; tile t belongs to the last
-// problem whose first tile is <= t.
+// problem with prefix sums of its tile counts; the owner map (written by the
+// maxima pass) gives the problem of C tile t.
 struct OzGrouped {
   const GroupedHeader* hdr;
   const GroupedProblem* recs;
@@ -886,8 +947,9 @@ struct OzGrouped {
   __device__ __forceinline__ OzTile tile(int64_t t) const {
     int64_t GroupedProblem::*begin = long_k ? &GroupedProblem::ltile_begin
                                             : &GroupedProblem::stile_begin;
-    const int64_t p = grouped_find(recs, hdr->count, t, begin);
-    const GroupedProblem& r = recs[p];
+    const int32_t* owner = reinterpret_cast<const int32_t*>(ws + hdr->off_owner) + hdr->atiles +
+                           hdr->btiles + (long_k ? hdr->stiles : 0);
+    const GroupedProblem& r = recs[owner[t]];
     const int64_t local = t - r.*begin;
     const int64_t tm = local / r.Nt, tn = local - (local / r.Nt) * r.Nt;
     OzTile j;
@@ -2291,10 +2353,8 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
 cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t short_kt, int* status,
                                  cudaStream_t s, bool rn) {
   const int sms = sm_count();
-  // many blocks per SM: the passes are latency-bound (a block reads its rows
-  // or columns, then splits tile by tile between block barriers)
-  oz_grouped_prep_a_kernel<<<sms * 16, 256, 0, s>>>(ws, S, beta, rn, status);
-  oz_grouped_prep_b_kernel<<<sms * 16, 256, 0, s>>>(ws, S, beta, rn, status);
+  oz_grouped_max_kernel<<<sms * 8, 256, 0, s>>>(ws, status);
+  oz_grouped_split_kernel<<<sms * 4, 256, 0, s>>>(ws, S, beta, rn);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
