@@ -1214,6 +1214,7 @@ __global__ void __launch_bounds__(128 + 32 * kEpiW, 1)
       bool acquired = false;
       int wcnt = 0;
       bool ok = true;
+      bool next_full = false;  // the next stage was seen full (mbar_test) during this one
       for (int64_t it = 0; ok; ++it) {
         const int ts = static_cast<int>(it % kTileRing);
         if (!mbar_wait_bounded(&sm.tfull[ts], static_cast<uint32_t>(it / kTileRing) & 1u,
@@ -1230,10 +1231,11 @@ __global__ void __launch_bounds__(128 + 32 * kEpiW, 1)
           int64_t kb = 0;
           int s = 1;
           for (int64_t st = 0; st < nst; ++st) {
-            if (!mbar_wait_bounded(&sm.full[stage], phase, abort_flag, status)) {
+            if (!next_full && !mbar_wait_bounded(&sm.full[stage], phase, abort_flag, status)) {
               ok = false;
               break;
             }
+            next_full = false;
             tc_fence_after();
             if (!acquired) {
               // a window of two slots starts on an even slot
@@ -1259,12 +1261,16 @@ __global__ void __launch_bounds__(128 + 32 * kEpiW, 1)
             const uint32_t d = tmem + static_cast<uint32_t>(first * kAccSlotCols);
             MXM_BOUNDS(first * kAccSlotCols + j.n_eff <= static_cast<int>(kAccCol) && nmma >= 1 &&
                            nmma <= kMmaPerStage, status);
+            const int nstage = stage + 1 == kStages ? 0 : stage + 1;
+            const uint32_t nphase = stage + 1 == kStages ? phase ^ 1u : phase;
 #pragma unroll
             for (int kk = 0; kk < kMmaPerStage; ++kk) {
               // k step kk: atom kk / 4 (16 KiB = +1024), 32 bytes per step inside it (+2)
               const uint64_t off = static_cast<uint64_t>((kk >> 2) * (kOzAtomBytes >> 4) + (kk & 3) * 2);
               if (kk < nmma)
                 mma_bf16_ss(d, da + off, db + off, idesc, (kk > 0 || wcnt > 0) ? 1u : 0u);
+              // half-way: look at the next stage while these MMAs run
+              if (kk == kMmaPerStage / 2 - 1) next_full = mbar_test(&sm.full[nstage], nphase);
             }
             mma_commit(&sm.empty[stage]);
             ++wcnt;
@@ -1779,6 +1785,18 @@ __global__ void __launch_bounds__(kP2Threads, 1)
       bool acq = false;
       uint32_t uses0 = 0u, uses1 = 0u;  // windows started in this issuer's two buffers
       bool ok = true;
+      // the next A / B ring slot was seen full (mbar_test) during this
+      // issuer's last MMAs: its wait is skipped (the acquire fence of the
+      // pair form is still taken)
+      bool a_seen = false, b_seen = false;
+      auto wait_full = [&](uint64_t* bars, int slot, uint32_t phase, bool& seen) -> bool {
+        if (seen) {
+          seen = false;
+          if constexpr (kPair) fence_acquire_cluster_shared();
+          return true;
+        }
+        return mbar_wait_bounded<false, kPair>(&bars[slot], phase, abort_flag, status);
+      };
       auto commit = [&](uint64_t* bar) {
         if constexpr (kPair)
           mma_commit_pair(bar, static_cast<uint16_t>(0x3));
@@ -1811,9 +1829,14 @@ __global__ void __launch_bounds__(kP2Threads, 1)
                    status);
         const uint32_t acc0 = cnt > 0 ? 1u : 0u;
 #pragma unroll
-        for (int kk = 0; kk < Fmt::kMmas; ++kk)
+        for (int kk = 0; kk < Fmt::kMmas; ++kk) {
           if (!kEdges || kk < nmma)
             Fmt::mma(d, da + Fmt::koff(kk), db + Fmt::kboff(kk), idesc, kk > 0 ? 1u : acc0);
+          if (kk == Fmt::kMmas / 2 - 1) {  // half-way: the slots the next waits are on
+            a_seen = mbar_test<kPair>(&sm.a_full[ra.slot], ra.phase);
+            b_seen = mbar_test<kPair>(&sm.b_full[rb.slot], rb.phase);
+          }
+        }
       };
       auto finish = [&](bool last) {
         if (++cnt == window || last) {
@@ -1832,7 +1855,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
           for (int64_t kb = 0; kb < Kt && ok; ++kb) {
             if constexpr (kEdges)
               nmma = tiles.kblock(q, kb, Kt) == Kt - 1 ? jt.last_mmas : Fmt::kMmas;
-            if (!mbar_wait_bounded<false, kPair>(&sm.b_full[rb.slot], rb.phase, abort_flag, status)) {
+            if (!wait_full(sm.b_full, rb.slot, rb.phase, b_seen)) {
               ok = false;
               break;
             }
@@ -1840,7 +1863,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
             rb.advance();
             if (x == 1) release(&sm.b_empty[bprev]);
             for (int s = 1; s <= g - 1; ++s) {
-              if (!mbar_wait_bounded<false, kPair>(&sm.a_full[ra.slot], ra.phase, abort_flag, status)) {
+              if (!wait_full(sm.a_full, ra.slot, ra.phase, a_seen)) {
                 ok = false;
                 break;
               }
@@ -1848,8 +1871,7 @@ __global__ void __launch_bounds__(kP2Threads, 1)
               ra.advance();
               int bnew = -1;
               if (s <= g - 2) {
-                if (!mbar_wait_bounded<false, kPair>(&sm.b_full[rb.slot], rb.phase, abort_flag,
-                                              status)) {
+                if (!wait_full(sm.b_full, rb.slot, rb.phase, b_seen)) {
                   ok = false;
                   break;
                 }

@@ -137,6 +137,38 @@ __device__ __forceinline__ void fence_acquire_cluster_shared() {
   asm volatile("fence.acquire.sync_restrict::shared::cluster.cluster;" ::: "memory");
 }
 
+// Non-blocking test of a phase (mbarrier.test_wait), for an MMA issuer to
+// look at the next stage's barrier while its current MMAs are in flight: one
+// thread feeds the tensor core with little queueing, so a blocking wait
+// between two stages leaves it idle for the wait's round trip, while a test
+// issued in the middle of a stage returns behind the remaining MMAs.  A
+// completed phase of a full barrier stays complete until the waiter itself
+// releases the slot, so a positive result stays valid until it is used.
+// kRemote: relaxed at cluster scope (the caller takes
+// fence_acquire_cluster_shared before using the slot, as after
+// mbar_try_wait_relaxed_cluster); otherwise acquire at CTA scope.
+template <bool kRemote = false>
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  if constexpr (kRemote)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.relaxed.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  return ok != 0;
+}
+
 // Wait until the phase with the given parity has completed.  Returns false
 // (and raises the abort flag and the status bit) after `limit_ns`, or at once
 // if another role of the block has already aborted.  kCluster: cluster-scope
