@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--no-check", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--suite", nargs="?", const="all",
-                   choices=("all", "gemm", "spmv", "cg", "fft", "probes"),
+                   choices=("all", "gemm", "grouped", "spmv", "cg", "fft", "probes"),
                    help="instead of the benchmark line: one JSON line per case of the "
                         "workload suite (FP64 sweep, slice counts and modes, rectangular "
                         "shapes, grouped batch under a CUDA graph; mod2as sparse products; "
@@ -543,6 +543,9 @@ def run_suite(args):
         run_fft_suite(emit, stream, args.only)
     if args.suite in ("spmv", "cg", "fft"):
         return
+    if args.suite == "grouped":
+        run_grouped_suite(emit, stream, names)
+        return
     dmma = mxm.mxm_peak_probe(1)
 
     def one(case, kind, m, k, n, runs, reps=3, seed=0, cfg=2, tuned=False):
@@ -586,8 +589,16 @@ def run_suite(args):
     for (m, k, n) in ((16384, 256, 16384), (128, 65536, 128), (32768, 1024, 64)):
         one("rectangular", "uniform", m, k, n,
             [(mxm.MODE_F64, 0), (mxm.MODE_EMUL_I8, 6), (mxm.MODE_EMUL_BF16, 5)], tuned=True)
-    # grouped: 2000 problems, m, k, n log-uniform in [16, 1024], one launch
-    # sequence captured in a CUDA graph and replayed
+    run_grouped_suite(emit, stream, names)
+
+
+def run_grouped_suite(emit, stream, names):
+    """The grouped batch: 2000 problems, m, k, n log-uniform in [16, 1024],
+    one launch sequence per mode captured in a CUDA graph and replayed."""
+    import numpy as np
+    import torch
+
+    from paper_1211_1581_gb300 import inputs, mxm, tune
     dims = [tuple(int(v) for v in d) for d in inputs.grouped_problems(0, 2000)]
     ds = []
     for p, (m, k, n) in enumerate(dims):
