@@ -386,6 +386,7 @@ __device__ __forceinline__ void split_a_tile(const double* __restrict__ A, int64
 // is read in four passes of 32 rows of B (coalesced along the rows) through
 // shared memory, then every thread takes V consecutive k of one column.
 constexpr int kSplitBRows = 32;
+constexpr int kSplitThreads = 256;  // the block size of the split launches
 template <int V>
 __device__ __forceinline__ void split_b_tile(const double* __restrict__ B, int64_t k, int64_t n,
                                              const uint64_t* __restrict__ colbits, int S,
@@ -400,10 +401,26 @@ __device__ __forceinline__ void split_b_tile(const double* __restrict__ B, int64
   for (int pass = 0; pass < kOzTileK / kSplitBRows; ++pass) {
     if (pass * kChunksPerPass >= chunk_lim) break;  // block-uniform
     const int64_t l0 = tk * kOzTileK + pass * kSplitBRows;
-    for (int p = threadIdx.x; p < kSplitBRows * kOzTileRows; p += blockDim.x) {
-      const int lr = p / kOzTileRows, cc = p % kOzTileRows;
-      const int64_t l = l0 + lr, col = col0 + cc;
-      sb[lr][cc] = (l < k && col < n) ? __ldg(B + l * n + col) : 0.0;
+    if (blockDim.x == kSplitThreads) {  // every launch: all of a thread's loads in flight at once
+      constexpr int kPer = kSplitBRows * kOzTileRows / kSplitThreads;
+      double v[kPer];
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int p = threadIdx.x + i * kSplitThreads;
+        const int64_t l = l0 + p / kOzTileRows, col = col0 + p % kOzTileRows;
+        v[i] = (l < k && col < n) ? __ldg(B + l * n + col) : 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int p = threadIdx.x + i * kSplitThreads;
+        sb[p / kOzTileRows][p % kOzTileRows] = v[i];
+      }
+    } else {
+      for (int p = threadIdx.x; p < kSplitBRows * kOzTileRows; p += blockDim.x) {
+        const int lr = p / kOzTileRows, cc = p % kOzTileRows;
+        const int64_t l = l0 + lr, col = col0 + cc;
+        sb[lr][cc] = (l < k && col < n) ? __ldg(B + l * n + col) : 0.0;
+      }
     }
     __syncthreads();
     constexpr int kChunks = kSplitBRows / V;  // chunks of V k per column in a pass
