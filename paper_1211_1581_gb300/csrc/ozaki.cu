@@ -357,27 +357,39 @@ __device__ __forceinline__ void split_a_tile(const double* __restrict__ A, int64
                                              int chunk_lim = SplitGeo<V>::kChunksPerRow) {
   using G = SplitGeo<V>;
   const bool pairs = ((k & 1) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
-#pragma unroll 2
-  for (int p = threadIdx.x; p < row_lim * chunk_lim; p += blockDim.x) {
-    const int c = p % chunk_lim, r = p / chunk_lim;
-    const int64_t row = tm * kOzTileRows + r;
-    const int64_t k0 = tk * kOzTileK + c * V;
-    double v[V];
-    int e = 0;
-    if (row < m) e = exponent_from_absbits(rowbits[row]);
-    const double* src = A + row * k + k0;
-    if (row < m && pairs && k0 + V <= k) {
+  const int total = row_lim * chunk_lim;
+  // two chunks per thread and step, both loaded before either is split
+  for (int p0 = threadIdx.x; p0 < total; p0 += 2 * blockDim.x) {
+    double v[2][V];
+    int e[2], rr[2], cc[2];
 #pragma unroll
-      for (int j = 0; j < V; j += 2) {
-        const double2 t = __ldg(reinterpret_cast<const double2*>(src + j));
-        v[j] = t.x;
-        v[j + 1] = t.y;
+    for (int h = 0; h < 2; ++h) {
+      const int p = p0 + h * static_cast<int>(blockDim.x);
+      const bool live = p < total;
+      const int c = live ? p % chunk_lim : 0, r = live ? p / chunk_lim : 0;
+      rr[h] = r;
+      cc[h] = c;
+      const int64_t row = tm * kOzTileRows + r;
+      const int64_t k0 = tk * kOzTileK + c * V;
+      const bool in = live && row < m;
+      e[h] = in ? exponent_from_absbits(rowbits[row]) : 0;
+      const double* src = A + (in ? row : 0) * k + k0;
+      if (in && pairs && k0 + V <= k) {
+#pragma unroll
+        for (int j = 0; j < V; j += 2) {
+          const double2 t = __ldg(reinterpret_cast<const double2*>(src + j));
+          v[h][j] = t.x;
+          v[h][j + 1] = t.y;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) v[h][j] = (in && k0 + j < k) ? __ldg(src + j) : 0.0;
       }
-    } else {
-#pragma unroll
-      for (int j = 0; j < V; ++j) v[j] = (row < m && k0 + j < k) ? __ldg(src + j) : 0.0;
     }
-    split_chunk(v, e, S, beta, tile + G::offset(r, c), slice_stride, rn);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (p0 + h * static_cast<int>(blockDim.x) < total)
+        split_chunk(v[h], e[h], S, beta, tile + G::offset(rr[h], cc[h]), slice_stride, rn);
   }
 }
 
@@ -650,7 +662,7 @@ __global__ void __launch_bounds__(256) oz_grouped_max_kernel(uint8_t* __restrict
 // robin over the blocks (tiles of one problem go to neighbouring blocks, so
 // every block gets a like mix of large and small tiles); the owner map gives
 // each tile's problem.
-__global__ void __launch_bounds__(256, 4) oz_grouped_split_kernel(uint8_t* __restrict__ ws,
+__global__ void __launch_bounds__(256, 3) oz_grouped_split_kernel(uint8_t* __restrict__ ws,
                                                                   int S, int beta, bool rn) {
   const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
   if (!hdr->valid) return;
@@ -2393,7 +2405,7 @@ cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t short_kt,
                                  cudaStream_t s, bool rn) {
   const int sms = sm_count();
   oz_grouped_max_kernel<<<sms * 8, 256, 0, s>>>(ws, status);
-  oz_grouped_split_kernel<<<sms * 4, 256, 0, s>>>(ws, S, beta, rn);
+  oz_grouped_split_kernel<<<sms * 3, 256, 0, s>>>(ws, S, beta, rn);  // 3 resident per SM
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
