@@ -485,10 +485,23 @@ __global__ void __launch_bounds__(256) oz_scale_split_a_kernel(
   const bool real = i < m;
   const double* a = A + (real ? i : 0) * k;
   uint32_t mh = 0;
-  for (int64_t l = threadIdx.x; l < kp; l += blockDim.x) {
-    const double v = (real && l < k) ? __ldg(a + l) : 0.0;
-    row[l] = v;
-    mh = max(mh, abs_hi(v));
+  // eight loads of a thread in flight before they go to shared memory
+  // (few blocks fit an SM with a whole row in shared memory)
+  for (int64_t l0 = threadIdx.x; l0 < kp; l0 += 8 * static_cast<int64_t>(blockDim.x)) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t l = l0 + u * static_cast<int64_t>(blockDim.x);
+      v[u] = (real && l < k) ? __ldg(a + l) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t l = l0 + u * static_cast<int64_t>(blockDim.x);
+      if (l < kp) {
+        row[l] = v[u];
+        mh = max(mh, abs_hi(v[u]));
+      }
+    }
   }
   mh = warp_max_u32(mh);
   if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mh;
