@@ -138,3 +138,30 @@ def test_grouped_2000_logu_sampled():
                 assert_bitwise(got, oracle.ozaki_gemm(A, B, S=S), f"p={p}")
             assert_within_bound(got, oracle.gemm_dot2(A, B), oracle.gemm_abs(A, B),
                                 A.shape[1], f"p={p} mode={mode}")
+
+
+def test_grouped_many_small_problems():
+    """6000 problems with m, k, n uniform in [0, 48], empty ones included:
+    thousands of claims on the maxima pass's cursor and on the slice GEMM's
+    tile cursor, and every operand tile's and C tile's problem taken from
+    the owner map.  300 random problems and every empty one are checked
+    against the oracle (bit-identical for the emulated modes)."""
+    rng = np.random.default_rng(11)
+    dims = [tuple(int(v) for v in rng.integers(0, 49, 3)) for _ in range(6000)]
+    hs, ds = make_group(dims, seed=4, kind="spread")
+    pick = sorted(set(rng.choice(len(dims), 300, replace=False).tolist())
+                  | {p for p, d in enumerate(dims) if 0 in d})
+    for mode, S in ((mxm.MODE_EMUL_I8, 7), (mxm.MODE_EMUL_RN8, 6), (mxm.MODE_F64, 0)):
+        for _, _, C in ds:
+            C.fill_(float("nan"))
+        assert run_group(ds, mode, S) == mxm.MXM_OK
+        for p in pick:
+            A, B = hs[p]
+            got = ds[p][2].cpu().numpy()
+            if mode == mxm.MODE_F64:
+                assert_within_bound(got, oracle.gemm_dot2(A, B), oracle.gemm_abs(A, B),
+                                    A.shape[1], f"p={p} {dims[p]}")
+            elif mode == mxm.MODE_EMUL_RN8:
+                assert_bitwise(got, oracle.ozaki_gemm_rn8(A, B, S), f"p={p} {dims[p]}")
+            else:
+                assert_bitwise(got, oracle.ozaki_gemm(A, B, S=S), f"p={p} {dims[p]}")
