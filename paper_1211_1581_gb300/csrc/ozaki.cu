@@ -436,8 +436,11 @@ __device__ __forceinline__ void split_b_tile(const double* __restrict__ B, int64
     }
     __syncthreads();
     constexpr int kChunks = kSplitBRows / V;  // chunks of V k per column in a pass
+    // consecutive threads take the consecutive chunks of one tile row (a
+    // row's chunks of a pass are one aligned group under the swizzle, so
+    // their 16-byte stores are contiguous)
     for (int p = threadIdx.x; p < kOzTileRows * kChunks; p += blockDim.x) {
-      const int r = p % kOzTileRows, cl = p / kOzTileRows;
+      const int r = p / kChunks, cl = p % kChunks;
       if (r >= row_lim || pass * kChunks + cl >= chunk_lim) continue;
       const int64_t col = col0 + r;
       const int f = col < n ? exponent_from_absbits(colbits[col]) : 0;
