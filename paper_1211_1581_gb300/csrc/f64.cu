@@ -164,9 +164,10 @@ __global__ void __launch_bounds__(256) f64_splitk_reduce_kernel(const double* __
 // SM) is the limit, so the operands are read straight from the caller's
 // arrays (L1/L2 serve the reuse) with no packed copies, and the pieces are
 // small enough that padding wastes little: every product is cut at 32 rows,
-// 32 columns and 4 k.  Each warp holds its 32 x 32 piece as 2 x 4 DMMA
-// m16n8 accumulators and reads the fragments of the next k step while the
-// current ones multiply.
+// 32 columns and 4 k, and the DMMA blocks of an edge piece that lie wholly
+// past the last row (16) or column (8) are not issued.  Each warp holds its
+// 32 x 32 piece as 2 x 4 DMMA m16n8 accumulators and reads the fragments of
+// the next k step while the current ones multiply.
 constexpr int kGroupedF64Threads = 256;
 
 __device__ __forceinline__ void load_frags(const double* __restrict__ A,
@@ -224,6 +225,9 @@ __global__ void __launch_bounds__(kGroupedF64Threads, 2)
       for (int ni = 0; ni < 4; ++ni)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[mi][ni][q] = 0.0;
+    // the m16 / n8 blocks holding any row / column of C (warp-uniform)
+    const bool mlive1 = row0 + 16 < m;
+    const int nlive = static_cast<int>((n - col0 + 7) / 8 < 4 ? (n - col0 + 7) / 8 : 4);
     double a[4], b[4], an[4], bn[4];
     load_frags(A, B, k, n, arow, bcol, rmask, cmask, t4, a, b);
     for (int64_t k0 = 0; k0 < k; k0 += kF64GroupedK) {
@@ -232,7 +236,8 @@ __global__ void __launch_bounds__(kGroupedF64Threads, 2)
       for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
         for (int ni = 0; ni < 4; ++ni)
-          dmma_16x8x4(acc[mi][ni], a[2 * mi], a[2 * mi + 1], b[ni]);
+          if ((mi == 0 || mlive1) && ni < nlive)
+            dmma_16x8x4(acc[mi][ni], a[2 * mi], a[2 * mi + 1], b[ni]);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         a[i] = an[i];
