@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "mxm_internal.h"
 #include "ptx.cuh"
@@ -332,6 +333,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   bool ok = true;
   for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
     const F64Tile j = tiles.tile(t);
+    // the m16 / n8 blocks of this warp's 32 x 64 region that hold any row /
+    // column of C (warp-uniform); the others are not issued (edge tiles)
+    const int64_t rows_left = j.m - (j.row0 + wm * 32);
+    const int64_t cols_left = j.n - (j.col0 + wn * 64);
+    const int mlive = rows_left <= 0 ? 0 : (rows_left > 16 ? 2 : 1);
+    const int nlive =
+        cols_left <= 0 ? 0 : (cols_left >= 64 ? 8 : static_cast<int>((cols_left + 7) / 8));
     double acc[2][8][4];
 #pragma unroll
     for (int mi = 0; mi < 2; ++mi)
@@ -340,37 +348,48 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[mi][ni][q] = 0.0;
 
-    for (int64_t kb = 0; kb < j.Kt; ++kb) {
-      if (!mbar_wait_bounded(&sm.full[stage], phase, abort_flag, status)) {
-        ok = false;
-        break;
-      }
-      const double* As = sm.a[stage];
-      const double* Bs = sm.b[stage];
-#pragma unroll
-      for (int kk = 0; kk < BK / 4; ++kk) {
-        const int c = kk * 4 + t4;
-        double a[2][2], b[8];
-#pragma unroll
-        for (int mi = 0; mi < 2; ++mi) {
-          const int r0 = wm * 32 + mi * 16 + g;
-          a[mi][0] = As[swz(r0, c)];
-          a[mi][1] = As[swz(r0 + 8, c)];
+    // kEdge: the predicated form for a region only partly inside C; whole
+    // regions keep the plain loop
+    auto kloop = [&](auto edge) {
+      constexpr bool kEdge = decltype(edge)::value;
+      for (int64_t kb = 0; kb < j.Kt; ++kb) {
+        if (!mbar_wait_bounded(&sm.full[stage], phase, abort_flag, status)) {
+          ok = false;
+          break;
         }
+        const double* As = sm.a[stage];
+        const double* Bs = sm.b[stage];
 #pragma unroll
-        for (int ni = 0; ni < 8; ++ni) b[ni] = Bs[swz(wn * 64 + ni * 8 + g, c)];
+        for (int kk = 0; kk < BK / 4; ++kk) {
+          const int c = kk * 4 + t4;
+          double a[2][2], b[8];
 #pragma unroll
-        for (int mi = 0; mi < 2; ++mi)
+          for (int mi = 0; mi < 2; ++mi) {
+            const int r0 = wm * 32 + mi * 16 + g;
+            a[mi][0] = As[swz(r0, c)];
+            a[mi][1] = As[swz(r0 + 8, c)];
+          }
 #pragma unroll
-          for (int ni = 0; ni < 8; ++ni) dmma_16x8x4(acc[mi][ni], a[mi][0], a[mi][1], b[ni]);
+          for (int ni = 0; ni < 8; ++ni) b[ni] = Bs[swz(wn * 64 + ni * 8 + g, c)];
+#pragma unroll
+          for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+            for (int ni = 0; ni < 8; ++ni)
+              if (!kEdge || (mi < mlive && ni < nlive))
+                dmma_16x8x4(acc[mi][ni], a[mi][0], a[mi][1], b[ni]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.empty[stage]);
+        if (++stage == kStages) {
+          stage = 0;
+          phase ^= 1u;
+        }
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sm.empty[stage]);
-      if (++stage == kStages) {
-        stage = 0;
-        phase ^= 1u;
-      }
-    }
+    };
+    if (mlive == 2 && nlive == 8)
+      kloop(std::false_type{});
+    else
+      kloop(std::true_type{});
     if (!ok) break;
 
     // epilogue: D fragment (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1)
