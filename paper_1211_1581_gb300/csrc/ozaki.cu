@@ -1037,10 +1037,11 @@ __device__ __forceinline__ int oz_exact_from(int S, int beta, int64_t Kt) {
   return gx;
 }
 
-// The final scaling of one result, out of line (like fold_step below) to
-// keep the epilogues compact: the instruction caches are small, and code
-// repeated for every element of a tile row overflowed them.
-__device__ __noinline__ double final_scale(uint64_t st, int e) {
+// The final scaling of one result.  Inline: the folds that call it are
+// rolled loops over a few columns at a time, so the code stays small (the
+// out-of-line form cost the grouped short-k GEMM ~1 % in call overhead and
+// the 8192^3 product nothing).
+__device__ __forceinline__ double final_scale(uint64_t st, int e) {
   return ldexp_rn(__longlong_as_double(static_cast<long long>(st)), e);
 }
 
