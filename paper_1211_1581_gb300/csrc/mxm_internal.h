@@ -336,7 +336,8 @@ struct GroupedHeader {
   int64_t off_sums, off_spill;  // emulated: running sums of every C tile, spill areas
   int64_t cursor_max;      // next unit of the emulated maxima pass (zeroed like cursor)
   int64_t off_owner;       // emulated: the problem (int32) owning each A tile, B tile,
-                           // short-k C tile and long-k C tile, in that order
+                           // short-k C tile, long-k C tile, A tile-row and B
+                           // tile-column, in that order
 };
 
 constexpr size_t kGroupedRecordsOff = 256;
@@ -368,7 +369,8 @@ __host__ __device__ inline void grouped_offsets(GroupedHeader& h, int planes, si
                            1024);
   h.off_owner = off;
   if (bits)
-    off = align_up(off + 4 * static_cast<size_t>(h.atiles + h.btiles + h.stiles + h.ltiles + 1),
+    off = align_up(off + 4 * static_cast<size_t>(h.atiles + h.btiles + h.stiles + h.ltiles +
+                                                 h.trows + h.tcols + 1),
                    1024);
   h.total = off;
 }

@@ -564,12 +564,13 @@ __global__ void __launch_bounds__(256) oz_split_b_kernel(
 }
 
 // ---------------------------------------------------------------- grouped steps 1-2
-// The scale and the split of a grouped call, in two passes over the operands.
-// oz_grouped_max_kernel (step 1) takes units of 32 rows of A or 32 columns
-// of B of one problem, their cost following k, from a cursor in the plan's
-// header (zeroed by the plan kernel on every call).  oz_grouped_split_kernel
-// (step 2) takes the 128 x 128 operand tiles, A's then B's, in equal
-// contiguous runs per block.  Only what the edge-tile copies of the slice
+// The scale and the split of a grouped call, in two passes over the operands,
+// after oz_grouped_owner_kernel has written the owner map (each unit's
+// problem).  oz_grouped_max_kernel (step 1) takes units of 32 rows of A or 32
+// columns of B of one problem, their cost following k, from a cursor in the
+// plan's header (zeroed by the plan kernel on every call).
+// oz_grouped_split_kernel (step 2) takes the 128 x 128 operand tiles, A's
+// then B's, round robin over the blocks.  Only what the edge-tile copies of the slice
 // GEMM read is written: rows up to the tile's rows rounded up to 8 (A) or
 // columns up to 16 (B, the MMA's N step), and in the last k-block the
 // 16-byte chunks up to k rounded up to 16 (with zeros past k).
@@ -583,6 +584,38 @@ __device__ __forceinline__ int grouped_chunk_lim(int64_t k, int64_t Kt, int64_t 
 
 constexpr int kMaxUnit = 32;  // rows of A or columns of B per unit of the maxima pass
 
+// The owner map of a grouped call: for every A tile, B tile, short-k C tile,
+// long-k C tile, A tile-row and B tile-column the index of its problem (the
+// later kernels look a unit's problem up instead of searching the problem
+// table).  A warp per problem.
+__global__ void __launch_bounds__(256) oz_grouped_owner_kernel(uint8_t* __restrict__ ws) {
+  const GroupedHeader* hdr = reinterpret_cast<const GroupedHeader*>(ws);
+  if (!hdr->valid) return;
+  const GroupedProblem* recs = reinterpret_cast<const GroupedProblem*>(ws + kGroupedRecordsOff);
+  int32_t* owner = reinterpret_cast<int32_t*>(ws + hdr->off_owner);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int64_t count = hdr->count;
+  const int64_t tot[6] = {hdr->atiles, hdr->btiles, hdr->stiles, hdr->ltiles, hdr->trows,
+                          hdr->tcols};
+  int64_t base[6];
+  base[0] = 0;
+  for (int f = 1; f < 6; ++f) base[f] = base[f - 1] + tot[f - 1];
+  for (int64_t q = static_cast<int64_t>(blockIdx.x) * nwarps + warp; q < count;
+       q += static_cast<int64_t>(gridDim.x) * nwarps) {
+    const GroupedProblem& r = recs[q];
+    const GroupedProblem* nx = q + 1 < count ? &recs[q + 1] : nullptr;
+    const int64_t b0[6] = {r.atile_begin, r.btile_begin, r.stile_begin, r.ltile_begin,
+                           r.trow_begin, r.tcol_begin};
+    const int64_t b1[6] = {nx ? nx->atile_begin : tot[0], nx ? nx->btile_begin : tot[1],
+                           nx ? nx->stile_begin : tot[2], nx ? nx->ltile_begin : tot[3],
+                           nx ? nx->trow_begin : tot[4], nx ? nx->tcol_begin : tot[5]};
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+      for (int64_t t = b0[f] + lane; t < b1[f]; t += 32)
+        owner[base[f] + t] = static_cast<int32_t>(q);
+  }
+}
+
 __global__ void __launch_bounds__(256) oz_grouped_max_kernel(uint8_t* __restrict__ ws,
                                                              int* __restrict__ status) {
   GroupedHeader* hdr = reinterpret_cast<GroupedHeader*>(ws);
@@ -594,24 +627,10 @@ __global__ void __launch_bounds__(256) oz_grouped_max_kernel(uint8_t* __restrict
   constexpr int kPer = kOzTileRows / kMaxUnit;  // units per tile-row (tile-column)
   const int64_t aunits = hdr->trows * kPer, total = aunits + hdr->tcols * kPer;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  {
-    // the owner map, read by the later kernels of the call: a warp per problem
-    int32_t* owner = reinterpret_cast<int32_t*>(ws + hdr->off_owner);
-    const int64_t count = hdr->count, at = hdr->atiles, bt = hdr->btiles, stl = hdr->stiles;
-    for (int64_t q = static_cast<int64_t>(blockIdx.x) * nwarps + warp; q < count;
-         q += static_cast<int64_t>(gridDim.x) * nwarps) {
-      const GroupedProblem& r = recs[q];
-      const GroupedProblem* nx = q + 1 < count ? &recs[q + 1] : nullptr;
-      const int64_t b0[4] = {r.atile_begin, r.btile_begin, r.stile_begin, r.ltile_begin};
-      const int64_t b1[4] = {nx ? nx->atile_begin : at, nx ? nx->btile_begin : bt,
-                             nx ? nx->stile_begin : stl, nx ? nx->ltile_begin : hdr->ltiles};
-      const int64_t base[4] = {0, at, at + bt, at + bt + stl};
-#pragma unroll
-      for (int f = 0; f < 4; ++f)
-        for (int64_t t = b0[f] + lane; t < b1[f]; t += 32)
-          owner[base[f] + t] = static_cast<int32_t>(q);
-    }
-  }
+  // the problem of each A tile-row and B tile-column (the owner map)
+  const int32_t* rowowner = reinterpret_cast<const int32_t*>(ws + hdr->off_owner) +
+                            hdr->atiles + hdr->btiles + hdr->stiles + hdr->ltiles;
+  const int32_t* colowner = rowowner + hdr->trows;
   __shared__ int64_t unit;
   __shared__ uint32_t red[8][kMaxUnit];
   for (;;) {
@@ -621,24 +640,49 @@ __global__ void __launch_bounds__(256) oz_grouped_max_kernel(uint8_t* __restrict
     __syncthreads();  // every thread has read the unit before thread 0 takes the next
     if (u >= total) break;  // block-uniform
     if (u < aunits) {
-      // 32 rows of A: a warp per row, eight loads in flight per lane
+      // 32 rows of A
       const int64_t it = u / kPer;
-      const GroupedProblem& p =
-          recs[grouped_find(recs, hdr->count, it, &GroupedProblem::trow_begin)];
+      const GroupedProblem& p = recs[rowowner[it]];
       const int64_t r0 = (it - p.trow_begin) * kOzTileRows + (u - it * kPer) * kMaxUnit;
-      for (int r = warp; r < kMaxUnit && r0 + r < p.m; r += nwarps) {
-        const uint64_t mx = warp_row_max(p.A + (r0 + r) * p.k, p.k, lane);
-        if (lane == 0) {
-          rowbits[p.row_begin + r0 + r] = mx;
-          if (mx >= kInfBits) atomicOr(status, kStatusNonFinite);
+      // a warp takes four rows at once (their loads in flight together:
+      // most rows are short)
+      for (int rb = warp; rb < kMaxUnit; rb += 4 * nwarps) {
+        const double* ar[4];
+        bool live[4];
+        uint32_t mh[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int64_t row = r0 + rb + i * nwarps;
+          live[i] = rb + i * nwarps < kMaxUnit && row < p.m;
+          ar[i] = p.A + (live[i] ? row : 0) * p.k;
+          mh[i] = 0;
+        }
+        for (int64_t l = lane; l < p.k; l += 32) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (live[i]) mh[i] = max(mh[i], abs_hi(__ldg(ar[i] + l)));
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (!live[i]) continue;  // warp-uniform
+          const uint32_t hi = warp_max_u32(mh[i]);
+          uint32_t lo = 0;
+          if (hi == 0) {  // every high word of the row is zero: the low words
+            for (int64_t l = lane; l < p.k; l += 32) lo = max(lo, lo_word(__ldg(ar[i] + l)));
+            lo = warp_max_u32(lo);
+          }
+          const uint64_t mx = max_bits(hi, lo);
+          if (lane == 0) {
+            rowbits[p.row_begin + r0 + rb + i * nwarps] = mx;
+            if (mx >= kInfBits) atomicOr(status, kStatusNonFinite);
+          }
         }
       }
     } else {
       // 32 columns of B: thread (h, c) takes column c of the rows l = h mod 8
       // (a warp reads 256 contiguous bytes of a row), four rows in flight
       const int64_t ic = (u - aunits) / kPer;
-      const GroupedProblem& p =
-          recs[grouped_find(recs, hdr->count, ic, &GroupedProblem::tcol_begin)];
+      const GroupedProblem& p = recs[colowner[ic]];
       const int64_t c0 =
           (ic - p.tcol_begin) * kOzTileRows + (u - aunits - ic * kPer) * kMaxUnit;
       const int c = threadIdx.x & (kMaxUnit - 1), h = threadIdx.x >> 5;
@@ -951,8 +995,8 @@ struct OzSingle {
 };
 
 // Tiles of a grouped call: the device plan (grouped_plan_kernel) lists every
-// problem with prefix sums of its tile counts; the owner map (written by the
-// maxima pass) gives the problem of C tile t.
+// problem with prefix sums of its tile counts; the owner map (written by
+// oz_grouped_owner_kernel) gives the problem of C tile t.
 struct OzGrouped {
   const GroupedHeader* hdr;
   const GroupedProblem* recs;
@@ -2421,6 +2465,7 @@ cudaError_t launch_ozaki_gemm(const uint8_t* aslices, const uint8_t* bslices,
 cudaError_t launch_ozaki_grouped(uint8_t* ws, int S, int beta, int64_t short_kt, int* status,
                                  cudaStream_t s, bool rn) {
   const int sms = sm_count();
+  oz_grouped_owner_kernel<<<sms * 2, 256, 0, s>>>(ws);
   oz_grouped_max_kernel<<<sms * 8, 256, 0, s>>>(ws, status);
   oz_grouped_split_kernel<<<sms * 3, 256, 0, s>>>(ws, S, beta, rn);  // 3 resident per SM
   cudaError_t e = cudaGetLastError();
